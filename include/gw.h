@@ -1,0 +1,154 @@
+/*
+ * gw.h -- C ABI of the GB300 periodic G0W0 hot path (localized RI, imaginary axis).
+ *
+ * The operations follow Ren et al., "All-electron periodic G0W0 implementation
+ * with numerical atomic orbital basis functions" (arXiv:2011.01400):
+ *   gw_chi0   -- Eqs. (AO_triple_split2), (AO_MO_transform), (chi0_matrix):
+ *                LRI triple coefficients -> band-pair coefficients M -> chi0(q, i w)
+ *   gw_screen -- Eqs. (symm_dielec_func), (screened_W_matr); Gamma point per
+ *                Eq. (dielectric_func_gamma): eps~ = 1 - V^1/2 chi0 V^1/2,
+ *                W^c = V^1/2 (eps~^{-1} - 1) V^1/2
+ *   gw_sigma  -- Eq. (GW_selfe_element) with W^c: Sigma_c_n(k, i w), one q term
+ *   gw_qp     -- continuation of Sigma_c to the real axis (Sec. II.A) and the
+ *                quasiparticle equation; indirect gap
+ *
+ * Conventions (all calls):
+ *   - Atomic units (Hartree, bohr). Complex numbers are gw_complex {re, im}
+ *     (layout of C99 double _Complex, numpy complex128, cuDoubleComplex).
+ *   - Mesh: Gamma-centred, k index = (i1*n2 + i2)*n3 + i3, fractional
+ *     coordinate (i1/n1, i2/n2, i3/n3); the q mesh equals the k mesh.
+ *   - "device" pointers are CUDA device memory owned by the caller; the
+ *     library only reads inputs and writes the outputs named per call.
+ *     "host" pointers are ordinary CPU memory.
+ *   - Every call is ordered on the plan's stream and returns a gw_status; none
+ *     aborts or throws. A failed call leaves the plan in an error state that
+ *     sticks until gw_plan_destroy (later calls return GW_ERR_STATE).
+ *     gw_last_error() returns a text for the last failure of this thread.
+ *   - Matrices are row-major. Hermitian outputs are written in full.
+ *   - No call uses more than the one current CUDA device.
+ */
+#ifndef GW_H
+#define GW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GW_OK = 0,
+  GW_ERR_ARG = 1,        /* invalid argument or size; nothing was launched           */
+  GW_ERR_NOMEM = 2,      /* device workspace allocation failed                       */
+  GW_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed               */
+  GW_ERR_NOT_PD = 4,     /* eps~ had a non-positive Cholesky pivot (chi0 not NSD)    */
+  GW_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up (pipeline stalled)     */
+  GW_ERR_STATE = 6,      /* call out of order (e.g. gw_screen before gw_chi0 for q)  */
+  GW_ERR_UNSUPPORTED = 7 /* valid request this build does not implement                */
+} gw_status;
+
+typedef enum {
+  GW_FP64 = 0,    /* plain method: every contraction in FP64 on CUDA cores          */
+  GW_3XTF32 = 1,  /* contractions as 3 TF32 split products on tcgen05, FP32 accum.   */
+  GW_3XBF16 = 2   /* contractions as 3 BF16 split products on tcgen05, FP32 accum.   */
+} gw_precision;
+
+typedef struct { double re, im; } gw_complex;
+
+typedef struct gw_plan_s* gw_plan;
+
+/* The problem, Sec. II of the paper. Sizes:
+ *   N_k = nk[0]*nk[1]*nk[2];  n_b(A), n_aux(A) = basis / ABF functions on atom A. */
+typedef struct {
+  int32_t nk[3];                 /* k mesh (= q mesh), each >= 1                            */
+  int32_t n_atoms, n_basis, n_bands, n_occ, n_aux;
+  const int32_t* basis_atom;     /* host [n_basis]: atom of each NAO, non-decreasing        */
+  const int32_t* aux_atom;       /* host [n_aux]:   atom of each ABF, non-decreasing        */
+  int32_t n_R;                   /* number of lattice vectors with stored LRI coefficients */
+  const int32_t* R;              /* host [n_R][3] lattice vectors in lattice coordinates    */
+  const double* eps;             /* device [N_k][n_bands] KS energies, ascending per k      */
+  const gw_complex* evec;        /* device [N_k][n_basis][n_bands] KS eigenvectors c_{i,n}(k) */
+  const double* ctil_R;          /* device: atoms concatenated in order; atom A block is
+                                    [n_R][n_aux(A)][n_b(A)][n_basis] = C~_{i(0),j(R)}^{mu(0)},
+                                    mu and i on A, j any (Eq. two_center_coeff_determination) */
+  const gw_complex* V;           /* device [N_k][n_aux][n_aux] Coulomb matrix V(q), Hermitian
+                                    positive definite (the truncated V^cut at q = 0)          */
+  const gw_complex* pmom;        /* device [N_k][3][n_bands][n_bands] momentum matrix p_mn(k);
+                                    may be NULL when head_wings == 0                          */
+  double omega_cell;             /* unit-cell volume (bohr^3), > 0 when head_wings != 0      */
+  double qhat[3];                /* direction of q -> 0 for the head and wings               */
+  int32_t head_wings;            /* 1: Gamma point by Eq. dielectric_func_gamma; 0: regular  */
+  int32_t n_freq;                /* imaginary frequencies, modified Gauss-Legendre, 1..256   */
+  double omega0;                 /* grid scale: w_j = omega0 (1+x_j)/(1-x_j) (Ha), > 0       */
+  int32_t sigma_lo, sigma_hi;    /* self-energy bands [sigma_lo, sigma_hi), 0-based          */
+  double spin;                   /* spin factor in chi0 (2 for doubly occupied bands)        */
+  double mu;                     /* chemical potential; NaN selects midgap                   */
+  gw_precision prec;
+} gw_problem;
+
+/* Build a plan: validates `prob`, copies the host arrays, allocates the
+ * library's own workspace, and on `stream` precomputes the half-transformed
+ * LRI coefficients (Eqs. expan_coeff_FT1/2 contracted with c(k)), V(q)^{1/2}
+ * for every q and the Coulomb eigenvector lambda = 1 at q = 0.
+ * `n_sys` must be 1. `stream` is a cudaStream_t (NULL = legacy default).
+ * On success *out owns the workspace until gw_plan_destroy.
+ * Errors: GW_ERR_ARG (bad sizes/pointers), GW_ERR_NOMEM, GW_ERR_CUDA. */
+gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw_plan* out);
+
+/* Release the plan and its workspace (waits for the plan's stream). NULL is a no-op. */
+gw_status gw_plan_destroy(gw_plan plan);
+
+/* chi0_{mu nu}(q, i w_j) for all j (Eq. chi0_matrix, Hermitised, occupations restored):
+ *   chi0 = -(s/N_k) sum_k sum_{i occ, a unocc} M^mu_{ai}(k,q) M^nu_{ai}(k,q)^* 2D/(w^2+D^2),
+ *   D = eps_a(k+q) - eps_i(k), M from the LRI coefficients (Eqs. AO_triple_split2, AO_MO_transform).
+ * chi0_out: device [n_freq][n_aux][n_aux] or NULL (kept only inside the plan).
+ * Errors: GW_ERR_ARG (sys, q out of range), GW_ERR_CUDA, GW_ERR_TIMEOUT. */
+gw_status gw_chi0(gw_plan plan, int32_t sys, int32_t q, gw_complex* chi0_out);
+
+/* W^c(q, i w_j) = V^1/2 (eps~^{-1} - 1) V^1/2, eps~ = 1 - V^1/2 chi0 V^1/2 (Eqs. symm_dielec_func,
+ * screened_W_matr); at q = 0 with head_wings, eps~ is assembled in the Coulomb eigenbasis
+ * with the head and wings of Eq. dielectric_func_gamma (insulator: f' term dropped).
+ * Uses the chi0 of the last gw_chi0 call, which must be for the same q (else GW_ERR_STATE).
+ * wc_out: device [n_freq][n_aux][n_aux] or NULL. eps~ is factorised and inverted in FP64.
+ * Errors: GW_ERR_STATE, GW_ERR_NOT_PD, GW_ERR_CUDA. */
+gw_status gw_screen(gw_plan plan, int32_t sys, int32_t q, gw_complex* wc_out);
+
+/* Adds the q term of Eq. (GW_selfe_element) with W^c in place of W:
+ *   Sigma_c_n(k, i w) += -(1/(2 pi N_q)) sum_m sum_j g_j S_nm(k,q,w'_j) 2z/(z^2 + w'_j^2),
+ *   S_nm = sum_{mu nu} C^mu_{nm}(k,k-q) W^c_{mu nu}(q, i w'_j) C^nu_{mn}(k-q,k),
+ *   z = i w + mu - eps_m(k-q), n in [sigma_lo, sigma_hi), m over all bands.
+ * Uses the W^c of the last gw_screen call, which must be for the same q (else GW_ERR_STATE).
+ * sigma_acc: device [N_k][sigma_hi-sigma_lo][n_freq], accumulated into (caller zeroes it),
+ *            or NULL to accumulate into the plan's own buffer (zeroed at plan creation). */
+gw_status gw_sigma(gw_plan plan, int32_t sys, int32_t q, gw_complex* sigma_acc);
+
+/* Quasiparticle energies: Sigma_c(i w) continued with the two-pole model
+ * (p1 z + p0)/(z^2 + q1 z + q0) fitted by linear least squares on all n_freq points,
+ * then E = eps_n + Re Sigma_c(E - mu) + dxv_n by Newton (tolerance 1e-10 Ha; linearised
+ * fallback flagged by a negative converged count). All in FP64 on the device.
+ * sigma:  device [N_k][n_sigma][n_freq], or NULL for the plan's own accumulator.
+ * dxv:    device [N_k][n_sigma] (Sigma_x - v_xc) or NULL for zero.
+ * e_qp:   host [N_k][n_sigma] output.
+ * gap:    host scalar output, min_k E_LUMO - max_k E_HOMO when both are in the window, else NaN.
+ * n_conv: host scalar output (may be NULL): number of (k, n) whose Newton iteration converged. */
+gw_status gw_qp(gw_plan plan, int32_t sys, const gw_complex* sigma, const double* dxv,
+                double* e_qp, double* gap, int32_t* n_conv);
+
+/* Host copies of the plan's frequency grid (w_j and quadrature weights g_j), [n_freq] each. */
+gw_status gw_plan_freq(gw_plan plan, double* freq, double* weight);
+
+/* Chemical potential the plan uses (host scalar). */
+gw_status gw_plan_mu(gw_plan plan, double* mu);
+
+/* Device time of the last chi0 contraction launch (ms, CUDA events on the plan's stream),
+ * and its algorithmic flop count (8 per complex multiply-add, Hermitian lower triangle). */
+gw_status gw_plan_last_chi0_stats(gw_plan plan, double* ms, double* flops);
+
+/* Text of the last error on the calling thread ("" if none). Never NULL. */
+const char* gw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GW_H */

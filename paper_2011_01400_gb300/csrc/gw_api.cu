@@ -1,0 +1,714 @@
+// C ABI of the G0W0 hot path: plan creation and the per-q calls (see include/gw.h).
+#include "gw_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace gw;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gw_status fail(gw_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define GW_CUDA(call)                                                                                  \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) {                                                                           \
+      return fail(GW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    }                                                                                                  \
+  } while (0)
+
+// Gauss-Legendre nodes and weights on (-1, 1) by Newton's method on P_n (ascending nodes).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int l = 2; l <= n; ++l) {
+        double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = (n == 1) ? z : p1;
+      double pm = (n == 1) ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+      double dz = pn / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = z;
+      for (int l = 2; l <= n; ++l) {
+        double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = (n == 1) ? z : p1, pm = (n == 1) ? 1.0 : p0;
+      dp = n * (z * pn - pm) / (z * z - 1.0);
+    }
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+template <typename T> struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+__global__ void k_frob_scale(int N, const c128* V, long long s, double* out) {
+  __shared__ double red[256];
+  const c128* a = V + blockIdx.x * s;
+  double acc = 0;
+  for (long long e = threadIdx.x; e < (long long)N * N; e += blockDim.x) acc += a[e].re * a[e].re + a[e].im * a[e].im;
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int t = blockDim.x / 2; t > 0; t >>= 1) {
+    if (threadIdx.x < t) red[threadIdx.x] += red[threadIdx.x + t];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sqrt(red[0]);
+}
+
+// Y = V / c (typed), Z = I
+template <typename T>
+__global__ void k_ns_init(int N, const c128* V, long long s, const double* c, cplx<T>* Y, cplx<T>* Z) {
+  const int b = blockIdx.y;
+  const double inv = 1.0 / c[b];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)N * N;
+       e += (long long)gridDim.x * blockDim.x) {
+    c128 v = V[b * s + e];
+    Y[b * s + e] = cplx<T>{(T)(v.re * inv), (T)(v.im * inv)};
+    int i = (int)(e / N), j = (int)(e % N);
+    Z[b * s + e] = cplx<T>{(T)(i == j ? 1 : 0), (T)0};
+  }
+}
+// out = sqrt(c) * Y (c128)
+template <typename T>
+__global__ void k_ns_final(int N, const cplx<T>* Y, long long s, const double* c, c128* out) {
+  const int b = blockIdx.y;
+  const double f = sqrt(c[b]);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)N * N;
+       e += (long long)gridDim.x * blockDim.x) {
+    cplx<T> y = Y[b * s + e];
+    out[b * s + e] = c128{f * (double)y.re, f * (double)y.im};
+  }
+}
+
+}  // namespace
+
+struct gw_plan_s {
+  gw_problem p{};
+  gw_precision prec;
+  bool fp64;
+  cudaStream_t st = nullptr;
+  int NK, N, NB, NBd, nocc, nunocc, nsig, nw, natoms;
+  std::vector<int> basis_atom, aux_atom, R;
+  LriGeom geom{};
+  std::vector<double> freq, fweight;
+  double mu = 0.0;
+  int err = 0;              // sticky error
+  int chi0_q = -1, wc_q = -1;
+  // device memory owned by the plan
+  std::vector<void*> allocs;
+  double *d_freq = nullptr, *d_fw = nullptr, *d_mu = nullptr;
+  void* d_T1 = nullptr;     // c128 (FP64) or c64 (split)
+  c128* d_Vh = nullptr;     // [NK][N][N] V(q)^1/2 (full, truncated at q=0)
+  c128* d_Vb0 = nullptr;    // [N][N] V(0)^1/2 without the lambda=1 component
+  c128* d_x1 = nullptr;     // [N]
+  double* d_v1 = nullptr;
+  double h_v1 = 0.0;
+  c128* d_chi0 = nullptr;   // [nw][N][N]
+  c128* d_E = nullptr;      // [nw][N][N] eps~ then eps~^-1 - 1
+  c128* d_Wc = nullptr;     // [nw][N][N]
+  c128* d_work = nullptr;   // [nw][N][N]
+  c128* d_tmp = nullptr;    // [nw][N][N]
+  c128* d_sigma = nullptr;  // [NK][nsig][nw]
+  double* d_head = nullptr; // [nw]
+  c128* d_h = nullptr;      // [nw][N]
+  int* d_status = nullptr;
+  // chunk workspaces
+  int chi_nkk = 1, sig_nkk = 1;
+  void* d_M = nullptr;        // chi0 M [N][ldm] (c128 or c64)
+  long long ldm = 0;
+  double* d_delta = nullptr;  // [ldm]
+  float* d_delta_f = nullptr;
+  c128* d_pq = nullptr;       // [ldm]
+  void* d_A = nullptr;        // sigma rows [R][N]
+  void* d_U = nullptr;        // [R][N]
+  double* d_S_d = nullptr;    // [R][nw]
+  float* d_S_f = nullptr;
+  long long sig_rows = 0;
+  // timing of the chi0 contraction
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double last_chi0_ms = 0.0, last_chi0_flops = 0.0;
+};
+
+namespace {
+
+template <typename T> gw_status dalloc(gw_plan_s* P, T** ptr, size_t count) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GW_ERR_NOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " +
+                                  cudaGetErrorString(e));
+  }
+  P->allocs.push_back(p);
+  *ptr = static_cast<T*>(p);
+  return GW_OK;
+}
+
+#define GW_TRY(x)                    \
+  do {                               \
+    gw_status s_ = (x);              \
+    if (s_ != GW_OK) return s_;      \
+  } while (0)
+
+gw_status check_launch(gw_plan_s* P, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    P->err = 1;
+    return fail(GW_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  }
+  return GW_OK;
+}
+
+gw_status read_status(gw_plan_s* P, const char* where) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, P->d_status, sizeof(int), cudaMemcpyDeviceToHost, P->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);
+  if (e != cudaSuccess) {
+    P->err = 1;
+    return fail(GW_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  }
+  if (st & ST_TIMEOUT) {
+    P->err = 1;
+    return fail(GW_ERR_TIMEOUT, std::string(where) + ": a device-side wait exceeded its bound");
+  }
+  if (st & ST_NOT_PD) {
+    P->err = 1;
+    return fail(GW_ERR_NOT_PD, std::string(where) + ": eps~ is not positive definite (non-positive pivot)");
+  }
+  if (st & ST_BADARG) {
+    P->err = 1;
+    return fail(GW_ERR_CUDA, std::string(where) + ": a kernel bounds check failed");
+  }
+  return GW_OK;
+}
+
+// V^1/2 of a batch of Hermitian PD matrices by the coupled Newton-Schulz iteration
+//   Y0 = V/c, Z0 = I;  T = (3 I - Z Y)/2;  Y <- Y T;  Z <- T Z;   V^1/2 = sqrt(c) Y,
+// c = ||V||_F. FP64 for the FP64 method, FP32 otherwise.
+template <typename T>
+gw_status newton_schulz(gw_plan_s* P, const c128* V, c128* out, int batch, int iters) {
+  const int N = P->N;
+  const long long s = (long long)N * N;
+  double* d_c;
+  cplx<T> *Y, *Z, *Tm, *Y2;
+  GW_TRY(dalloc(P, &d_c, batch));
+  GW_TRY(dalloc(P, &Y, s * batch));
+  GW_TRY(dalloc(P, &Z, s * batch));
+  GW_TRY(dalloc(P, &Tm, s * batch));
+  GW_TRY(dalloc(P, &Y2, s * batch));
+  k_frob_scale<<<batch, 256, 0, P->st>>>(N, V, s, d_c);
+  dim3 g(std::min<long long>((s + 255) / 256, 1024), batch);
+  k_ns_init<T><<<g, 256, 0, P->st>>>(N, V, s, d_c, Y, Z);
+  const cplx<T> one{(T)1, (T)0}, zero{(T)0, (T)0}, mhalf{(T)-0.5, (T)0};
+  for (int it = 0; it < iters; ++it) {
+    // Tm = -0.5 Z Y + 1.5 I
+    launch_zgemm<T>(N, N, N, mhalf, Z, N, s, OP_N, Y, N, s, OP_N, zero, Tm, N, s, batch, P->st);
+    launch_axpby_identity<T>(N, Tm, s, batch, (T)1.5, P->st);
+    launch_zgemm<T>(N, N, N, one, Y, N, s, OP_N, Tm, N, s, OP_N, zero, Y2, N, s, batch, P->st);
+    launch_zgemm<T>(N, N, N, one, Tm, N, s, OP_N, Z, N, s, OP_N, zero, Y, N, s, batch, P->st);  // Y <- T Z (temp)
+    std::swap(Z, Y);   // Z = T Z
+    std::swap(Y, Y2);  // Y = Y T
+  }
+  k_ns_final<T><<<g, 256, 0, P->st>>>(N, Y, s, d_c, out);
+  GW_TRY(check_launch(P, "newton_schulz"));
+  cudaError_t e = cudaStreamSynchronize(P->st);
+  if (e != cudaSuccess) return fail(GW_ERR_CUDA, std::string("newton_schulz: ") + cudaGetErrorString(e));
+  // release the temporaries (they were the last five allocations)
+  for (int i = 0; i < 5; ++i) {
+    cudaFree(P->allocs.back());
+    P->allocs.pop_back();
+  }
+  return GW_OK;
+}
+
+gw_status validate(const gw_problem* p, int n_sys) {
+  if (!p) return fail(GW_ERR_ARG, "problem is NULL");
+  if (n_sys != 1) return fail(GW_ERR_UNSUPPORTED, "n_sys must be 1 in this build");
+  for (int d = 0; d < 3; ++d)
+    if (p->nk[d] < 1 || p->nk[d] > 64) return fail(GW_ERR_ARG, "nk out of range [1, 64]");
+  if (p->n_atoms < 1 || p->n_atoms > 64) return fail(GW_ERR_ARG, "n_atoms out of range [1, 64]");
+  if (p->n_basis < 1 || p->n_bands < 2 || p->n_bands > p->n_basis) return fail(GW_ERR_ARG, "bad n_basis / n_bands");
+  if (p->n_occ < 1 || p->n_occ >= p->n_bands) return fail(GW_ERR_ARG, "n_occ must be in [1, n_bands)");
+  if (p->n_aux < 1 || p->n_aux > 4096) return fail(GW_ERR_ARG, "n_aux out of range [1, 4096]");
+  if (!p->basis_atom || !p->aux_atom || !p->R) return fail(GW_ERR_ARG, "basis_atom / aux_atom / R is NULL");
+  if (p->n_R < 1 || p->n_R > 64) return fail(GW_ERR_ARG, "n_R out of range [1, 64]");
+  if (!p->eps || !p->evec || !p->ctil_R || !p->V) return fail(GW_ERR_ARG, "a device input pointer is NULL");
+  if (p->head_wings && (!p->pmom || !(p->omega_cell > 0.0)))
+    return fail(GW_ERR_ARG, "head_wings needs pmom and omega_cell > 0");
+  if (p->n_freq < 1 || p->n_freq > 256) return fail(GW_ERR_ARG, "n_freq out of range [1, 256]");
+  if (!(p->omega0 > 0.0)) return fail(GW_ERR_ARG, "omega0 must be > 0");
+  if (p->sigma_lo < 0 || p->sigma_hi > p->n_bands || p->sigma_lo >= p->sigma_hi)
+    return fail(GW_ERR_ARG, "sigma window must satisfy 0 <= lo < hi <= n_bands");
+  if (!(p->spin > 0.0)) return fail(GW_ERR_ARG, "spin must be > 0");
+  if (p->prec != GW_FP64 && p->prec != GW_3XTF32 && p->prec != GW_3XBF16) return fail(GW_ERR_ARG, "bad precision");
+  for (int i = 0; i < p->n_basis; ++i) {
+    if (p->basis_atom[i] < 0 || p->basis_atom[i] >= p->n_atoms) return fail(GW_ERR_ARG, "basis_atom out of range");
+    if (i && p->basis_atom[i] < p->basis_atom[i - 1]) return fail(GW_ERR_ARG, "basis_atom must be non-decreasing");
+  }
+  for (int i = 0; i < p->n_aux; ++i) {
+    if (p->aux_atom[i] < 0 || p->aux_atom[i] >= p->n_atoms) return fail(GW_ERR_ARG, "aux_atom out of range");
+    if (i && p->aux_atom[i] < p->aux_atom[i - 1]) return fail(GW_ERR_ARG, "aux_atom must be non-decreasing");
+  }
+  return GW_OK;
+}
+
+bool plan_ok(gw_plan P, int32_t sys, gw_status* s) {
+  if (!P) {
+    *s = fail(GW_ERR_ARG, "plan is NULL");
+    return false;
+  }
+  if (P->err) {
+    *s = fail(GW_ERR_STATE, "plan is in an error state from an earlier call");
+    return false;
+  }
+  if (sys != 0) {
+    *s = fail(GW_ERR_ARG, "sys out of range");
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gw_last_error(void) { return g_last_error.c_str(); }
+
+gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw_plan* out) {
+  if (!out) return fail(GW_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  GW_TRY(validate(prob, n_sys));
+  gw_plan_s* P = new (std::nothrow) gw_plan_s();
+  if (!P) return fail(GW_ERR_NOMEM, "host allocation failed");
+  P->p = *prob;
+  P->prec = prob->prec;
+  P->fp64 = prob->prec == GW_FP64;
+  P->st = static_cast<cudaStream_t>(stream);
+  P->NK = prob->nk[0] * prob->nk[1] * prob->nk[2];
+  P->N = prob->n_aux;
+  P->NB = prob->n_basis;
+  P->NBd = prob->n_bands;
+  P->nocc = prob->n_occ;
+  P->nunocc = prob->n_bands - prob->n_occ;
+  P->nsig = prob->sigma_hi - prob->sigma_lo;
+  P->nw = prob->n_freq;
+  P->natoms = prob->n_atoms;
+  P->basis_atom.assign(prob->basis_atom, prob->basis_atom + prob->n_basis);
+  P->aux_atom.assign(prob->aux_atom, prob->aux_atom + prob->n_aux);
+  P->R.assign(prob->R, prob->R + 3 * prob->n_R);
+  P->p.basis_atom = P->basis_atom.data();
+  P->p.aux_atom = P->aux_atom.data();
+  P->p.R = P->R.data();
+  auto cleanup = [&](gw_status s) {
+    std::string msg = g_last_error;
+    gw_plan_destroy(P);
+    g_last_error = msg;
+    return s;
+  };
+  // geometry
+  LriGeom& g = P->geom;
+  g.n_atoms = P->natoms;
+  g.NK = P->NK;
+  g.NB = P->NB;
+  g.NBd = P->NBd;
+  g.N = P->N;
+  g.nR = prob->n_R;
+  for (int d = 0; d < 3; ++d) g.nk[d] = prob->nk[d];
+  long long coff = 0, toff = 0;
+  for (int A = 0; A < P->natoms; ++A) {
+    int b0 = -1, nb = 0, x0 = -1, nx = 0;
+    for (int i = 0; i < P->NB; ++i)
+      if (P->basis_atom[i] == A) {
+        if (b0 < 0) b0 = i;
+        ++nb;
+      }
+    for (int i = 0; i < P->N; ++i)
+      if (P->aux_atom[i] == A) {
+        if (x0 < 0) x0 = i;
+        ++nx;
+      }
+    if (nb == 0 || nx == 0) return cleanup(fail(GW_ERR_ARG, "every atom needs >= 1 basis and >= 1 aux function"));
+    g.atom_b0[A] = b0;
+    g.atom_nb[A] = nb;
+    g.atom_x0[A] = x0;
+    g.atom_nx[A] = nx;
+    g.ctil_off[A] = coff;
+    g.t_off[A] = toff;
+    coff += (long long)prob->n_R * nx * nb * P->NB;
+    toff += (long long)P->NK * nx * nb * P->NBd;
+  }
+  for (int r = 0; r < prob->n_R; ++r)
+    for (int d = 0; d < 3; ++d) g.R[r][d] = P->R[3 * r + d];
+  // frequency grid
+  std::vector<double> x, w;
+  gauss_legendre(P->nw, x, w);
+  P->freq.resize(P->nw);
+  P->fweight.resize(P->nw);
+  for (int j = 0; j < P->nw; ++j) {
+    P->freq[j] = prob->omega0 * (1.0 + x[j]) / (1.0 - x[j]);
+    P->fweight[j] = 2.0 * prob->omega0 * w[j] / ((1.0 - x[j]) * (1.0 - x[j]));
+  }
+  const int N = P->N, nw = P->nw;
+  const size_t NN = (size_t)N * N;
+  gw_status s;
+#define ALLOC(ptr, n)                                 \
+  do {                                                \
+    s = dalloc(P, &ptr, (n));                         \
+    if (s != GW_OK) return cleanup(s);                \
+  } while (0)
+  ALLOC(P->d_freq, nw);
+  ALLOC(P->d_fw, nw);
+  ALLOC(P->d_mu, 1);
+  ALLOC(P->d_status, 1);
+  ALLOC(P->d_Vh, NN * P->NK);
+  ALLOC(P->d_chi0, NN * nw);
+  ALLOC(P->d_E, NN * nw);
+  ALLOC(P->d_Wc, NN * nw);
+  ALLOC(P->d_work, NN * nw);
+  ALLOC(P->d_tmp, NN * nw);
+  ALLOC(P->d_sigma, (size_t)P->NK * P->nsig * nw);
+  ALLOC(P->d_head, nw);
+  ALLOC(P->d_h, (size_t)nw * N);
+  if (P->fp64) {
+    c128* t;
+    ALLOC(t, (size_t)toff);
+    P->d_T1 = t;
+  } else {
+    c64* t;
+    ALLOC(t, (size_t)toff);
+    P->d_T1 = t;
+  }
+  if (prob->head_wings) {
+    ALLOC(P->d_Vb0, NN);
+    ALLOC(P->d_x1, N);
+    ALLOC(P->d_v1, 1);
+  }
+  // chunk sizes: ~512 MB per M-type buffer
+  const size_t esz = P->fp64 ? sizeof(c128) : sizeof(c64);
+  const size_t budget = 512ull << 20;
+  const long long rows_chi = (long long)P->nocc * P->nunocc;
+  P->chi_nkk = (int)std::max<long long>(1, std::min<long long>(P->NK, budget / (rows_chi * N * esz)));
+  P->ldm = ((rows_chi * P->chi_nkk + 31) / 32) * 32;
+  const long long rows_sig = (long long)P->nsig * P->NBd;
+  P->sig_nkk = (int)std::max<long long>(1, std::min<long long>(P->NK, budget / (rows_sig * N * esz)));
+  P->sig_rows = rows_sig * P->sig_nkk;
+  if (P->fp64) {
+    c128 *a, *b, *c;
+    ALLOC(a, (size_t)N * P->ldm);
+    ALLOC(b, (size_t)P->sig_rows * N);
+    ALLOC(c, (size_t)P->sig_rows * N);
+    P->d_M = a;
+    P->d_A = b;
+    P->d_U = c;
+    ALLOC(P->d_S_d, (size_t)P->sig_rows * nw);
+  } else {
+    c64 *a, *b, *c;
+    ALLOC(a, (size_t)N * P->ldm);
+    ALLOC(b, (size_t)P->sig_rows * N);
+    ALLOC(c, (size_t)P->sig_rows * N);
+    P->d_M = a;
+    P->d_A = b;
+    P->d_U = c;
+    ALLOC(P->d_S_f, (size_t)P->sig_rows * nw);
+  }
+  ALLOC(P->d_delta, P->ldm);
+  ALLOC(P->d_delta_f, P->ldm);
+  ALLOC(P->d_pq, P->ldm);
+#undef ALLOC
+  if (cudaEventCreate(&P->ev0) != cudaSuccess || cudaEventCreate(&P->ev1) != cudaSuccess)
+    return cleanup(fail(GW_ERR_CUDA, "cudaEventCreate failed"));
+  cudaStream_t st = P->st;
+#define CK(call)                                                                                     \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return cleanup(fail(GW_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_))); \
+  } while (0)
+  CK(cudaMemcpyAsync(P->d_freq, P->freq.data(), nw * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(P->d_fw, P->fweight.data(), nw * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(P->d_sigma, 0, sizeof(c128) * (size_t)P->NK * P->nsig * nw, st));
+  // chemical potential
+  if (std::isnan(prob->mu)) {
+    launch_midgap(P->NK, P->NBd, P->nocc, prob->eps, P->d_mu, st);
+  } else {
+    CK(cudaMemcpyAsync(P->d_mu, &prob->mu, sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(&P->mu, P->d_mu, sizeof(double), cudaMemcpyDeviceToHost, st));
+  // half-transformed LRI coefficients
+  if (P->fp64)
+    launch_lri_halfT<double>(g, prob->ctil_R, reinterpret_cast<const c128*>(prob->evec),
+                             static_cast<c128*>(P->d_T1), nullptr, st);
+  else
+    launch_lri_halfT<float>(g, prob->ctil_R, reinterpret_cast<const c128*>(prob->evec), static_cast<c64*>(P->d_T1),
+                            nullptr, st);
+  if ((s = check_launch(P, "lri_halfT")) != GW_OK) return cleanup(s);
+  // V(q)^1/2; at q = 0 with head_wings split off the lambda = 1 eigenvector first
+  const c128* V = reinterpret_cast<const c128*>(prob->V);
+  CK(cudaMemcpyAsync(P->d_Vh, V, sizeof(c128) * NN * P->NK, cudaMemcpyDeviceToDevice, st));
+  double t_shift = 1.0;
+  if (prob->head_wings) {
+    launch_power_iter(N, V, P->d_x1, P->d_v1, 200, st);
+    CK(cudaMemcpyAsync(&P->h_v1, P->d_v1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<c128> diag(N);
+    CK(cudaMemcpy2DAsync(diag.data(), sizeof(c128), V, sizeof(c128) * (N + 1), sizeof(c128), N,
+                         cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double tr = 0;
+    for (int i = 0; i < N; ++i) tr += diag[i].re;
+    t_shift = N > 1 ? std::max(1e-3, (tr - P->h_v1) / (N - 1)) : 1.0;
+    // B = V(0) - v1 x1 x1^H + t x1 x1^H
+    launch_rank1(N, P->d_Vh, P->d_x1, t_shift - P->h_v1, st);
+  }
+  if (P->fp64)
+    s = newton_schulz<double>(P, P->d_Vh, P->d_Vh, P->NK, 40);
+  else
+    s = newton_schulz<float>(P, P->d_Vh, P->d_Vh, P->NK, 40);
+  if (s != GW_OK) return cleanup(s);
+  if (prob->head_wings) {
+    // Vb0 = sqrt(B) - sqrt(t) x1 x1^H ;  Vh(0) = Vb0 + sqrt(v1) x1 x1^H
+    launch_rank1(N, P->d_Vh, P->d_x1, -std::sqrt(t_shift), st);
+    CK(cudaMemcpyAsync(P->d_Vb0, P->d_Vh, sizeof(c128) * NN, cudaMemcpyDeviceToDevice, st));
+    launch_rank1(N, P->d_Vh, P->d_x1, std::sqrt(std::max(P->h_v1, 0.0)), st);
+  }
+  if ((s = check_launch(P, "plan setup")) != GW_OK) return cleanup(s);
+  CK(cudaStreamSynchronize(st));
+#undef CK
+  *out = P;
+  return GW_OK;
+}
+
+gw_status gw_plan_destroy(gw_plan P) {
+  if (!P) return GW_OK;
+  if (P->st) cudaStreamSynchronize(P->st);
+  else cudaDeviceSynchronize();
+  for (void* a : P->allocs) cudaFree(a);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  delete P;
+  return GW_OK;
+}
+
+gw_status gw_plan_freq(gw_plan P, double* freq, double* weight) {
+  if (!P) return fail(GW_ERR_ARG, "plan is NULL");
+  if (freq) std::copy(P->freq.begin(), P->freq.end(), freq);
+  if (weight) std::copy(P->fweight.begin(), P->fweight.end(), weight);
+  return GW_OK;
+}
+
+gw_status gw_plan_mu(gw_plan P, double* mu) {
+  if (!P || !mu) return fail(GW_ERR_ARG, "NULL argument");
+  *mu = P->mu;
+  return GW_OK;
+}
+
+gw_status gw_plan_last_chi0_stats(gw_plan P, double* ms, double* flops) {
+  if (!P) return fail(GW_ERR_ARG, "plan is NULL");
+  if (ms) *ms = P->last_chi0_ms;
+  if (flops) *flops = P->last_chi0_flops;
+  return GW_OK;
+}
+
+gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw;
+  const size_t NN = (size_t)N * N;
+  const c128* evec = reinterpret_cast<const c128*>(P->p.evec);
+  GW_CUDA(cudaMemsetAsync(P->d_chi0, 0, sizeof(c128) * NN * nw, st));
+  const bool hw = P->p.head_wings && q == 0;
+  if (hw) {
+    std::vector<double> ones(nw, 1.0);
+    GW_CUDA(cudaMemcpyAsync(P->d_head, ones.data(), nw * sizeof(double), cudaMemcpyHostToDevice, st));
+    GW_CUDA(cudaMemsetAsync(P->d_h, 0, sizeof(c128) * nw * N, st));
+  }
+  const double scale = -P->p.spin / P->NK;
+  const int na = P->nunocc, nb = P->nocc;
+  float total_ms = 0.f;
+  for (int kk0 = 0; kk0 < P->NK; kk0 += P->chi_nkk) {
+    const int nkk = std::min(P->chi_nkk, P->NK - kk0);
+    const int K = nkk * na * nb;
+    launch_pairs(P->NK, P->NBd, P->p.nk, q, kk0, nkk, P->nocc, na, 0, nb, P->p.eps,
+                 reinterpret_cast<const c128*>(P->p.pmom), P->p.qhat, P->d_delta, P->d_delta_f,
+                 hw ? P->d_pq : nullptr, st);
+    GW_CUDA(cudaEventRecord(P->ev0, st));
+    if (P->fp64) {
+      c128* M = static_cast<c128*>(P->d_M);
+      launch_mgen<double>(P->geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK,
+                          P->nocc, na, 0, nb, M, 1, P->ldm, st);
+      launch_chi0_simt<double>(N, K, M, P->ldm, nullptr, P->d_delta, P->d_freq, nw, scale, P->d_chi0, st);
+      if (hw)
+        launch_head_wings<double>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
+                                  4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
+    } else {
+      c64* M = static_cast<c64*>(P->d_M);
+      launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK,
+                         P->nocc, na, 0, nb, M, 1, P->ldm, st);
+      launch_chi0_simt<float>(N, K, M, P->ldm, P->d_delta_f, nullptr, P->d_freq, nw, scale, P->d_chi0, st);
+      if (hw)
+        launch_head_wings<float>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
+                                 4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
+    }
+    GW_CUDA(cudaEventRecord(P->ev1, st));
+    GW_TRY(check_launch(P, "gw_chi0"));
+    GW_CUDA(cudaEventSynchronize(P->ev1));
+    float ms = 0.f;
+    GW_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
+    total_ms += ms;
+  }
+  P->last_chi0_ms = total_ms;
+  P->last_chi0_flops = 8.0 * (double)P->NK * na * nb * ((double)N * (N + 1) / 2) * nw;
+  if (chi0_out)
+    GW_CUDA(cudaMemcpyAsync(chi0_out, P->d_chi0, sizeof(c128) * NN * nw, cudaMemcpyDeviceToDevice, st));
+  P->chi0_q = q;
+  P->wc_q = -1;
+  return GW_OK;
+}
+
+gw_status gw_screen(gw_plan P, int32_t sys, int32_t q, gw_complex* wc_out) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
+  if (P->chi0_q != q) return fail(GW_ERR_STATE, "gw_screen needs gw_chi0 for the same q first");
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw;
+  const long long NN = (long long)N * N;
+  const bool hw = P->p.head_wings && q == 0;
+  const c128* Vh = P->d_Vh + (long long)q * NN;
+  const c128* Vin = hw ? P->d_Vb0 : Vh;     // V^1/2 entering eps~ (body only at q = 0)
+  const c128 one{1, 0}, zero{0, 0}, mone{-1, 0};
+  // eps~ = 1 - Vin chi0 Vin
+  launch_zgemm<double>(N, N, N, one, P->d_chi0, N, NN, OP_N, Vin, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
+  launch_zgemm<double>(N, N, N, mone, Vin, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, P->d_E, N, NN, nw, st);
+  launch_axpby_identity<double>(N, P->d_E, NN, nw, 1.0, st);
+  if (hw) {
+    // Vbh[w] = Vb0 h[w]  (stored in d_tmp rows), then the rank-2 head / wing correction
+    launch_zgemm<double>(nw, N, N, one, P->d_h, N, 0, OP_N, P->d_Vb0, N, 0, OP_T, zero, P->d_tmp, N, 0, 1, st);
+    const double c = (P->p.spin / P->NK) * std::sqrt(4.0 * M_PI / P->p.omega_cell);
+    launch_q0_correction(N, nw, P->d_E, P->d_x1, P->d_tmp, P->d_head, c, st);
+  }
+  GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+  launch_chol_inv_minus_I(N, P->d_E, nw, NN, P->d_work, P->d_status, st);
+  // W^c = Vh (eps~^-1 - 1) Vh
+  launch_zgemm<double>(N, N, N, one, P->d_E, N, NN, OP_N, Vh, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
+  launch_zgemm<double>(N, N, N, one, Vh, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, P->d_Wc, N, NN, nw, st);
+  GW_TRY(check_launch(P, "gw_screen"));
+  GW_TRY(read_status(P, "gw_screen"));
+  if (wc_out) GW_CUDA(cudaMemcpyAsync(wc_out, P->d_Wc, sizeof(c128) * NN * nw, cudaMemcpyDeviceToDevice, st));
+  P->wc_q = q;
+  return GW_OK;
+}
+
+gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
+  if (P->wc_q != q) return fail(GW_ERR_STATE, "gw_sigma needs gw_screen for the same q first");
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw, NBd = P->NBd, nsig = P->nsig;
+  const long long NN = (long long)N * N;
+  const c128* evec = reinterpret_cast<const c128*>(P->p.evec);
+  c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
+  const double pref = -1.0 / (2.0 * M_PI * P->NK);
+  if (!P->fp64) launch_convert((int)(NN * nw), P->d_Wc, reinterpret_cast<c64*>(P->d_work), st);
+  for (int kk0 = 0; kk0 < P->NK; kk0 += P->sig_nkk) {
+    const int nkk = std::min(P->sig_nkk, P->NK - kk0);
+    const int R = nkk * nsig * NBd;
+    if (P->fp64) {
+      c128* A = static_cast<c128*>(P->d_A);
+      c128* U = static_cast<c128*>(P->d_U);
+      launch_mgen<double>(P->geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk,
+                          MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, N, 1, st);
+      for (int j = 0; j < nw; ++j) {
+        launch_zgemm<double>(R, N, N, c128{1, 0}, A, N, 0, OP_N, P->d_Wc + j * NN, N, 0, OP_N, c128{0, 0}, U, N, 0,
+                             1, st);
+        launch_rowdot<double>(R, N, U, A, N, nullptr, P->d_S_d, j, nw, st);
+      }
+    } else {
+      c64* A = static_cast<c64*>(P->d_A);
+      c64* U = static_cast<c64*>(P->d_U);
+      const c64* W32 = reinterpret_cast<const c64*>(P->d_work);
+      launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK_MINUS_Q,
+                         P->p.sigma_lo, nsig, 0, NBd, A, N, 1, st);
+      for (int j = 0; j < nw; ++j) {
+        launch_zgemm<float>(R, N, N, c64{1, 0}, A, N, 0, OP_N, W32 + j * NN, N, 0, OP_N, c64{0, 0}, U, N, 0, 1, st);
+        launch_rowdot<float>(R, N, U, A, N, P->d_S_f, nullptr, j, nw, st);
+      }
+    }
+    launch_sigma_conv_chunk(kk0, nkk, nsig, NBd, P->p.nk, q, P->p.eps, P->d_mu, P->d_S_f, P->d_S_d, P->d_freq,
+                            P->d_fw, nw, pref, sig, P->fp64, st);
+    GW_TRY(check_launch(P, "gw_sigma"));
+  }
+  return GW_OK;
+}
+
+gw_status gw_qp(gw_plan P, int32_t sys, const gw_complex* sigma, const double* dxv, double* e_qp, double* gap,
+                int32_t* n_conv) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (!e_qp || !gap) return fail(GW_ERR_ARG, "e_qp and gap must not be NULL");
+  cudaStream_t st = P->st;
+  const int n = P->NK * P->nsig;
+  double* d_e;
+  int* d_c;
+  GW_TRY(dalloc(P, &d_e, n));
+  GW_TRY(dalloc(P, &d_c, n));
+  const c128* sg = sigma ? reinterpret_cast<const c128*>(sigma) : P->d_sigma;
+  launch_qp(P->NK, P->nsig, P->NBd, P->p.sigma_lo, P->nw, sg, dxv, P->p.eps, P->d_mu, P->d_freq, d_e, d_c, st);
+  GW_TRY(check_launch(P, "gw_qp"));
+  std::vector<int> conv(n);
+  GW_CUDA(cudaMemcpyAsync(e_qp, d_e, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GW_CUDA(cudaMemcpyAsync(conv.data(), d_c, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+  GW_CUDA(cudaStreamSynchronize(st));
+  cudaFree(P->allocs.back());
+  P->allocs.pop_back();
+  cudaFree(P->allocs.back());
+  P->allocs.pop_back();
+  int nc = 0;
+  for (int i = 0; i < n; ++i) nc += conv[i];
+  if (n_conv) *n_conv = nc;
+  const int h = P->nocc - 1 - P->p.sigma_lo, l = P->nocc - P->p.sigma_lo;
+  if (h >= 0 && h < P->nsig && l >= 0 && l < P->nsig) {
+    double hmax = -1e300, lmin = 1e300;
+    for (int k = 0; k < P->NK; ++k) {
+      hmax = std::max(hmax, e_qp[k * P->nsig + h]);
+      lmin = std::min(lmin, e_qp[k * P->nsig + l]);
+    }
+    *gap = lmin - hmax;
+  } else {
+    *gap = std::nan("");
+  }
+  return GW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+// Internal declarations shared by the CUDA translation units of libgw.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/gw.h"
+
+namespace gw {
+
+// complex helpers (device and host)
+template <typename T> struct cplx { T re, im; };
+using c64 = cplx<float>;
+using c128 = cplx<double>;
+
+template <typename T> __host__ __device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T> __host__ __device__ __forceinline__ cplx<T> cmulc(cplx<T> a, cplx<T> b) {  // a * conj(b)
+  return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
+}
+template <typename T> __host__ __device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) {
+  return {a.re + b.re, a.im + b.im};
+}
+template <typename T> __host__ __device__ __forceinline__ cplx<T> cfma(cplx<T> a, cplx<T> b, cplx<T> c) {  // a*b + c
+  return {fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im))};
+}
+template <typename T> __host__ __device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return {a.re, -a.im}; }
+
+// device status word bits (written by kernels, read by the host after a call)
+enum : int {
+  ST_NOT_PD = 1,     // non-positive Cholesky pivot
+  ST_TIMEOUT = 2,    // a bounded wait gave up
+  ST_BADARG = 4,     // kernel-side bounds check tripped
+  ST_NOCONV = 8      // an iteration did not converge (informational)
+};
+
+// operand modes of the generic complex GEMM
+enum Op { OP_N = 0, OP_T = 1, OP_C = 2, OP_CONJ = 3 };   // as is, transpose, conj-transpose, conj only
+
+// ---- kernels (launch wrappers), grouped by translation unit ---------------------------------
+
+// k_lri.cu -- step (a)
+// T1_A[k][mu][i][b] = sum_R e^{2 pi i k.R} sum_j C~_A[R][mu][i][j] c[k][j][b]              (mu, i on A)
+// T2_A[k][mu][j][a] = sum_R e^{-2 pi i k.R} sum_i C~_A[R][mu][j][i] conj(c[k][i][a])      (mu, j on A)
+struct LriGeom {
+  int n_atoms, NK, NB, NBd, N, nR;
+  int nk[3];
+  int atom_b0[64], atom_nb[64], atom_x0[64], atom_nx[64];
+  long long ctil_off[64];      // element offset of atom block in ctil_R
+  long long t_off[64];         // element offset of atom block in T1/T2
+  int R[64][3];
+};
+template <typename T>
+void launch_lri_halfT(const LriGeom& g, const double* ctil, const c128* evec, cplx<T>* T1, cplx<T>* T2,
+                      cudaStream_t st);
+
+// M^mu_{ab}(k', q) for a in [a0, a0+na) at k'+q and b in [b0, b0+nb) at k', for the k' of each row block.
+// Row index r = ((kk * na) + a) * nb + b for kk in [0, nkk); k' = kmap(kk) (see MapMode).
+// out element (r, mu) at out[r * s_r + mu * s_mu].
+enum MapMode { MAP_K_IS_KK = 0, MAP_K_IS_KK_MINUS_Q = 1 };
+template <typename T>
+void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* T2, const c128* evec, int q,
+                 int kk0, int nkk, MapMode mode, int a0, int na, int b0, int nb, cplx<T>* out, long long s_r,
+                 long long s_mu, cudaStream_t st);
+// split planes for the tensor-core chi0 B operand: for row mu, K index 2r + {0: re, 1: im}
+void launch_mgen_planes(const LriGeom& g, const c64* T1, const c64* T2, const c128* evec, int q, int kk0,
+                        int nkk, int a0, int na, int b0, int nb, void* hi, void* lo, long long ldk,
+                        long long kofs, int tf32, cudaStream_t st);
+
+// k_linalg.cu
+template <typename T>
+void launch_zgemm(int m, int n, int k, cplx<T> alpha, const cplx<T>* A, long long lda, long long sA, Op opA,
+                  const cplx<T>* B, long long ldb, long long sB, Op opB, cplx<T> beta, cplx<T>* C,
+                  long long ldc, long long sC, int batch, cudaStream_t st);
+// chi0[w][mu][nu] += scale * sum_r w_w(D_r) Mt[mu][r] conj(Mt[nu][r]),  Mt row-major [N][ldm]
+template <typename T>
+void launch_chi0_simt(int N, int K, const cplx<T>* Mt, long long ldm, const float* delta_f, const double* delta_d,
+                      const double* freq, int nw, double scale, c128* chi0, cudaStream_t st);
+// per matrix b: A[b] (Hermitian PD, row-major N x N, FP64) -> A[b] := A[b]^{-1} - I. Sets ST_NOT_PD.
+void launch_chol_inv_minus_I(int N, c128* A, int batch, long long stride, c128* work, int* status,
+                             cudaStream_t st);
+template <typename T> void launch_axpby_identity(int N, cplx<T>* A, long long s, int batch, T diag, cudaStream_t st);
+void launch_convert(int n, const c128* in, c64* out, cudaStream_t st);
+void launch_convert_back(int n, const c64* in, c128* out, cudaStream_t st);
+// dominant eigenpair of a Hermitian matrix by power iteration (FP64)
+void launch_power_iter(int N, const c128* A, c128* x, double* lam, int iters, cudaStream_t st);
+// A += alpha * x x^H
+void launch_rank1(int N, c128* A, const c128* x, double alpha, cudaStream_t st);
+// q=0 head and wing vector: head[w], h[w][nu]
+template <typename T>
+void launch_head_wings(int N, int K, const cplx<T>* Mt, long long ldm, const double* delta, const c128* pq,
+                       const double* freq, int nw, double head_pref, double* head, c128* h, cudaStream_t st);
+// pair tables: delta[r] and (p.qhat)_{ia}(k) for r = ((kk*na)+a)*nb+b
+void launch_pairs(int NK, int NBd, const int* nk, int q, int kk0, int nkk, int a0, int na, int b0, int nb,
+                  const double* eps, const c128* pmom, const double* qhat, double* delta, float* delta_f,
+                  c128* pq, cudaStream_t st);
+// eps~(0) += (head - 1) x1 x1^H + x1 r + r^H x1^H, r = -c conj(Vb h)
+void launch_q0_correction(int N, int nw, c128* eps_t, const c128* x1, const c128* Vbh, const double* head,
+                          double c, cudaStream_t st);
+void launch_midgap(int NK, int NBd, int nocc, const double* eps, double* mu, cudaStream_t st);
+
+// k_sigma.cu
+// S[r][j] = Re sum_nu U[r][nu] conj(a[r][nu])
+template <typename T>
+void launch_rowdot(int R, int N, const cplx<T>* U, const cplx<T>* a, long long ld, float* S_f, double* S_d, int j,
+                   int nw, cudaStream_t st);
+// sigma[k][n][w] += pref * sum_m sum_j g_j S[(kk,n,m)][j] 2z/(z^2+w_j^2), z = i w + mu - eps_m(k-q),
+// for the target k = kk0 + kk of one chunk of rows r = ((kk*nsig)+n)*NBd + m.
+void launch_sigma_conv_chunk(int kk0, int nkk, int nsig, int NBd, const int* nk, int q, const double* eps,
+                             const double* mu, const float* S_f, const double* S_d, const double* freq,
+                             const double* gw, int nw, double pref, c128* sigma, bool fp64, cudaStream_t st);
+void launch_qp(int NK, int nsig, int NBd, int sig_lo, int nw, const c128* sigma, const double* dxv,
+               const double* eps, const double* mu, const double* freq, double* e_qp, int* conv,
+               cudaStream_t st);
+
+// k_tc.cu -- tcgen05 split-precision kernels
+struct TcChi0Args {
+  int N;            // n_aux
+  int Kpad;         // padded number of pair rows (multiple of the K chunk)
+  int K;            // valid rows
+  const void* Bhi;  // planes [N][2*Kpad] (bf16 or fp32)
+  const void* Blo;
+  const float* delta;   // [Kpad] transition energies (0 for padding)
+  const double* freq;   // [nw]
+  int nw;
+  double scale;     // -(s / N_k)
+  c128* chi0;       // [nw][N][N]
+  int tf32;
+  int* status;
+  int seg_rows;     // rows per TMEM accumulation segment
+};
+gw_status tc_chi0_run(const TcChi0Args& a, cudaStream_t st, std::string& err);
+bool tc_available();
+
+}  // namespace gw

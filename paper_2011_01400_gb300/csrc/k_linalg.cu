@@ -1,0 +1,529 @@
+// CUDA-core linear algebra of the G0W0 path: the generic complex GEMM used by the
+// FP64 method and by the V^1/2 Newton-Schulz iteration, the FP64 chi0 contraction,
+// the FP64 Cholesky factorisation + inversion of eps~, and the q = 0 helpers.
+#include "gw_internal.h"
+
+namespace gw {
+
+// ---------------------------------------------------------------------------------------------
+// Generic batched complex GEMM, C = alpha op(A) op(B) + beta C. 64x64 tile, 256 threads,
+// 4x4 outputs per thread, K chunk 8.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ cplx<T> load_op(const cplx<T>* X, long long ld, int r, int c, int op) {
+  // element (r, c) of op(X)
+  cplx<T> v = (op == OP_N || op == OP_CONJ) ? X[(long long)r * ld + c] : X[(long long)c * ld + r];
+  if (op == OP_C || op == OP_CONJ) v.im = -v.im;
+  return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_zgemm(int m, int n, int k, cplx<T> alpha, const cplx<T>* __restrict__ A,
+                                               long long lda, long long sA, int opA, const cplx<T>* __restrict__ B,
+                                               long long ldb, long long sB, int opB, cplx<T> beta,
+                                               cplx<T>* __restrict__ C, long long ldc, long long sC) {
+  __shared__ cplx<T> As[8][64 + 1];
+  __shared__ cplx<T> Bs[8][64 + 1];
+  const int bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  cplx<T> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = {0, 0};
+  for (int k0 = 0; k0 < k; k0 += 8) {
+    for (int e = threadIdx.x; e < 8 * 64; e += 256) {
+      int kk = e % 8, mm = e / 8;
+      int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < m && gk < k) ? load_op(A, lda, gm, gk, opA) : cplx<T>{0, 0};
+      int nn = e % 64, kb = e / 64;
+      int gn = n0 + nn, gk2 = k0 + kb;
+      Bs[kb][nn] = (gn < n && gk2 < k) ? load_op(B, ldb, gk2, gn, opB) : cplx<T>{0, 0};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      cplx<T> a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < m && gn < n) {
+        cplx<T>* c = C + (long long)gm * ldc + gn;
+        cplx<T> v = cmul(alpha, acc[i][j]);
+        if (beta.re != (T)0 || beta.im != (T)0) v = cfma(beta, *c, v);
+        *c = v;
+      }
+    }
+}
+
+template <typename T>
+void launch_zgemm(int m, int n, int k, cplx<T> alpha, const cplx<T>* A, long long lda, long long sA, Op opA,
+                  const cplx<T>* B, long long ldb, long long sB, Op opB, cplx<T> beta, cplx<T>* C, long long ldc,
+                  long long sC, int batch, cudaStream_t st) {
+  dim3 grid((n + 63) / 64, (m + 63) / 64, batch);
+  k_zgemm<T><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, (int)opA, B, ldb, sB, (int)opB, beta, C, ldc, sC);
+}
+template void launch_zgemm<double>(int, int, int, c128, const c128*, long long, long long, Op, const c128*,
+                                   long long, long long, Op, c128, c128*, long long, long long, int, cudaStream_t);
+template void launch_zgemm<float>(int, int, int, c64, const c64*, long long, long long, Op, const c64*, long long,
+                                  long long, Op, c64, c64*, long long, long long, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------------
+// chi0 on CUDA cores (the FP64 method): Hermitian weighted rank-K update, lower tiles only,
+// one block per (lower 32x32 tile, frequency).
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_chi0_simt(int N, int K, const cplx<T>* __restrict__ Mt, long long ldm,
+                                                   const float* __restrict__ delta_f,
+                                                   const double* __restrict__ delta_d,
+                                                   const double* __restrict__ freq, double scale,
+                                                   c128* __restrict__ chi0) {
+  __shared__ cplx<T> As[16][33];
+  __shared__ cplx<T> Bs[16][33];
+  // lower-tile index -> (ti, tj), ti >= tj
+  int t = blockIdx.x;
+  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  while (ti * (ti + 1) / 2 > t) --ti;
+  int tj = t - ti * (ti + 1) / 2;
+  const int w_i = blockIdx.y;
+  const T om = (T)freq[w_i];
+  const int mu0 = ti * 32, nu0 = tj * 32;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  cplx<T> acc[2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+      int kk = e % 16, mm = e / 16;
+      int gk = k0 + kk;
+      cplx<T> a = {0, 0}, b = {0, 0};
+      if (gk < K) {
+        T d = delta_d ? (T)delta_d[gk] : (T)delta_f[gk];
+        T w = (T)2 * d / (om * om + d * d);
+        if (mu0 + mm < N) {
+          a = Mt[(long long)(mu0 + mm) * ldm + gk];
+          a.re *= w;
+          a.im *= w;
+        }
+        if (nu0 + mm < N) b = Mt[(long long)(nu0 + mm) * ldm + gk];
+      }
+      As[kk][mm] = a;
+      Bs[kk][mm] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      cplx<T> a0 = As[kk][ty], a1 = As[kk][ty + 16];
+      cplx<T> b0 = Bs[kk][tx], b1 = Bs[kk][tx + 16];
+      // a * conj(b)
+      acc[0][0] = cadd(acc[0][0], cmulc(a0, b0));
+      acc[0][1] = cadd(acc[0][1], cmulc(a0, b1));
+      acc[1][0] = cadd(acc[1][0], cmulc(a1, b0));
+      acc[1][1] = cadd(acc[1][1], cmulc(a1, b1));
+    }
+    __syncthreads();
+  }
+  c128* out = chi0 + (long long)w_i * N * N;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      int mu = mu0 + ty + 16 * i, nu = nu0 + tx + 16 * j;
+      if (mu < N && nu < N && (ti != tj || mu >= nu)) {
+        double re = scale * (double)acc[i][j].re, im = scale * (double)acc[i][j].im;
+        c128* p = out + (long long)mu * N + nu;
+        p->re += re;
+        p->im += im;
+        if (mu != nu) {
+          c128* q = out + (long long)nu * N + mu;
+          q->re += re;
+          q->im -= im;
+        }
+      }
+    }
+}
+
+template <typename T>
+void launch_chi0_simt(int N, int K, const cplx<T>* Mt, long long ldm, const float* delta_f, const double* delta_d,
+                      const double* freq, int nw, double scale, c128* chi0, cudaStream_t st) {
+  int nt = (N + 31) / 32;
+  dim3 grid(nt * (nt + 1) / 2, nw);
+  k_chi0_simt<T><<<grid, 256, 0, st>>>(N, K, Mt, ldm, delta_f, delta_d, freq, scale, chi0);
+}
+template void launch_chi0_simt<double>(int, int, const c128*, long long, const float*, const double*, const double*,
+                                       int, double, c128*, cudaStream_t);
+template void launch_chi0_simt<float>(int, int, const c64*, long long, const float*, const double*, const double*,
+                                      int, double, c128*, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------------
+// FP64 Cholesky factorisation and inversion of eps~ (Hermitian positive definite), one block
+// per matrix: eps~ = U^H U (up-looking, in place in the upper triangle), U^{-1} by backward
+// substitution (work buffer), then A := U^{-1} U^{-H} - I.
+// ---------------------------------------------------------------------------------------------
+constexpr int CHOL_THREADS = 512;
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < blockDim.x / 32) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[0] = s;
+  }
+  __syncthreads();
+  s = red[0];
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol_inv(int N, c128* __restrict__ Aall, long long stride,
+                                                           c128* __restrict__ Wall, int* __restrict__ status) {
+  extern __shared__ c128 col[];      // [N]
+  __shared__ double red[32];
+  __shared__ double s_piv;
+  c128* A = Aall + blockIdx.x * stride;
+  c128* W = Wall + blockIdx.x * stride;
+  // 1) eps~ = U^H U: U[j][i] = (A[j][i] - sum_{k<j} conj(U[k][j]) U[k][i]) / U[j][j]
+  for (int j = 0; j < N; ++j) {
+    for (int k = threadIdx.x; k < j; k += blockDim.x) col[k] = A[(long long)k * N + j];
+    __syncthreads();
+    double part = 0;
+    for (int k = threadIdx.x; k < j; k += blockDim.x) part += col[k].re * col[k].re + col[k].im * col[k].im;
+    double s = block_sum(part, red);
+    if (threadIdx.x == 0) {
+      double piv = A[(long long)j * N + j].re - s;
+      if (!(piv > 0.0)) {
+        atomicOr(status, ST_NOT_PD);
+        piv = 1.0;
+      }
+      s_piv = sqrt(piv);
+      A[(long long)j * N + j] = c128{s_piv, 0.0};
+    }
+    __syncthreads();
+    const double inv = 1.0 / s_piv;
+    for (int i = j + 1 + threadIdx.x; i < N; i += blockDim.x) {
+      double sr = A[(long long)j * N + i].re, si = A[(long long)j * N + i].im;
+      for (int k = 0; k < j; ++k) {
+        c128 u = A[(long long)k * N + i];
+        c128 c = col[k];  // U[k][j]; subtract conj(c) * u
+        sr -= c.re * u.re + c.im * u.im;
+        si -= c.re * u.im - c.im * u.re;
+      }
+      A[(long long)j * N + i] = c128{sr * inv, si * inv};
+    }
+    __syncthreads();
+  }
+  // 2) W = U^{-1} (upper), rows from the bottom:
+  //    W[i][i] = 1/U[i][i];  W[i][l] = -(1/U[i][i]) sum_{k=i+1}^{l} U[i][k] W[k][l]
+  for (int e = threadIdx.x; e < N * N; e += blockDim.x) W[e] = c128{0.0, 0.0};
+  __syncthreads();
+  for (int i = N - 1; i >= 0; --i) {
+    for (int k = i + threadIdx.x; k < N; k += blockDim.x) col[k] = A[(long long)i * N + k];
+    __syncthreads();
+    const double dinv = 1.0 / col[i].re;
+    for (int l = i + threadIdx.x; l < N; l += blockDim.x) {
+      if (l == i) {
+        W[(long long)i * N + i] = c128{dinv, 0.0};
+      } else {
+        double sr = 0, si = 0;
+        for (int k = i + 1; k <= l; ++k) {
+          c128 u = col[k], w = W[(long long)k * N + l];
+          sr += u.re * w.re - u.im * w.im;
+          si += u.re * w.im + u.im * w.re;
+        }
+        W[(long long)i * N + l] = c128{-sr * dinv, -si * dinv};
+      }
+    }
+    __syncthreads();
+  }
+  // 3) A = W W^H - I: A[i][l] = sum_{k >= max(i,l)} W[i][k] conj(W[l][k]); lower tiles, mirrored
+  const int TT = 16;
+  __shared__ c128 Ti[16][17], Tl[16][17];
+  const int nt = (N + TT - 1) / TT;
+  for (int ti = 0; ti < nt; ++ti) {
+    for (int tl = 0; tl <= ti; ++tl) {
+      // 512 threads: 256 outputs, two k-halves
+      const int o = threadIdx.x % 256, half = threadIdx.x / 256;
+      const int ii = ti * TT + o / TT, ll = tl * TT + o % TT;
+      double sr = 0, si = 0;
+      for (int k0 = ti * TT; k0 < N; k0 += TT) {
+        for (int e = threadIdx.x; e < 2 * TT * TT; e += blockDim.x) {
+          int which = e / (TT * TT), r = (e % (TT * TT)) / TT, c = e % TT;
+          int row = (which == 0 ? ti : tl) * TT + r, kk = k0 + c;
+          c128 v = (row < N && kk < N) ? W[(long long)row * N + kk] : c128{0.0, 0.0};
+          if (which == 0) Ti[r][c] = v; else Tl[r][c] = v;
+        }
+        __syncthreads();
+        for (int c = half; c < TT; c += 2) {
+          c128 a = Ti[o / TT][c], b = Tl[o % TT][c];
+          sr += a.re * b.re + a.im * b.im;
+          si += a.im * b.re - a.re * b.im;
+        }
+        __syncthreads();
+      }
+      // combine the two halves through shared memory
+      __shared__ double part_re[256], part_im[256];
+      if (half == 1) { part_re[o] = sr; part_im[o] = si; }
+      __syncthreads();
+      if (half == 0 && ii < N && ll < N && ii >= ll) {
+        sr += part_re[o];
+        si += part_im[o];
+        if (ii == ll) { sr -= 1.0; si = 0.0; }
+        A[(long long)ii * N + ll] = c128{sr, si};
+        if (ii != ll) A[(long long)ll * N + ii] = c128{sr, -si};
+      }
+      __syncthreads();
+    }
+  }
+}
+
+void launch_chol_inv_minus_I(int N, c128* A, int batch, long long stride, c128* work, int* status, cudaStream_t st) {
+  size_t smem = sizeof(c128) * (size_t)N;
+  k_chol_inv<<<batch, CHOL_THREADS, smem, st>>>(N, A, stride, work, status);
+}
+
+// ---------------------------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_axpby_identity(int N, cplx<T>* A, long long s, T diag) {
+  cplx<T>* a = A + blockIdx.y * s;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
+    a[(long long)i * N + i].re += diag;
+}
+template <typename T> void launch_axpby_identity(int N, cplx<T>* A, long long s, int batch, T diag, cudaStream_t st) {
+  dim3 grid((N + 255) / 256, batch);
+  k_axpby_identity<T><<<grid, 256, 0, st>>>(N, A, s, diag);
+}
+template void launch_axpby_identity<double>(int, c128*, long long, int, double, cudaStream_t);
+template void launch_axpby_identity<float>(int, c64*, long long, int, float, cudaStream_t);
+
+__global__ void k_convert(int n, const c128* in, c64* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = c64{(float)in[i].re, (float)in[i].im};
+}
+__global__ void k_convert_back(int n, const c64* in, c128* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = c128{(double)in[i].re, (double)in[i].im};
+}
+void launch_convert(int n, const c128* in, c64* out, cudaStream_t st) {
+  k_convert<<<std::min((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, in, out);
+}
+void launch_convert_back(int n, const c64* in, c128* out, cudaStream_t st) {
+  k_convert_back<<<std::min((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, in, out);
+}
+
+// Dominant eigenpair by power iteration with a Rayleigh quotient (one block, FP64).
+__global__ void k_power_iter(int N, const c128* __restrict__ A, c128* __restrict__ x, double* lam, int iters) {
+  extern __shared__ c128 v[];   // [2N]
+  __shared__ double red[32];
+  c128* y = v + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) v[i] = c128{1.0 + 0.001 * (i % 7), 0.0};
+  __syncthreads();
+  double rq = 0;
+  for (int it = 0; it < iters; ++it) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      double sr = 0, si = 0;
+      for (int j = 0; j < N; ++j) {
+        c128 a = A[(long long)i * N + j], b = v[j];
+        sr += a.re * b.re - a.im * b.im;
+        si += a.re * b.im + a.im * b.re;
+      }
+      y[i] = c128{sr, si};
+    }
+    __syncthreads();
+    double p = 0, d = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      p += y[i].re * y[i].re + y[i].im * y[i].im;
+      d += v[i].re * y[i].re + v[i].im * y[i].im;   // Re v^H y
+    }
+    double nrm2 = block_sum(p, red);
+    rq = block_sum(d, red);
+    double inv = 1.0 / sqrt(nrm2);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) v[i] = c128{y[i].re * inv, y[i].im * inv};
+    __syncthreads();
+  }
+  // fix the phase: largest-magnitude component real positive
+  if (threadIdx.x == 0) {
+    int imax = 0;
+    double best = -1;
+    for (int i = 0; i < N; ++i) {
+      double m = v[i].re * v[i].re + v[i].im * v[i].im;
+      if (m > best) { best = m; imax = i; }
+    }
+    double m = sqrt(best);
+    red[0] = v[imax].re / m;
+    red[1] = -v[imax].im / m;
+    *lam = rq;
+  }
+  __syncthreads();
+  c128 ph = c128{red[0], red[1]};
+  for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = cmul(v[i], ph);
+}
+void launch_power_iter(int N, const c128* A, c128* x, double* lam, int iters, cudaStream_t st) {
+  k_power_iter<<<1, 512, 2 * N * sizeof(c128), st>>>(N, A, x, lam, iters);
+}
+
+__global__ void k_rank1(int N, c128* A, const c128* x, double alpha) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)N * N;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / N), j = (int)(e % N);
+    c128 v = cmulc(x[i], x[j]);
+    A[e].re += alpha * v.re;
+    A[e].im += alpha * v.im;
+  }
+}
+void launch_rank1(int N, c128* A, const c128* x, double alpha, cudaStream_t st) {
+  k_rank1<<<std::min((N * N + 255) / 256, 152 * 16), 256, 0, st>>>(N, A, x, alpha);
+}
+
+// head[w] += pref * sum_r |pq_r|^2 2 / (D (D^2 + w^2));  h[w][nu] += sum_r conj(pq_r) Mt[nu][r] 2/(w^2 + D^2)
+template <typename T>
+__global__ void k_head_wings(int N, int K, const cplx<T>* __restrict__ Mt, long long ldm,
+                             const double* __restrict__ delta, const c128* __restrict__ pq,
+                             const double* __restrict__ freq, double head_pref, double* head, c128* h) {
+  __shared__ double red[32];
+  const int nu = blockIdx.x, w_i = blockIdx.y;
+  const double om = freq[w_i];
+  if (nu == N) {  // one extra block row computes the head
+    double part = 0;
+    for (int r = threadIdx.x; r < K; r += blockDim.x) {
+      double d = delta[r];
+      c128 p = pq[r];
+      part += (p.re * p.re + p.im * p.im) * 2.0 / (d * (d * d + om * om));
+    }
+    double s = block_sum(part, red);
+    if (threadIdx.x == 0) head[w_i] += head_pref * s;
+    return;
+  }
+  double sr = 0, si = 0;
+  for (int r = threadIdx.x; r < K; r += blockDim.x) {
+    double d = delta[r];
+    double wt = 2.0 / (om * om + d * d);
+    c128 p = pq[r];
+    cplx<T> m = Mt[(long long)nu * ldm + r];
+    // conj(p) * m
+    sr += wt * (p.re * (double)m.re + p.im * (double)m.im);
+    si += wt * (p.re * (double)m.im - p.im * (double)m.re);
+  }
+  double a = block_sum(sr, red);
+  double b = block_sum(si, red);
+  if (threadIdx.x == 0) {
+    h[(long long)w_i * N + nu].re += a;
+    h[(long long)w_i * N + nu].im += b;
+  }
+}
+template <typename T>
+void launch_head_wings(int N, int K, const cplx<T>* Mt, long long ldm, const double* delta, const c128* pq,
+                       const double* freq, int nw, double head_pref, double* head, c128* h, cudaStream_t st) {
+  dim3 grid(N + 1, nw);
+  k_head_wings<T><<<grid, 256, 0, st>>>(N, K, Mt, ldm, delta, pq, freq, head_pref, head, h);
+}
+template void launch_head_wings<double>(int, int, const c128*, long long, const double*, const c128*, const double*,
+                                        int, double, double*, c128*, cudaStream_t);
+template void launch_head_wings<float>(int, int, const c64*, long long, const double*, const c128*, const double*, int,
+                                       double, double*, c128*, cudaStream_t);
+
+// Pair tables for rows r = ((kk*na)+a)*nb+b (a at k+q, b at k, k = kk0+kk):
+// delta[r] = eps_a(k+q) - eps_b(k); pq[r] = (p(k) . qhat)_{b a} (used at q = 0 only).
+__global__ void k_pairs(int NBd, int n1, int n2, int n3, int q, int kk0, int nkk, int a0, int na, int b0, int nb,
+                        const double* __restrict__ eps, const c128* __restrict__ pmom, double qx, double qy,
+                        double qz, double* delta, float* delta_f, c128* pq) {
+  const long long total = (long long)nkk * na * nb;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < total;
+       r += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(r % nb), a = (int)((r / nb) % na), kk = (int)(r / ((long long)na * nb));
+    int k = kk0 + kk;
+    int k3 = k % n3, k2 = (k / n3) % n2, k1 = k / (n2 * n3);
+    int q3 = q % n3, q2 = (q / n3) % n2, q1 = q / (n2 * n3);
+    int kq = (((k1 + q1) % n1) * n2 + ((k2 + q2) % n2)) * n3 + ((k3 + q3) % n3);
+    double d = eps[(long long)kq * NBd + a0 + a] - eps[(long long)k * NBd + b0 + b];
+    if (delta) delta[r] = d;
+    if (delta_f) delta_f[r] = (float)d;
+    if (pq) {
+      c128 s = {0, 0};
+      const double qh[3] = {qx, qy, qz};
+      for (int x = 0; x < 3; ++x) {
+        c128 p = pmom[(((long long)k * 3 + x) * NBd + (b0 + b)) * NBd + (a0 + a)];
+        s.re += qh[x] * p.re;
+        s.im += qh[x] * p.im;
+      }
+      pq[r] = s;
+    }
+  }
+}
+void launch_pairs(int NK, int NBd, const int* nk, int q, int kk0, int nkk, int a0, int na, int b0, int nb,
+                  const double* eps, const c128* pmom, const double* qhat, double* delta, float* delta_f, c128* pq,
+                  cudaStream_t st) {
+  long long total = (long long)nkk * na * nb;
+  int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);
+  k_pairs<<<blocks, 256, 0, st>>>(NBd, nk[0], nk[1], nk[2], q, kk0, nkk, a0, na, b0, nb, eps, pmom,
+                                  qhat ? qhat[0] : 0, qhat ? qhat[1] : 0, qhat ? qhat[2] : 0, delta, delta_f, pq);
+}
+
+// eps~(0)[w] += (head_w - 1) x1 x1^H + x1 r_w + r_w^H x1^H,  r_w[nu] = -c conj(Vbh[w][nu])
+__global__ void k_q0_correction(int N, c128* eps_t, const c128* __restrict__ x1, const c128* __restrict__ Vbh,
+                                const double* __restrict__ head, double c) {
+  const int w_i = blockIdx.y;
+  const double hm1 = head[w_i] - 1.0;
+  c128* E = eps_t + (long long)w_i * N * N;
+  const c128* v = Vbh + (long long)w_i * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)N * N;
+       e += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(e / N), j = (int)(e % N);
+    c128 xx = cmulc(x1[i], x1[j]);                  // x1_i conj(x1_j)
+    c128 rj = c128{-c * v[j].re, c * v[j].im};      // r_j = -c conj(v_j)
+    c128 ri = c128{-c * v[i].re, c * v[i].im};
+    c128 t1 = cmul(x1[i], rj);                      // x1_i r_j
+    c128 t2 = cmulc(cconj(ri), x1[j]);              // conj(r_i) conj(x1_j)
+    E[e].re += hm1 * xx.re + t1.re + t2.re;
+    E[e].im += hm1 * xx.im + t1.im + t2.im;
+  }
+}
+void launch_q0_correction(int N, int nw, c128* eps_t, const c128* x1, const c128* Vbh, const double* head, double c,
+                          cudaStream_t st) {
+  dim3 grid(std::min((N * N + 255) / 256, 256), nw);
+  k_q0_correction<<<grid, 256, 0, st>>>(N, eps_t, x1, Vbh, head, c);
+}
+
+__global__ void k_midgap(int NK, int NBd, int nocc, const double* eps, double* mu) {
+  __shared__ double hmax[256], lmin[256];
+  double h = -1e300, l = 1e300;
+  for (int k = threadIdx.x; k < NK; k += blockDim.x) {
+    h = fmax(h, eps[(long long)k * NBd + nocc - 1]);
+    l = fmin(l, eps[(long long)k * NBd + nocc]);
+  }
+  hmax[threadIdx.x] = h;
+  lmin[threadIdx.x] = l;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      hmax[threadIdx.x] = fmax(hmax[threadIdx.x], hmax[threadIdx.x + s]);
+      lmin[threadIdx.x] = fmin(lmin[threadIdx.x], lmin[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *mu = 0.5 * (hmax[0] + lmin[0]);
+}
+void launch_midgap(int NK, int NBd, int nocc, const double* eps, double* mu, cudaStream_t st) {
+  k_midgap<<<1, 256, 0, st>>>(NK, NBd, nocc, eps, mu);
+}
+
+}  // namespace gw

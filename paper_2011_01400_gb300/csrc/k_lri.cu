@@ -1,0 +1,196 @@
+// Step (a): LRI triple coefficients -> band-pair coefficients M^mu_{ab}(k, q).
+//
+// Eq. (AO_triple_split2): C~^mu_{ij}(k+q,k) = C~^{mu(0)}_{j(0),i(-k-q)} + C~^{mu(0)}_{i(0),j(k)},
+// with C~_{i(0),j(R)}^{mu(0)} nonzero only for mu on the atom of i, and the
+// Fourier sums of Eqs. (expan_coeff_FT1/2). Inserting this into Eq. (AO_MO_transform)
+// and contracting the NAO index that is not on mu's atom first gives the
+// half-transformed coefficients (computed once per k at plan time)
+//     T1^mu_{ib}(k) = sum_R e^{i k.R} sum_j C~^{mu(0)}_{i(0),j(R)} c_{jb}(k),   i on atom(mu)
+// and, because the stored C~(R) are real (real NAOs and ABFs), the second
+// sector's transform is conj(T1). Then per (k, q):
+//     M^mu_{ab}(k,q) = sum_{j in A(mu)} c_{jb}(k) conj(T1^mu_{ja}(k+q))
+//                    + sum_{i in A(mu)} conj(c_{ia}(k+q)) T1^mu_{ib}(k),
+// which is Eq. (AO_MO_transform) exactly, with n_b(A) instead of N_b terms per sum.
+#include "gw_internal.h"
+#include <cuda_bf16.h>
+
+namespace gw {
+
+__constant__ LriGeom c_geom;
+
+template <typename T>
+__global__ void k_lri_halfT(const double* __restrict__ ctil, const c128* __restrict__ evec, cplx<T>* __restrict__ T1,
+                            int A) {
+  const LriGeom& g = c_geom;
+  const int nb_A = g.atom_nb[A], nx_A = g.atom_nx[A];
+  const long long total = (long long)g.NK * nx_A * nb_A * g.NBd;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int b = (int)(idx % g.NBd);
+    long long t = idx / g.NBd;
+    int i = (int)(t % nb_A);
+    t /= nb_A;
+    int mu = (int)(t % nx_A);
+    int k = (int)(t / nx_A);
+    int k3 = k % g.nk[2], k2 = (k / g.nk[2]) % g.nk[1], k1 = k / (g.nk[1] * g.nk[2]);
+    double acc_re = 0.0, acc_im = 0.0;
+    const c128* ck = evec + (long long)k * g.NB * g.NBd;
+    for (int r = 0; r < g.nR; ++r) {
+      // phase e^{2 pi i k.R}, k in fractional coordinates
+      double ph = 2.0 * ((double)k1 * g.R[r][0] / g.nk[0] + (double)k2 * g.R[r][1] / g.nk[1] +
+                         (double)k3 * g.R[r][2] / g.nk[2]);
+      double s, c;
+      sincospi(ph, &s, &c);
+      const double* crow = ctil + g.ctil_off[A] + (((long long)r * nx_A + mu) * nb_A + i) * g.NB;
+      double sr = 0.0, si = 0.0;
+      for (int j = 0; j < g.NB; ++j) {
+        c128 cj = ck[(long long)j * g.NBd + b];
+        sr = fma(crow[j], cj.re, sr);
+        si = fma(crow[j], cj.im, si);
+      }
+      acc_re += c * sr - s * si;
+      acc_im += c * si + s * sr;
+    }
+    T1[g.t_off[A] + idx] = cplx<T>{(T)acc_re, (T)acc_im};
+  }
+}
+
+template <typename T>
+void launch_lri_halfT(const LriGeom& g, const double* ctil, const c128* evec, cplx<T>* T1, cplx<T>* /*T2*/,
+                      cudaStream_t st) {
+  cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
+  for (int A = 0; A < g.n_atoms; ++A) {
+    long long total = (long long)g.NK * g.atom_nx[A] * g.atom_nb[A] * g.NBd;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
+    k_lri_halfT<T><<<blocks, 256, 0, st>>>(ctil, evec, T1, A);
+  }
+}
+template void launch_lri_halfT<double>(const LriGeom&, const double*, const c128*, c128*, c128*, cudaStream_t);
+template void launch_lri_halfT<float>(const LriGeom&, const double*, const c128*, c64*, c64*, cudaStream_t);
+
+// ---------------------------------------------------------------------------------------------
+// M generation. One block per (row-k kk, block of MU ABFs); threads over (a, b) pairs.
+// ---------------------------------------------------------------------------------------------
+constexpr int MGEN_MU = 8;
+
+__device__ __forceinline__ int aux_atom_of(const LriGeom& g, int mu) {
+  int A = 0;
+  while (A + 1 < g.n_atoms && mu >= g.atom_x0[A + 1]) ++A;
+  return A;
+}
+
+template <typename T, typename Store>
+__device__ __forceinline__ void mgen_body(const cplx<T>* __restrict__ T1, const c128* __restrict__ evec, int q,
+                                          int kk0, int mode, int a0, int na, int b0, int nb, Store store) {
+  const LriGeom& g = c_geom;
+  const int kk = blockIdx.x;
+  int ktgt = kk0 + kk;
+  int k3 = ktgt % g.nk[2], k2 = (ktgt / g.nk[2]) % g.nk[1], k1 = ktgt / (g.nk[1] * g.nk[2]);
+  int q3 = q % g.nk[2], q2 = (q / g.nk[2]) % g.nk[1], q1 = q / (g.nk[1] * g.nk[2]);
+  int kp;  // k' (b bands live here), k'+q (a bands live here)
+  if (mode == MAP_K_IS_KK) {
+    kp = ktgt;
+  } else {
+    kp = (((k1 - q1 + g.nk[0]) % g.nk[0]) * g.nk[1] + ((k2 - q2 + g.nk[1]) % g.nk[1])) * g.nk[2] +
+         ((k3 - q3 + g.nk[2]) % g.nk[2]);
+  }
+  int p3 = kp % g.nk[2], p2 = (kp / g.nk[2]) % g.nk[1], p1 = kp / (g.nk[1] * g.nk[2]);
+  int kpq = (((p1 + q1) % g.nk[0]) * g.nk[1] + ((p2 + q2) % g.nk[1])) * g.nk[2] + ((p3 + q3) % g.nk[2]);
+  const c128* ck = evec + (long long)kp * g.NB * g.NBd;    // c(k')
+  const c128* ckq = evec + (long long)kpq * g.NB * g.NBd;  // c(k'+q)
+  const int mu_begin = blockIdx.y * MGEN_MU;
+  const int mu_end = min(mu_begin + MGEN_MU, g.N);
+  const int npair = na * nb;
+  for (int mu = mu_begin; mu < mu_end; ++mu) {
+    const int A = aux_atom_of(g, mu);
+    const int nbA = g.atom_nb[A], b0A = g.atom_b0[A];
+    const int mul = mu - g.atom_x0[A];
+    const cplx<T>* t1k = T1 + g.t_off[A] + (((long long)kp * g.atom_nx[A] + mul) * nbA) * g.NBd;
+    const cplx<T>* t1kq = T1 + g.t_off[A] + (((long long)kpq * g.atom_nx[A] + mul) * nbA) * g.NBd;
+    for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+      const int a = a0 + p / nb, b = b0 + p % nb;
+      T sr = 0, si = 0;
+      for (int j = 0; j < nbA; ++j) {
+        // c_{jb}(k') conj(T1^mu_{ja}(k'+q))
+        c128 cjb = ck[(long long)(b0A + j) * g.NBd + b];
+        cplx<T> t = t1kq[(long long)j * g.NBd + a];
+        T cr = (T)cjb.re, ci = (T)cjb.im;
+        sr += cr * t.re + ci * t.im;
+        si += ci * t.re - cr * t.im;
+        // conj(c_{ja}(k'+q)) T1^mu_{jb}(k')
+        c128 cja = ckq[(long long)(b0A + j) * g.NBd + a];
+        cplx<T> u = t1k[(long long)j * g.NBd + b];
+        T dr = (T)cja.re, di = (T)cja.im;
+        sr += dr * u.re + di * u.im;
+        si += dr * u.im - di * u.re;
+      }
+      long long r = ((long long)kk * na + (p / nb)) * nb + (p % nb);
+      store(r, mu, sr, si);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_mgen(const cplx<T>* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int mode,
+                       int a0, int na, int b0, int nb, cplx<T>* __restrict__ out, long long s_r, long long s_mu) {
+  mgen_body<T>(T1, evec, q, kk0, mode, a0, na, b0, nb, [&](long long r, int mu, T re, T im) {
+    out[r * s_r + (long long)mu * s_mu] = cplx<T>{re, im};
+  });
+}
+
+template <typename T>
+void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* /*T2*/, const c128* evec, int q, int kk0,
+                 int nkk, MapMode mode, int a0, int na, int b0, int nb, cplx<T>* out, long long s_r, long long s_mu,
+                 cudaStream_t st) {
+  cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
+  dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
+  k_mgen<T><<<grid, 256, 0, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r, s_mu);
+}
+template void launch_mgen<double>(const LriGeom&, const c128*, const c128*, const c128*, int, int, int, MapMode, int,
+                                  int, int, int, c128*, long long, long long, cudaStream_t);
+template void launch_mgen<float>(const LriGeom&, const c64*, const c64*, const c128*, int, int, int, MapMode, int,
+                                 int, int, int, c64*, long long, long long, cudaStream_t);
+
+// Split planes for the tensor-core chi0 operand: row mu, K index kofs + 2r + {re, im}.
+// BF16: hi = bf16(x), lo = bf16(x - hi). TF32: hi = x rounded to 10 explicit mantissa bits
+// (stored as fp32 with the low 13 bits zero), lo = x - hi in fp32.
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;          // inf / nan unchanged
+  u += 0x1000u;                                             // round half away on the 13 dropped bits
+  u &= 0xffffe000u;
+  return __uint_as_float(u);
+}
+
+__global__ void k_mgen_planes(const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int a0,
+                              int na, int b0, int nb, void* __restrict__ hi, void* __restrict__ lo, long long ldk,
+                              long long kofs, int tf32) {
+  mgen_body<float>(T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, [&](long long r, int mu, float re, float im) {
+    long long e = (long long)mu * ldk + kofs + 2 * r;
+    if (tf32) {
+      float hr = tf32_round(re), hi_ = tf32_round(im);
+      float2* H = reinterpret_cast<float2*>(reinterpret_cast<float*>(hi) + e);
+      float2* L = reinterpret_cast<float2*>(reinterpret_cast<float*>(lo) + e);
+      *H = make_float2(hr, hi_);
+      *L = make_float2(re - hr, im - hi_);
+    } else {
+      __nv_bfloat16 hr = __float2bfloat16_rn(re), hm = __float2bfloat16_rn(im);
+      __nv_bfloat16 lr = __float2bfloat16_rn(re - __bfloat162float(hr));
+      __nv_bfloat16 lm = __float2bfloat16_rn(im - __bfloat162float(hm));
+      __nv_bfloat162* H = reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(hi) + e);
+      __nv_bfloat162* L = reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(lo) + e);
+      *H = __halves2bfloat162(hr, hm);
+      *L = __halves2bfloat162(lr, lm);
+    }
+  });
+}
+
+void launch_mgen_planes(const LriGeom& g, const c64* T1, const c64* /*T2*/, const c128* evec, int q, int kk0, int nkk,
+                        int a0, int na, int b0, int nb, void* hi, void* lo, long long ldk, long long kofs, int tf32,
+                        cudaStream_t st) {
+  cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
+  dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
+  k_mgen_planes<<<grid, 256, 0, st>>>(T1, evec, q, kk0, a0, na, b0, nb, hi, lo, ldk, kofs, tf32);
+}
+
+}  // namespace gw

@@ -1,0 +1,210 @@
+"""Thin Python binding of libgw (include/gw.h): argument marshalling only.
+
+Every function here forwards to the C ABI entry of the same name. Device
+memory and streams come from PyTorch; all arithmetic runs in the CUDA kernels
+of libgw.so. There is no CPU path: loading fails loudly when the library is
+missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgw.so")
+
+GW_OK, GW_ERR_ARG, GW_ERR_NOMEM, GW_ERR_CUDA, GW_ERR_NOT_PD, GW_ERR_TIMEOUT, GW_ERR_STATE, GW_ERR_UNSUPPORTED = range(8)
+GW_FP64, GW_3XTF32, GW_3XBF16 = 0, 1, 2
+PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16}
+
+# every symbol include/gw.h declares
+EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_qp",
+           "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_last_error")
+
+
+class GwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"gw status {status}: {msg}")
+        self.status = status
+
+
+class gw_problem(ctypes.Structure):
+    _fields_ = [
+        ("nk", ctypes.c_int32 * 3),
+        ("n_atoms", ctypes.c_int32), ("n_basis", ctypes.c_int32), ("n_bands", ctypes.c_int32),
+        ("n_occ", ctypes.c_int32), ("n_aux", ctypes.c_int32),
+        ("basis_atom", ctypes.POINTER(ctypes.c_int32)),
+        ("aux_atom", ctypes.POINTER(ctypes.c_int32)),
+        ("n_R", ctypes.c_int32),
+        ("R", ctypes.POINTER(ctypes.c_int32)),
+        ("eps", ctypes.c_void_p),
+        ("evec", ctypes.c_void_p),
+        ("ctil_R", ctypes.c_void_p),
+        ("V", ctypes.c_void_p),
+        ("pmom", ctypes.c_void_p),
+        ("omega_cell", ctypes.c_double),
+        ("qhat", ctypes.c_double * 3),
+        ("head_wings", ctypes.c_int32),
+        ("n_freq", ctypes.c_int32),
+        ("omega0", ctypes.c_double),
+        ("sigma_lo", ctypes.c_int32), ("sigma_hi", ctypes.c_int32),
+        ("spin", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("prec", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libgw.so (built in-tree by __graft_entry__.build()); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)
+    lib.gw_plan_create.argtypes = [ctypes.POINTER(gw_problem), i32, vp, ctypes.POINTER(vp)]
+    lib.gw_plan_destroy.argtypes = [vp]
+    lib.gw_chi0.argtypes = [vp, i32, i32, vp]
+    lib.gw_screen.argtypes = [vp, i32, i32, vp]
+    lib.gw_sigma.argtypes = [vp, i32, i32, vp]
+    lib.gw_qp.argtypes = [vp, i32, vp, vp, dp, dp, ctypes.POINTER(i32)]
+    lib.gw_plan_freq.argtypes = [vp, dp, dp]
+    lib.gw_plan_mu.argtypes = [vp, dp]
+    lib.gw_plan_last_chi0_stats.argtypes = [vp, dp, dp]
+    lib.gw_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "gw_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != GW_OK:
+        raise GwError(status, load().gw_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------------------------
+# ABI calls (same names as include/gw.h)
+# ---------------------------------------------------------------------------------------------
+
+
+def gw_plan_create(prob, n_sys=1, stream=None):
+    import torch
+    h = ctypes.c_void_p()
+    s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    _check(load().gw_plan_create(ctypes.byref(prob), n_sys, ctypes.c_void_p(s), ctypes.byref(h)))
+    return h
+
+
+def gw_plan_destroy(plan):
+    _check(load().gw_plan_destroy(plan))
+
+
+def gw_chi0(plan, sys, q, chi0_out=None):
+    _check(load().gw_chi0(plan, sys, q, _ptr(chi0_out)))
+
+
+def gw_screen(plan, sys, q, wc_out=None):
+    _check(load().gw_screen(plan, sys, q, _ptr(wc_out)))
+
+
+def gw_sigma(plan, sys, q, sigma_acc=None):
+    _check(load().gw_sigma(plan, sys, q, _ptr(sigma_acc)))
+
+
+def gw_qp(plan, sys, n_k, n_sigma, sigma=None, dxv=None):
+    e = np.zeros((n_k, n_sigma))
+    gap = ctypes.c_double()
+    nconv = ctypes.c_int32()
+    _check(load().gw_qp(plan, sys, _ptr(sigma), _ptr(dxv),
+                        e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(gap), ctypes.byref(nconv)))
+    return e, gap.value, nconv.value
+
+
+def gw_plan_freq(plan, n_freq):
+    f = np.zeros(n_freq)
+    w = np.zeros(n_freq)
+    _check(load().gw_plan_freq(plan, f.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return f, w
+
+
+def gw_plan_mu(plan):
+    m = ctypes.c_double()
+    _check(load().gw_plan_mu(plan, ctypes.byref(m)))
+    return m.value
+
+
+def gw_plan_last_chi0_stats(plan):
+    ms, fl = ctypes.c_double(), ctypes.c_double()
+    _check(load().gw_plan_last_chi0_stats(plan, ctypes.byref(ms), ctypes.byref(fl)))
+    return ms.value, fl.value
+
+
+# ---------------------------------------------------------------------------------------------
+# marshalling of a seeded synthetic system into device tensors + a gw_problem
+# ---------------------------------------------------------------------------------------------
+
+
+class Problem:
+    """Keeps the device tensors and host arrays that a gw_problem points to alive."""
+
+    def __init__(self, system, prec="3xbf16", device="cuda", host=False):
+        import torch
+        s = system
+        self.system = s
+        dev = torch.device(device)
+        self.basis_atom = np.ascontiguousarray(s.basis_atom, dtype=np.int32)
+        self.aux_atom = np.ascontiguousarray(s.aux_atom, dtype=np.int32)
+        self.R = np.ascontiguousarray(s.R, dtype=np.int32)
+        # host copies (pinned) for end-to-end timing; device copies for the ABI
+        self.h = dict(eps=torch.from_numpy(np.ascontiguousarray(s.eps)),
+                      evec=torch.from_numpy(np.ascontiguousarray(s.evec)),
+                      ctil=torch.from_numpy(np.ascontiguousarray(s.ctil_flat())),
+                      V=torch.from_numpy(np.ascontiguousarray(s.V)),
+                      pmom=torch.from_numpy(np.ascontiguousarray(s.pmom)))
+        if host:
+            self.h = {k: v.pin_memory() for k, v in self.h.items()}
+        self.d = {k: v.to(dev) for k, v in self.h.items()}
+        p = gw_problem()
+        p.nk[:] = list(s.nk)
+        p.n_atoms, p.n_basis, p.n_bands, p.n_occ, p.n_aux = s.n_atoms, s.n_basis, s.n_bands, s.n_occ, s.n_aux
+        p.basis_atom = self.basis_atom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        p.aux_atom = self.aux_atom.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        p.n_R = self.R.shape[0]
+        p.R = self.R.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        p.eps = self.d["eps"].data_ptr()
+        p.evec = self.d["evec"].data_ptr()
+        p.ctil_R = self.d["ctil"].data_ptr()
+        p.V = self.d["V"].data_ptr()
+        p.pmom = self.d["pmom"].data_ptr()
+        p.omega_cell = s.omega_cell
+        p.qhat[:] = list(s.qhat)
+        p.head_wings = int(s.head_wings)
+        p.n_freq = s.n_freq
+        p.omega0 = s.omega0
+        p.sigma_lo, p.sigma_hi = s.sigma_lo, s.sigma_hi
+        p.spin = s.spin
+        p.mu = math.nan
+        p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        self.prob = p
+
+    def upload(self):
+        """Host -> device copy of every input (the end-to-end path)."""
+        for k in self.d:
+            self.d[k].copy_(self.h[k], non_blocking=True)
+
+    def nbytes(self):
+        return sum(v.numel() * v.element_size() for v in self.h.values())
