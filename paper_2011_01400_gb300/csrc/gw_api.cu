@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -153,6 +154,11 @@ struct gw_plan_s {
   double* d_S_d = nullptr;    // [R][nw]
   float* d_S_f = nullptr;
   long long sig_rows = 0;
+  float* d_Praw = nullptr;    // fp32 plane of M for the tensor-core chi0 [N][2*ldm]
+  void* d_Pb[6] = {};         // B1 / B2 split planes [N][2*ldm]
+  int n_bpl = 0;
+  int seg_rows = 2048;        // pair rows per FP64 promotion segment of the tensor-core chi0
+  float* d_wtab = nullptr;    // [nw][ldm] Lorentzian weights
   // timing of the chi0 contraction
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double last_chi0_ms = 0.0, last_chi0_flops = 0.0;
@@ -440,6 +446,18 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
     P->d_U = c;
     ALLOC(P->d_S_f, (size_t)P->sig_rows * nw);
   }
+  if (!P->fp64) {
+    const size_t pe = (size_t)N * 2 * P->ldm * (P->prec == GW_3XTF32 ? 4 : 2);
+    ALLOC(P->d_Praw, (size_t)N * 2 * P->ldm);
+    P->n_bpl = P->prec == GW_3XTF32 ? 4 : 6;
+    for (int i = 0; i < P->n_bpl; ++i) {
+      uint8_t* pp;
+      ALLOC(pp, pe);
+      P->d_Pb[i] = pp;
+    }
+    ALLOC(P->d_wtab, (size_t)nw * P->ldm);
+    if (const char* e = std::getenv("GW_CHI0_SEG_ROWS")) P->seg_rows = std::max(32, std::atoi(e));
+  }
   ALLOC(P->d_delta, P->ldm);
   ALLOC(P->d_delta_f, P->ldm);
   ALLOC(P->d_pq, P->ldm);
@@ -561,31 +579,72 @@ gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
     launch_pairs(P->NK, P->NBd, P->p.nk, q, kk0, nkk, P->nocc, na, 0, nb, P->p.eps,
                  reinterpret_cast<const c128*>(P->p.pmom), P->p.qhat, P->d_delta, P->d_delta_f,
                  hw ? P->d_pq : nullptr, st);
-    GW_CUDA(cudaEventRecord(P->ev0, st));
     if (P->fp64) {
       c128* M = static_cast<c128*>(P->d_M);
       launch_mgen<double>(P->geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK,
                           P->nocc, na, 0, nb, M, 1, P->ldm, st);
+      GW_CUDA(cudaEventRecord(P->ev0, st));
       launch_chi0_simt<double>(N, K, M, P->ldm, nullptr, P->d_delta, P->d_freq, nw, scale, P->d_chi0, st);
+      GW_CUDA(cudaEventRecord(P->ev1, st));
       if (hw)
         launch_head_wings<double>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
                                   4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
     } else {
-      c64* M = static_cast<c64*>(P->d_M);
-      launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK,
-                         P->nocc, na, 0, nb, M, 1, P->ldm, st);
-      launch_chi0_simt<float>(N, K, M, P->ldm, P->d_delta_f, nullptr, P->d_freq, nw, scale, P->d_chi0, st);
-      if (hw)
+      // split planes [N][2*ldm] (zero rows beyond K), then the tcgen05 contraction
+      const int tf32 = P->prec == GW_3XTF32;
+      const size_t esz = tf32 ? 4 : 2;
+      if (K < P->ldm) {
+        // zero the padding pair rows K .. ldm-1 of every plane (and their transition energies)
+        const size_t pad = (size_t)(P->ldm - K) * 2;
+        GW_CUDA(cudaMemset2DAsync(P->d_Praw + 2 * (size_t)K, 2 * P->ldm * sizeof(float), 0, pad * sizeof(float), N,
+                                  st));
+        for (int i = 0; i < P->n_bpl; ++i)
+          GW_CUDA(cudaMemset2DAsync(static_cast<uint8_t*>(P->d_Pb[i]) + 2 * (size_t)K * esz, 2 * P->ldm * esz, 0,
+                                    pad * esz, N, st));
+        GW_CUDA(cudaMemsetAsync(P->d_delta_f + K, 0, sizeof(float) * (P->ldm - K), st));
+      }
+      launch_mgen_planes(P->geom, static_cast<const c64*>(P->d_T1), evec, q, kk0, nkk, P->nocc, na, 0, nb,
+                         P->d_Praw, P->d_Pb, 2 * P->ldm, 0, tf32, st);
+      TcChi0Args a{};
+      a.N = N;
+      a.Kpad = (int)P->ldm;
+      a.K = K;
+      a.raw = P->d_Praw;
+      for (int i = 0; i < 6; ++i) a.bpl[i] = P->d_Pb[i];
+      a.delta = P->d_delta_f;
+      a.freq = P->d_freq;
+      a.nw = nw;
+      a.scale = scale;
+      a.chi0 = P->d_chi0;
+      a.tf32 = tf32;
+      a.status = P->d_status;
+      a.seg_rows = P->seg_rows;
+      a.wtab = P->d_wtab;
+      std::string err;
+      GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+      GW_CUDA(cudaEventRecord(P->ev0, st));
+      gw_status ts = tc_chi0_run(a, st, err);
+      if (ts != GW_OK) {
+        P->err = 1;
+        return fail(ts, err);
+      }
+      GW_CUDA(cudaEventRecord(P->ev1, st));
+      if (hw) {
+        c64* M = static_cast<c64*>(P->d_M);
+        launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK,
+                           P->nocc, na, 0, nb, M, 1, P->ldm, st);
         launch_head_wings<float>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
                                  4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
+      }
+      GW_TRY(read_status(P, "gw_chi0"));
     }
-    GW_CUDA(cudaEventRecord(P->ev1, st));
     GW_TRY(check_launch(P, "gw_chi0"));
     GW_CUDA(cudaEventSynchronize(P->ev1));
     float ms = 0.f;
     GW_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
     total_ms += ms;
   }
+  if (!P->fp64) tc_herm_fill(N, nw, P->d_chi0, st);
   P->last_chi0_ms = total_ms;
   P->last_chi0_flops = 8.0 * (double)P->NK * na * nb * ((double)N * (N + 1) / 2) * nw;
   if (chi0_out)

@@ -67,9 +67,10 @@ void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* T2, const c
                  int kk0, int nkk, MapMode mode, int a0, int na, int b0, int nb, cplx<T>* out, long long s_r,
                  long long s_mu, cudaStream_t st);
 // split planes for the tensor-core chi0 B operand: for row mu, K index 2r + {0: re, 1: im}
-void launch_mgen_planes(const LriGeom& g, const c64* T1, const c64* T2, const c128* evec, int q, int kk0,
-                        int nkk, int a0, int na, int b0, int nb, void* hi, void* lo, long long ldk,
-                        long long kofs, int tf32, cudaStream_t st);
+// raw fp32 plane + B1/B2 split planes (3 BF16 pieces or 2 TF32 pieces each), see k_lri.cu
+void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
+                        int b0, int nb, float* raw, void* const* bplanes, long long ldk, long long kofs, int tf32,
+                        cudaStream_t st);
 
 // k_linalg.cu
 template <typename T>
@@ -122,8 +123,8 @@ struct TcChi0Args {
   int N;            // n_aux
   int Kpad;         // padded number of pair rows (multiple of the K chunk)
   int K;            // valid rows
-  const void* Bhi;  // planes [N][2*Kpad] (bf16 or fp32)
-  const void* Blo;
+  const float* raw;       // [N][2*Kpad] fp32 (re, im) of M, read by the A-side transform
+  const void* bpl[6];     // B1 pieces then B2 pieces, [N][2*Kpad] each (bf16 x3 or tf32 x2)
   const float* delta;   // [Kpad] transition energies (0 for padding)
   const double* freq;   // [nw]
   int nw;
@@ -131,9 +132,11 @@ struct TcChi0Args {
   c128* chi0;       // [nw][N][N]
   int tf32;
   int* status;
-  int seg_rows;     // rows per TMEM accumulation segment
+  int seg_rows;     // pair rows per FP64 promotion segment
+  float* wtab;      // workspace [nw][Kpad] for the Lorentzian weights
 };
 gw_status tc_chi0_run(const TcChi0Args& a, cudaStream_t st, std::string& err);
 bool tc_available();
+void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st);
 
 }  // namespace gw

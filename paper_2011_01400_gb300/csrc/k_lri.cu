@@ -151,9 +151,12 @@ template void launch_mgen<double>(const LriGeom&, const c128*, const c128*, cons
 template void launch_mgen<float>(const LriGeom&, const c64*, const c64*, const c128*, int, int, int, MapMode, int,
                                  int, int, int, c64*, long long, long long, cudaStream_t);
 
-// Split planes for the tensor-core chi0 operand: row mu, K index kofs + 2r + {re, im}.
-// BF16: hi = bf16(x), lo = bf16(x - hi). TF32: hi = x rounded to 10 explicit mantissa bits
-// (stored as fp32 with the low 13 bits zero), lo = x - hi in fp32.
+// Operand planes for the tensor-core chi0 (row mu, K index kofs + 2r + {0, 1}):
+//   raw:  fp32 (re, im) of M^mu_r -- read by the transform warps that build the weighted A side;
+//   B1 pieces: split of (re, im);  B2 pieces: split of (-im, re)  (the complex product's second
+//   half, so that one K-concatenated MMA over [B1; B2] yields Re and Im columns).
+// BF16: three pieces h = bf16(x), m = bf16(x - h), l = bf16(x - h - m).
+// TF32: two pieces h = x rounded to 10 explicit mantissa bits (fp32 container), l = x - h.
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t u = __float_as_uint(x);
   if ((u & 0x7f800000u) == 0x7f800000u) return x;          // inf / nan unchanged
@@ -162,35 +165,51 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(u);
 }
 
+struct PlanePtrs {
+  float* raw;
+  void* b[6];      // B1 pieces then B2 pieces
+};
+
 __global__ void k_mgen_planes(const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int a0,
-                              int na, int b0, int nb, void* __restrict__ hi, void* __restrict__ lo, long long ldk,
-                              long long kofs, int tf32) {
+                              int na, int b0, int nb, PlanePtrs P, long long ldk, long long kofs, int tf32) {
   mgen_body<float>(T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, [&](long long r, int mu, float re, float im) {
-    long long e = (long long)mu * ldk + kofs + 2 * r;
+    const long long e = (long long)mu * ldk + kofs + 2 * r;
+    *reinterpret_cast<float2*>(P.raw + e) = make_float2(re, im);
+    const float v1[2] = {re, im}, v2[2] = {-im, re};
     if (tf32) {
-      float hr = tf32_round(re), hi_ = tf32_round(im);
-      float2* H = reinterpret_cast<float2*>(reinterpret_cast<float*>(hi) + e);
-      float2* L = reinterpret_cast<float2*>(reinterpret_cast<float*>(lo) + e);
-      *H = make_float2(hr, hi_);
-      *L = make_float2(re - hr, im - hi_);
+      for (int half = 0; half < 2; ++half) {
+        const float* v = half ? v2 : v1;
+        const float h0 = tf32_round(v[0]), h1 = tf32_round(v[1]);
+        *reinterpret_cast<float2*>(reinterpret_cast<float*>(P.b[2 * half + 0]) + e) = make_float2(h0, h1);
+        *reinterpret_cast<float2*>(reinterpret_cast<float*>(P.b[2 * half + 1]) + e) =
+            make_float2(v[0] - h0, v[1] - h1);
+      }
     } else {
-      __nv_bfloat16 hr = __float2bfloat16_rn(re), hm = __float2bfloat16_rn(im);
-      __nv_bfloat16 lr = __float2bfloat16_rn(re - __bfloat162float(hr));
-      __nv_bfloat16 lm = __float2bfloat16_rn(im - __bfloat162float(hm));
-      __nv_bfloat162* H = reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(hi) + e);
-      __nv_bfloat162* L = reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(lo) + e);
-      *H = __halves2bfloat162(hr, hm);
-      *L = __halves2bfloat162(lr, lm);
+      for (int half = 0; half < 2; ++half) {
+        const float* v = half ? v2 : v1;
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);
+        const float2 hf = __bfloat1622float2(h);
+        const float r0 = v[0] - hf.x, r1 = v[1] - hf.y;
+        const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+        const float2 mf = __bfloat1622float2(m);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half + 0]) + e) = h;
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half + 1]) + e) = m;
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half + 2]) + e) = l;
+      }
     }
   });
 }
 
-void launch_mgen_planes(const LriGeom& g, const c64* T1, const c64* /*T2*/, const c128* evec, int q, int kk0, int nkk,
-                        int a0, int na, int b0, int nb, void* hi, void* lo, long long ldk, long long kofs, int tf32,
+void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
+                        int b0, int nb, float* raw, void* const* bplanes, long long ldk, long long kofs, int tf32,
                         cudaStream_t st) {
   cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
+  PlanePtrs P{};
+  P.raw = raw;
+  for (int i = 0; i < (tf32 ? 4 : 6); ++i) P.b[i] = bplanes[i];
   dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
-  k_mgen_planes<<<grid, 256, 0, st>>>(T1, evec, q, kk0, a0, na, b0, nb, hi, lo, ldk, kofs, tf32);
+  k_mgen_planes<<<grid, 256, 0, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs, tf32);
 }
 
 }  // namespace gw

@@ -1,0 +1,580 @@
+// Step (b) on the 5th-generation tensor cores: chi0(q, i w) as a weighted Hermitian rank-K
+// update in split precision (Eq. chi0_matrix, Hermitised, occupations restored):
+//
+//   chi0_{mu nu}(w) = scale * sum_r w_w(D_r) M^mu_r conj(M^nu_r),   w_w(D) = 2 D / (w^2 + D^2),
+//
+// r = (k, i occ, a unocc). Real form: with y = w M^mu (A side) and b = M^nu (B side), every
+// operand row interleaving (re, im) along K,
+//   Re chi0 = sum_r (y_re b_re + y_im b_im) = A . B1^T,  B1 = (b_re,  b_im),
+//   Im chi0 = sum_r (y_im b_re - y_re b_im) = A . B2^T,  B2 = (-b_im, b_re),
+// so one MMA against the stacked operand [B1; B2] (N = 2 x 64) yields Re and Im columns.
+// Operands are split into pieces (BF16: h + m + l, TF32: h + l) and the products of combined
+// order >= 2^-16 (BF16: hh, hm, mh, hl, lh, mm) or 2^-11 (TF32: hh, hl, lh) are accumulated.
+//
+// Accumulation. The tensor-core FP32 accumulator rounds every addition toward zero, which
+// biases a long sum by ~3e-8 relative per accumulation. So:
+//   * hh goes to accumulator D1, which is drained after every stage (4 MMAs per output)
+//     into FP32 running sums held in registers by the epilogue warps (round to nearest);
+//   * the correction products (2^-8 smaller) go to D2, drained once per segment;
+//   * after each segment the running sums are added in FP64 into the output.
+//
+// Data flow per CTA (one 128 x 64 complex output tile from the host tile list, one frequency):
+//   * warp 0 (TMA):  B1 / B2 pieces, 64 rows x 128 B each per stage, SWIZZLE_128B
+//   * warps 2-5:     A rows: read the fp32 plane of the tile's mu rows, multiply by the
+//                    Lorentzian weight, split, write the A pieces in the UMMA K-major
+//                    128B-swizzled layout (the weight is fused into the operand load)
+//   * warp 1:        one elected thread issues tcgen05.mma (M = 128, N = 128) into TMEM
+//   * warps 6-13:    epilogue (two warps per TMEM lane quadrant, 32 complex columns each)
+// All mbarrier waits are bounded; on expiry the kernel sets ST_TIMEOUT and unwinds.
+#include "gw_internal.h"
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <vector>
+
+namespace gw {
+
+namespace {
+
+constexpr int BM = 128, BN = 64;                   // complex output tile
+constexpr int ROWB = 128;                          // bytes per operand row per stage (one swizzle atom)
+constexpr int TILE = 128 * ROWB;                   // 16 KB: A piece (128 rows) or B piece ([B1; B2], 128 rows)
+constexpr int HALF = 64 * ROWB;                    // 8 KB: B1 or B2 part of a B piece
+constexpr int SMEM_BYTES = 192 * 1024 + 1024 + 256;
+constexpr int NTHREADS = 448;
+constexpr int MAX_TILES = 4096;
+constexpr long long WAIT_LIMIT = 4000000000LL;     // clock64 ticks (~2 s) per wait
+// TMEM columns: D1 buffers at 0 and 128 (re: +0..63, im: +64..127); D2 buffers at 256 and 384
+constexpr uint32_t D1_COL = 0, D2_COL = 256, DBUF = 128;
+
+template <bool TF32> struct Cfg {
+  static constexpr int NP = TF32 ? 2 : 3;          // pieces per operand
+  static constexpr int STAGE = 2 * NP * TILE;      // B pieces then A pieces
+  static constexpr int STAGES = (192 * 1024) / STAGE;
+  static constexpr int RS = TF32 ? 16 : 32;        // complex pair rows per stage
+};
+
+__constant__ short2 c_tiles[MAX_TILES];            // (m0 / BM, n0 / BN) of each output tile
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: returns false (and flags ST_TIMEOUT) when the phase does not complete in time.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > WAIT_LIMIT) {
+      atomicOr(status, ST_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns (one per thread row); the wait is separate.
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused by swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version
+  d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ uint32_t swz(int row, int chunk) {  // byte offset of 16-B chunk in a 128B-swizzled tile
+  return (uint32_t)(row * ROWB + ((chunk ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7f800000u) == 0x7f800000u) return x;
+  u += 0x1000u;
+  u &= 0xffffe000u;
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t*>(&h); }
+
+struct Chi0Params {
+  int N, Kpad, nstage, seg;
+  const float* raw;   // [N][ldk] fp32 (re, im) planes of M, read by the A-side transform
+  long long ldk;      // elements per plane row
+  const float* wtab;  // [nw][Kpad] Lorentzian weights
+  int Kw;             // leading dim of wtab
+  double scale;
+  c128* out;          // [nw][N][N]
+  int* status;
+};
+
+struct Maps {
+  CUtensorMap m[6];   // B1 pieces then B2 pieces
+};
+
+template <bool TF32>
+__global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc(const __grid_constant__ Maps maps, Chi0Params p) {
+  using C = Cfg<TF32>;
+  constexpr int NP = C::NP, STAGES = C::STAGES, STAGE = C::STAGE, RS = C::RS;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint64_t* full_b = bars;                   // [STAGES]
+  uint64_t* full_a = bars + STAGES;          // [STAGES]
+  uint64_t* empty = bars + 2 * STAGES;       // [STAGES]
+  uint64_t* t1full = bars + 3 * STAGES;      // [2] D1 of a stage ready
+  uint64_t* t1empty = bars + 3 * STAGES + 2; // [2] D1 drained
+  uint64_t* t2full = bars + 3 * STAGES + 4;  // [2] D2 of a segment ready
+  uint64_t* t2empty = bars + 3 * STAGES + 6; // [2] D2 drained
+  uint64_t* done = bars + 3 * STAGES + 8;
+  uint32_t* tmem_base_p = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 9);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const short2 tl = c_tiles[blockIdx.x];
+  const int m0 = tl.x * BM, n0 = tl.y * BN;
+  const int w_i = blockIdx.y;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_b[s], 1);
+      mbar_init(&full_a[s], 128);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&t1full[b], 1);
+      mbar_init(&t1empty[b], 256);
+      mbar_init(&t2full[b], 1);
+      mbar_init(&t2empty[b], 256);
+    }
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_base_p, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_base_p;
+  const int nst = p.nstage;
+  const int F = p.seg;
+
+  if (warp == 0) {
+    // ---------------- TMA producer: B1 / B2 pieces ----------------
+    if (lane == 0) {
+      for (int i = 0; i < nst; ++i) {
+        const int s = i % STAGES;
+        if (!mbar_wait(&empty[s], ((i / STAGES) & 1) ^ 1, p.status)) break;
+        uint8_t* st = smem + s * STAGE;
+        mbar_arrive_expect_tx(&full_b[s], NP * TILE);
+        const int x = i * (ROWB / (TF32 ? 4 : 2));
+#pragma unroll
+        for (int pc = 0; pc < NP; ++pc) {
+          tma_load_2d(st + pc * TILE, &maps.m[pc], &full_b[s], x, n0);              // B1 rows 0..63
+          tma_load_2d(st + pc * TILE + HALF, &maps.m[NP + pc], &full_b[s], x, n0);  // B2 rows 64..127
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t fmt = TF32 ? 2u : 1u;
+      const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)((2 * BN) >> 3) << 17) |
+                             ((uint32_t)(BM >> 4) << 24);
+      for (int i = 0; i < nst; ++i) {
+        const int s = i % STAGES;
+        const int b = i & 1;
+        const int g = i / F, b2 = g & 1;
+        const bool seg_first = (i % F) == 0;
+        if (i >= 2 && !mbar_wait(&t1empty[b], ((i >> 1) - 1) & 1, p.status)) break;
+        if (seg_first && g >= 2 && !mbar_wait(&t2empty[b2], ((g >> 1) - 1) & 1, p.status)) break;
+        if (!mbar_wait(&full_b[s], (i / STAGES) & 1, p.status)) break;
+        if (!mbar_wait(&full_a[s], (i / STAGES) & 1, p.status)) break;
+        tc_fence_after();
+        const uint32_t bbase = smem_u32(smem + s * STAGE);
+        const uint32_t abase = bbase + NP * TILE;
+        const uint32_t d1 = tmem + D1_COL + b * DBUF;
+        const uint32_t d2 = tmem + D2_COL + b2 * DBUF;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint32_t ko = kk * 32;
+          const uint32_t acc1 = kk == 0 ? 0u : 1u;
+          const uint32_t acc2 = (seg_first && kk == 0) ? 0u : 1u;
+          const uint64_t A0 = sdesc(abase + ko), B0 = sdesc(bbase + ko);
+          const uint64_t A1 = sdesc(abase + TILE + ko), B1 = sdesc(bbase + TILE + ko);
+          mma<TF32>(d1, A0, B0, idesc, acc1);
+          mma<TF32>(d2, A0, B1, idesc, acc2);
+          mma<TF32>(d2, A1, B0, idesc, 1u);
+          if constexpr (NP == 3) {
+            const uint64_t A2 = sdesc(abase + 2 * TILE + ko), B2 = sdesc(bbase + 2 * TILE + ko);
+            mma<TF32>(d2, A0, B2, idesc, 1u);
+            mma<TF32>(d2, A2, B0, idesc, 1u);
+            mma<TF32>(d2, A1, B1, idesc, 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+        mma_commit(&t1full[b]);
+        if ((i % F) == F - 1 || i == nst - 1) mma_commit(&t2full[b2]);
+      }
+      mma_commit(done);
+      mbar_wait(done, 0, p.status);
+    }
+  } else if (warp >= 2 && warp <= 5) {
+    // ---------------- transform: weighted, split A operand ----------------
+    const int row = threadIdx.x - 64;          // 0..127
+    const int mu = m0 + row;
+    const float* wrow = p.wtab + (long long)w_i * p.Kw;
+    for (int i = 0; i < nst; ++i) {
+      const int s = i % STAGES;
+      if (!mbar_wait(&empty[s], ((i / STAGES) & 1) ^ 1, p.status)) break;
+      uint8_t* at = smem + s * STAGE + NP * TILE;
+      const int r0 = i * RS;
+      if (mu < p.N) {
+        const float4* g = reinterpret_cast<const float4*>(p.raw + (long long)mu * p.ldk + 2LL * r0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          uint32_t o[NP][4];
+          if constexpr (TF32) {
+            // 16-B chunk c = 2 complex pairs
+            const float4 v = __ldg(g + c);
+            const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              const float wt = wrow[r0 + 2 * c + q];
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const float y = wt * x[2 * q + e];
+                const float h = tf32_rn(y);
+                o[0][2 * q + e] = __float_as_uint(h);
+                o[1][2 * q + e] = __float_as_uint(y - h);
+              }
+            }
+          } else {
+            // 16-B chunk c = 4 complex pairs (8 bf16)
+            const float4 v0 = __ldg(g + 2 * c), v1 = __ldg(g + 2 * c + 1);
+            const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float wt = wrow[r0 + 4 * c + q];
+              const float yr = wt * x[2 * q], yi = wt * x[2 * q + 1];
+              const __nv_bfloat162 h = __floats2bfloat162_rn(yr, yi);
+              const float2 hf = __bfloat1622float2(h);
+              const float rr = yr - hf.x, ri = yi - hf.y;
+              const __nv_bfloat162 m = __floats2bfloat162_rn(rr, ri);
+              const float2 mf = __bfloat1622float2(m);
+              const __nv_bfloat162 l = __floats2bfloat162_rn(rr - mf.x, ri - mf.y);
+              o[0][q] = bf2_bits(h);
+              o[1][q] = bf2_bits(m);
+              o[NP - 1][q] = bf2_bits(l);
+            }
+          }
+          const uint32_t off = swz(row, c);
+#pragma unroll
+          for (int pc = 0; pc < NP; ++pc)
+            *reinterpret_cast<uint4*>(at + pc * TILE + off) = make_uint4(o[pc][0], o[pc][1], o[pc][2], o[pc][3]);
+        }
+      } else {
+        const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const uint32_t off = swz(row, c);
+#pragma unroll
+          for (int pc = 0; pc < NP; ++pc) *reinterpret_cast<uint4*>(at + pc * TILE + off) = z;
+        }
+      }
+      fence_proxy_async();
+      mbar_arrive(&full_a[s]);
+    }
+  } else {
+    // ---------------- epilogue: drain D1 per stage, D2 per segment, FP64 flush ----------------
+    const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
+    const int half = (warp - 6) >> 2;          // output columns half*32 .. half*32+31
+    const int row = quad * 32 + lane;
+    const int mu = m0 + row;
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+    float sr[32], si[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
+    for (int i = 0; i < nst; ++i) {
+      const int b = i & 1;
+      if (!mbar_wait(&t1full[b], (i >> 1) & 1, p.status)) break;
+      tc_fence_after();
+      {
+        uint32_t vr[32], vi[32];
+        const uint32_t t = tmem + lane_off + D1_COL + b * DBUF + half * 32;
+        tmem_ld32_nowait(t, vr);
+        tmem_ld32_nowait(t + BN, vi);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          sr[j] += __uint_as_float(vr[j]);
+          si[j] += __uint_as_float(vi[j]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&t1empty[b]);
+      if ((i % F) == F - 1 || i == nst - 1) {
+        const int g = i / F, b2 = g & 1;
+        if (!mbar_wait(&t2full[b2], (g >> 1) & 1, p.status)) break;
+        tc_fence_after();
+        {
+          uint32_t vr[32], vi[32];
+          const uint32_t t = tmem + lane_off + D2_COL + b2 * DBUF + half * 32;
+          tmem_ld32_nowait(t, vr);
+          tmem_ld32_nowait(t + BN, vi);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            sr[j] += __uint_as_float(vr[j]);
+            si[j] += __uint_as_float(vi[j]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&t2empty[b2]);
+        if (mu < p.N) {
+          c128* orow = p.out + ((long long)w_i * p.N + mu) * p.N + n0 + half * 32;
+          const int nmax = p.N - (n0 + half * 32);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            if (j < nmax) {
+              c128 o = orow[j];
+              o.re += p.scale * (double)sr[j];
+              o.im += p.scale * (double)si[j];
+              orow[j] = o;
+            }
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+// w_w(D_r) = 2 D / (w^2 + D^2) for every frequency and pair row (0 for padding rows)
+__global__ void k_weights(int Kpad, int nw, const float* __restrict__ delta, const double* __restrict__ freq,
+                          float* __restrict__ wtab) {
+  const long long total = (long long)nw * Kpad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % Kpad), j = (int)(e / Kpad);
+    const float d = delta[r];
+    const float w = (float)freq[j];
+    wtab[e] = 2.0f * d / (w * w + d * d);
+  }
+}
+
+// chi0[w][i][j] = conj(chi0[w][j][i]) for i < j (the kernel writes lower tiles only)
+__global__ void k_herm_fill(int N, int nw, c128* chi0) {
+  const long long total = (long long)nw * N * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % N), i = (int)((e / N) % N);
+    const long long w = e / ((long long)N * N);
+    if (i < j) {
+      const c128 v = chi0[(w * N + j) * N + i];
+      chi0[(w * N + i) * N + j] = c128{v.re, -v.im};
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int tf32, long long ldk, int rows, std::string& err) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) {
+    err = "cuTensorMapEncodeTiled is unavailable";
+    return false;
+  }
+  const int esz = tf32 ? 4 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ldk * esz)};
+  cuuint32_t box[2] = {(cuuint32_t)(ROWB / esz), (cuuint32_t)BN};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
+// Lower-triangle tile list: every (mb, nb) with some nu <= mu inside, ordered by mb.
+int build_tiles(int N, std::vector<short2>& t) {
+  t.clear();
+  const int nmb = (N + BM - 1) / BM, nnb = (N + BN - 1) / BN;
+  for (int mb = 0; mb < nmb; ++mb)
+    for (int nb = 0; nb < nnb; ++nb) {
+      const int mu_max = std::min(N, (mb + 1) * BM) - 1;
+      if (nb * BN <= mu_max) t.push_back(make_short2((short)mb, (short)nb));
+    }
+  return (int)t.size();
+}
+
+template <bool TF32> void set_smem_attr() {
+  cudaFuncSetAttribute(k_chi0_tc<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+}
+
+}  // namespace
+
+bool tc_available() { return get_encode() != nullptr; }
+
+gw_status tc_chi0_run(const TcChi0Args& a, cudaStream_t st, std::string& err) {
+  const int RS = a.tf32 ? Cfg<true>::RS : Cfg<false>::RS;
+  const int NP = a.tf32 ? 2 : 3;
+  if (a.Kpad % 32 != 0 || a.N < 1) {
+    err = "tc_chi0: Kpad must be a multiple of 32";
+    return GW_ERR_ARG;
+  }
+  std::vector<short2> tiles;
+  const int nt = build_tiles(a.N, tiles);
+  if (nt > MAX_TILES) {
+    err = "tc_chi0: n_aux too large for the tile table";
+    return GW_ERR_ARG;
+  }
+  Maps maps;
+  const long long ldk = 2LL * a.Kpad;
+  for (int i = 0; i < 2 * NP; ++i)
+    if (!make_map(&maps.m[i], a.bpl[i], a.tf32, ldk, a.N, err)) return GW_ERR_CUDA;
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_tiles, tiles.data(), nt * sizeof(short2), 0, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    err = std::string("tc_chi0 tile table: ") + cudaGetErrorString(e);
+    return GW_ERR_CUDA;
+  }
+  k_weights<<<std::min<long long>(((long long)a.nw * a.Kpad + 255) / 256, 152 * 32), 256, 0, st>>>(
+      a.Kpad, a.nw, a.delta, a.freq, a.wtab);
+  Chi0Params p{};
+  p.N = a.N;
+  p.Kpad = a.Kpad;
+  p.nstage = a.Kpad / RS;
+  p.seg = std::max(1, a.seg_rows / RS);
+  p.raw = a.raw;
+  p.ldk = ldk;
+  p.wtab = a.wtab;
+  p.Kw = a.Kpad;
+  p.scale = a.scale;
+  p.out = a.chi0;
+  p.status = a.status;
+  dim3 grid(nt, a.nw);
+  if (a.tf32) {
+    set_smem_attr<true>();
+    k_chi0_tc<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(maps, p);
+  } else {
+    set_smem_attr<false>();
+    k_chi0_tc<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(maps, p);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("k_chi0_tc launch: ") + cudaGetErrorString(e);
+    return GW_ERR_CUDA;
+  }
+  return GW_OK;
+}
+
+void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st) {
+  const long long total = (long long)nw * N * N;
+  k_herm_fill<<<std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, st>>>(N, nw, chi0);
+}
+
+}  // namespace gw
