@@ -1,0 +1,325 @@
+"""Benchmark of the periodic G0W0 hot path on one GB300 (or N independent replicas).
+
+A step is one complete G0W0 pass over one synthetic system: plan (half-transformed
+LRI coefficients, V(q)^1/2 for every q, the Coulomb head eigenvector), then for
+every q: chi0 -> eps~ / W^c -> Sigma_c, then the continuation and QP solve.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config cfg1] [--prec 3xbf16]
+  python bench.py --impl reference ...     (the FP64 CPU oracle on a bounded slice)
+
+Prints one JSON line (rank 0). value = Sigma_c time-to-solution (s per system, whole job:
+seconds per step / systems processed by all ranks), lower is better.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G0W0 Σc time-to-solution & χ0 TFLOP/s: split-prec vs FP64 on 1 GB300 @ ≤1 meV"
+WORKLOADS = {
+    "cfg0": "tiny synthetic insulator: 2x2x2 k, 2 atoms, 32 NAO, 32 bands (4 occ), 96 ABF, 16 imaginary frequencies",
+    "cfg1": "Si-like 2-atom fcc cell: 6x6x6 k (216 k, 216 q), 78 NAO, 78 bands (4 occ), 400 ABF, 32 imaginary "
+            "frequencies, Sigma_c for the 8 bands at the gap",
+}
+
+
+def algorithmic_flops(s):
+    """Useful flops of one step (8 per complex multiply-add): chi0 Hermitian update, screen, Sigma_c."""
+    NK, N, nw = s.n_k, s.n_aux, s.n_freq
+    nocc, nun, nsig = s.n_occ, s.n_bands - s.n_occ, s.sigma_hi - s.sigma_lo
+    chi0 = 8.0 * NK * nocc * nun * (N * (N + 1) / 2) * nw * NK
+    screen = 4 * 8.0 * N ** 3 * nw * NK
+    sigma = 8.0 * (NK * nsig * s.n_bands) * N * N * nw * NK
+    return dict(chi0=chi0, screen=screen, sigma=sigma, total=chi0 + screen + sigma)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            bf16 = d.get("bf16_tflops_sustained") or d.get("bf16_tflops")
+            hbm = d.get("hbm_gbs")
+            if bf16:
+                return float(bf16), float(hbm or 6800.0), "of measured"
+        except Exception:
+            pass
+    return 1900.0, 6800.0, "of fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(system, seconds_hint=20.0):
+    """Time the FP64 oracle on bounded slices of the same workload; extrapolate by algorithmic flops.
+
+    Slices: chi0 for q = 1 at 2 frequencies (all k); eps~/W^c for q = 1 at 2 frequencies;
+    Sigma_c for q = 1 from 2 target k (all frequencies). Each slice is scaled by the ratio of
+    its algorithmic flops to the full step's.
+    """
+    import numpy as np
+    from oracle import gw_oracle as O
+
+    s = system
+    om, g = O.freq_grid(s.n_freq, s.omega0)
+    mu = O.mu_midgap(s)
+    fl = algorithmic_flops(s)
+    iq = 1 % s.n_k
+    # chi0 = M generation for every k (once per q) + one weighted product per frequency
+    occ, unocc = np.arange(s.n_occ), np.arange(s.n_occ, s.n_bands)
+    t0 = time.perf_counter()
+    Ms = [O.mo_triple(s, ik, iq, unocc, occ).reshape(s.n_aux, -1) for ik in range(s.n_k)]
+    t_m = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    c = O.chi0(s, iq, om[:2]) if s.n_k <= 8 else None
+    if c is None:
+        c = np.zeros((2, s.n_aux, s.n_aux), dtype=np.complex128)
+        for ik in range(s.n_k):
+            ikq = O.k_plus(s.nk, ik, iq)
+            D = (s.eps[ikq][unocc][:, None] - s.eps[ik][occ][None, :]).ravel()
+            for w_i, w in enumerate(om[:2]):
+                c[w_i] += (Ms[ik] * (2.0 * D / (w * w + D * D))[None, :]) @ np.conj(Ms[ik]).T
+        c *= -(s.spin / s.n_k)
+    t_h = time.perf_counter() - t0
+    t_chi = t_m + t_h
+    t0 = time.perf_counter()
+    e, W = O.screen(s, iq, c, om[:2])
+    t_scr = time.perf_counter() - t0
+    # Sigma slice: two target k, all w' (needs W^c at every frequency: use the slice's W^c repeated)
+    Wfull = np.repeat(W[:1], s.n_freq, axis=0)
+    t0 = time.perf_counter()
+    nk_s = min(2, s.n_k)
+    for ik in range(nk_s):
+        ikmq = O.k_minus(s.nk, ik, iq)
+        M = O.mo_triple(s, ikmq, iq, np.arange(s.sigma_lo, s.sigma_hi), np.arange(s.n_bands))
+        Mf = M.reshape(s.n_aux, -1)
+        for j in range(s.n_freq):
+            _ = np.sum(Mf * (Wfull[j] @ np.conj(Mf)), axis=0)
+    t_sig = time.perf_counter() - t0
+    NK, nw = s.n_k, s.n_freq
+    est = NK * (t_m + t_h * nw / 2.0) + t_scr * (NK * nw / 2.0) + t_sig * (NK * NK / nk_s)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return dict(value=est, unit="s", cores=cores, kind="oracle",
+                sample=f"FP64 NumPy oracle, extrapolated: M for q=1 (all {NK} k) {t_m:.2f} s + chi0 products "
+                       f"x 2 w {t_h:.2f} s, "
+                       f"screen q=1 x 2 w {t_scr:.2f} s, Sigma_c q=1 x {nk_s} k x {nw} w' {t_sig:.2f} s; "
+                       f"scaled to {NK} q x {nw} w and {NK} k",
+                slice_seconds=t_chi + t_scr + t_sig)
+
+
+def run_reference(args, system, world, rank):
+    if rank != 0:
+        return
+    samples = []
+    for _ in range(args.warmup):
+        oracle_sample(system)
+    for _ in range(args.steps):
+        samples.append(oracle_sample(system))
+    v = statistics.median([x["value"] for x in samples])
+    cb = dict(samples[-1])
+    cb["value"] = v
+    line = dict(metric=METRIC, value=v, unit="s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=statistics.median([x["slice_seconds"] for x in samples]) * 1e3,
+                higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                impl="reference",
+                config=dict(workload=WORKLOADS[args.config], name=args.config, global_batch=1, seq_len=0,
+                            parallelism="single"),
+                cpu_baseline=cb, e2e=dict(value=v, unit="s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def g0w0_step(gw, plan_prob, s, torch, chi_ms):
+    """One complete pass: plan, every q (chi0, screen, sigma), QP. Returns (e_qp, gap)."""
+    plan = gw.gw_plan_create(plan_prob)
+    try:
+        for q in range(s.n_k):
+            gw.gw_chi0(plan, 0, q)
+            ms, fl = gw.gw_plan_last_chi0_stats(plan)
+            chi_ms.append((ms, fl))
+            gw.gw_screen(plan, 0, q)
+            gw.gw_sigma(plan, 0, q)
+        e, gap, nconv = gw.gw_qp(plan, 0, s.n_k, s.sigma_hi - s.sigma_lo)
+    finally:
+        gw.gw_plan_destroy(plan)
+    return e, gap
+
+
+def run_device(args, system, world, rank):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2011_01400_gb300 import gw
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    s = system
+    pb = gw.Problem(s, args.prec, host=True)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    chi_ms = []
+    for _ in range(args.warmup):
+        g0w0_step(gw, pb.prob, s, torch, chi_ms)
+    torch.cuda.synchronize()
+    # device-resident timed region
+    chi_ms.clear()
+    clocks = Clocks(dev)
+    l0 = gw.gw_kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e, gap = g0w0_step(gw, pb.prob, s, torch, chi_ms)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    launches = gw.gw_kernel_launches() - l0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # end to end: host inputs copied in every step, QP energies read back
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    chi_e2e = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        pb.upload()
+        e_qp, gap = g0w0_step(gw, pb.prob, s, torch, chi_e2e)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms, ms_e2e], dtype=torch.float64)
+    if world > 1:
+        t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t = t.cpu()
+    ms, ms_e2e = float(t[0]), float(t[1])
+    if rank != 0:
+        return
+    fl = algorithmic_flops(s)
+    chi_avg_ms = sum(x[0] for x in chi_ms) / len(chi_ms)
+    chi_flops = chi_ms[0][1]
+    peak_bf16, peak_hbm, peak_kind = load_peaks()
+    tf32 = args.prec == "3xtf32"
+    peak = peak_bf16 * (0.5 if tf32 else 1.0) if args.prec != "fp64" else 1.25
+    achieved = chi_flops / (chi_avg_ms * 1e-3) / 1e12
+    products = {"3xbf16": 6, "3xtf32": 3, "fp64": 1}[args.prec]
+    line = dict(
+        metric=METRIC,
+        value=ms / 1e3 / world,
+        unit="s",
+        n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
+        higher_is_better=False, scaling="weak", vs_baseline=None,
+        dtype={"3xbf16": "bf16x3-split/f32-acc/f64", "3xtf32": "tf32x2-split/f32-acc/f64", "fp64": "f64"}[args.prec],
+        data="synthetic",
+        config=dict(workload=WORKLOADS[args.config], name=args.config, precision=args.prec, systems_per_step=world,
+                    global_batch=world, seq_len=0, parallelism="replicas" if world > 1 else "single",
+                    l2="inputs larger than L2 (chi0 operand planes 0.8 GB per q)"),
+        chi0_tflops=achieved,
+        step_useful_tflops=fl["total"] / (ms * 1e-3) / 1e12,
+        roofline=dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                      traffic=None, kernel="k_tc<chi0> (tcgen05 weighted Hermitian update)",
+                      peak_note=f"{'TF32' if tf32 else 'BF16'} dense {peak_kind}; achieved counts algorithmic "
+                                f"flops (8 per complex MAC, lower triangle); tensor-issued = x{products}",
+                      tensor_issued_frac=achieved * products / peak),
+        e2e=dict(value=ms_e2e / 1e3 / world, unit="s", h2d_bytes_per_step=pb.nbytes(),
+                 d2h_bytes_per_step=s.n_k * (s.sigma_hi - s.sigma_lo) * 8 + 8),
+        gpu_launches=launches,
+        clocks=ck,
+        gap_ha=gap,
+    )
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(s)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--config", default="cfg1", choices=list(WORKLOADS))
+    ap.add_argument("--prec", default="3xbf16", choices=["3xbf16", "3xtf32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "native":
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2011_01400_gb300.synth import make_system
+    system = make_system(args.config, seed=1000 * int(args.config[-1]) + rank)
+    if args.impl == "reference":
+        run_reference(args, system, world, rank)
+    else:
+        run_device(args, system, world, rank)
+    if world > 1 and args.impl == "native":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -144,6 +144,9 @@ gw_status gw_plan_mu(gw_plan plan, double* mu);
  * and its algorithmic flop count (8 per complex multiply-add, Hermitian lower triangle). */
 gw_status gw_plan_last_chi0_stats(gw_plan plan, double* ms, double* flops);
 
+/* Number of CUDA kernels this library has launched in the calling process so far (host-side count). */
+gw_status gw_kernel_launches(uint64_t* count);
+
 /* Text of the last error on the calling thread ("" if none). Never NULL. */
 const char* gw_last_error(void);
 

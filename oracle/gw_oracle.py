@@ -127,7 +127,7 @@ def mo_triple(sys, ik, iq, a_bands, b_bands):
     Ct = ao_triple(sys, ik, iq)
     ca = sys.evec[ikq][:, a_bands]      # [i, a]
     cb = sys.evec[ik][:, b_bands]       # [j, b]
-    return np.einsum("ia,uij,jb->uab", np.conj(ca), Ct, cb)
+    return np.einsum("ia,uij,jb->uab", np.conj(ca), Ct, cb, optimize=True)
 
 
 # ----------------------------------------------------------------------------

@@ -10,6 +10,10 @@
 #include <string>
 #include <vector>
 
+namespace gw {
+unsigned long long g_launch_count = 0;
+}
+
 using namespace gw;
 
 namespace {
@@ -159,6 +163,11 @@ struct gw_plan_s {
   int n_bpl = 0;
   int seg_rows = 2048;        // pair rows per FP64 promotion segment of the tensor-core chi0
   float* d_wtab = nullptr;    // [nw][ldm] Lorentzian weights
+  int Kx = 0;                 // n_aux rounded up to 32 (K of the Sigma contraction)
+  PlaneSet d_Wpl{};           // W^c split planes [nw*N][2*Kx]
+  c64* d_Vh32 = nullptr;      // FP32 copies of V^1/2 for the split-precision screen
+  c64* d_Vb32 = nullptr;
+  TcWorkspace tcws;
   // timing of the chi0 contraction
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double last_chi0_ms = 0.0, last_chi0_flops = 0.0;
@@ -231,9 +240,9 @@ gw_status newton_schulz(gw_plan_s* P, const c128* V, c128* out, int batch, int i
   GW_TRY(dalloc(P, &Z, s * batch));
   GW_TRY(dalloc(P, &Tm, s * batch));
   GW_TRY(dalloc(P, &Y2, s * batch));
-  k_frob_scale<<<batch, 256, 0, P->st>>>(N, V, s, d_c);
+  ++::gw::g_launch_count, k_frob_scale<<<batch, 256, 0, P->st>>>(N, V, s, d_c);
   dim3 g(std::min<long long>((s + 255) / 256, 1024), batch);
-  k_ns_init<T><<<g, 256, 0, P->st>>>(N, V, s, d_c, Y, Z);
+  ++::gw::g_launch_count, k_ns_init<T><<<g, 256, 0, P->st>>>(N, V, s, d_c, Y, Z);
   const cplx<T> one{(T)1, (T)0}, zero{(T)0, (T)0}, mhalf{(T)-0.5, (T)0};
   for (int it = 0; it < iters; ++it) {
     // Tm = -0.5 Z Y + 1.5 I
@@ -244,7 +253,7 @@ gw_status newton_schulz(gw_plan_s* P, const c128* V, c128* out, int batch, int i
     std::swap(Z, Y);   // Z = T Z
     std::swap(Y, Y2);  // Y = Y T
   }
-  k_ns_final<T><<<g, 256, 0, P->st>>>(N, Y, s, d_c, out);
+  ++::gw::g_launch_count, k_ns_final<T><<<g, 256, 0, P->st>>>(N, Y, s, d_c, out);
   GW_TRY(check_launch(P, "newton_schulz"));
   cudaError_t e = cudaStreamSynchronize(P->st);
   if (e != cudaSuccess) return fail(GW_ERR_CUDA, std::string("newton_schulz: ") + cudaGetErrorString(e));
@@ -308,6 +317,12 @@ bool plan_ok(gw_plan P, int32_t sys, gw_status* s) {
 extern "C" {
 
 const char* gw_last_error(void) { return g_last_error.c_str(); }
+
+gw_status gw_kernel_launches(uint64_t* count) {
+  if (!count) return fail(GW_ERR_ARG, "count is NULL");
+  *count = (uint64_t)::gw::g_launch_count;
+  return GW_OK;
+}
 
 gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw_plan* out) {
   if (!out) return fail(GW_ERR_ARG, "out is NULL");
@@ -437,14 +452,26 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
     P->d_U = c;
     ALLOC(P->d_S_d, (size_t)P->sig_rows * nw);
   } else {
-    c64 *a, *b, *c;
+    c64 *a, *b;
+    P->Kx = ((N + 31) / 32) * 32;
     ALLOC(a, (size_t)N * P->ldm);
-    ALLOC(b, (size_t)P->sig_rows * N);
-    ALLOC(c, (size_t)P->sig_rows * N);
+    ALLOC(b, (size_t)P->sig_rows * P->Kx);   // raw plane of the Sigma rows, zero beyond n_aux
     P->d_M = a;
     P->d_A = b;
-    P->d_U = c;
     ALLOC(P->d_S_f, (size_t)P->sig_rows * nw);
+    const size_t we = (size_t)nw * N * 2 * P->Kx * (P->prec == GW_3XTF32 ? 4 : 2);
+    for (int i = 0; i < (P->prec == GW_3XTF32 ? 4 : 6); ++i) {
+      uint8_t* pp;
+      ALLOC(pp, we);
+      P->d_Wpl.b[i] = pp;
+    }
+    c64 *v32, *b32;
+    ALLOC(v32, NN * P->NK);
+    P->d_Vh32 = v32;
+    if (prob->head_wings) {
+      ALLOC(b32, NN);
+      P->d_Vb32 = b32;
+    }
   }
   if (!P->fp64) {
     const size_t pe = (size_t)N * 2 * P->ldm * (P->prec == GW_3XTF32 ? 4 : 2);
@@ -516,6 +543,11 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
     launch_rank1(N, P->d_Vh, P->d_x1, -std::sqrt(t_shift), st);
     CK(cudaMemcpyAsync(P->d_Vb0, P->d_Vh, sizeof(c128) * NN, cudaMemcpyDeviceToDevice, st));
     launch_rank1(N, P->d_Vh, P->d_x1, std::sqrt(std::max(P->h_v1, 0.0)), st);
+  }
+  if (!P->fp64) {
+    launch_convert((int)(NN * P->NK), P->d_Vh, P->d_Vh32, st);
+    if (prob->head_wings) launch_convert((int)NN, P->d_Vb0, P->d_Vb32, st);
+    CK(cudaMemsetAsync(P->d_A, 0, sizeof(c64) * (size_t)P->sig_rows * P->Kx, st));
   }
   if ((s = check_launch(P, "plan setup")) != GW_OK) return cleanup(s);
   CK(cudaStreamSynchronize(st));
@@ -623,7 +655,7 @@ gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
       std::string err;
       GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
       GW_CUDA(cudaEventRecord(P->ev0, st));
-      gw_status ts = tc_chi0_run(a, st, err);
+      gw_status ts = tc_chi0_run(a, P->tcws, st, err);
       if (ts != GW_OK) {
         P->err = 1;
         return fail(ts, err);
@@ -666,9 +698,23 @@ gw_status gw_screen(gw_plan P, int32_t sys, int32_t q, gw_complex* wc_out) {
   const c128* Vh = P->d_Vh + (long long)q * NN;
   const c128* Vin = hw ? P->d_Vb0 : Vh;     // V^1/2 entering eps~ (body only at q = 0)
   const c128 one{1, 0}, zero{0, 0}, mone{-1, 0};
+  const c64 one32{1, 0}, zero32{0, 0}, mone32{-1, 0};
+  // FP32 scratch for the split-precision path: two halves of d_work and d_tmp
+  c64* A32 = reinterpret_cast<c64*>(P->d_work);
+  c64* B32 = A32 + NN * nw;
+  c64* C32 = reinterpret_cast<c64*>(P->d_tmp);
+  const c64* Vh32 = P->fp64 ? nullptr : P->d_Vh32 + (long long)q * NN;
+  const c64* Vin32 = P->fp64 ? nullptr : (hw ? P->d_Vb32 : Vh32);
   // eps~ = 1 - Vin chi0 Vin
-  launch_zgemm<double>(N, N, N, one, P->d_chi0, N, NN, OP_N, Vin, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
-  launch_zgemm<double>(N, N, N, mone, Vin, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, P->d_E, N, NN, nw, st);
+  if (P->fp64) {
+    launch_zgemm<double>(N, N, N, one, P->d_chi0, N, NN, OP_N, Vin, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
+    launch_zgemm<double>(N, N, N, mone, Vin, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, P->d_E, N, NN, nw, st);
+  } else {
+    launch_convert((int)(NN * nw), P->d_chi0, A32, st);
+    launch_zgemm<float>(N, N, N, one32, A32, N, NN, OP_N, Vin32, N, 0, OP_N, zero32, B32, N, NN, nw, st);
+    launch_zgemm<float>(N, N, N, mone32, Vin32, N, 0, OP_N, B32, N, NN, OP_N, zero32, C32, N, NN, nw, st);
+    launch_convert_back((int)(NN * nw), C32, P->d_E, st);
+  }
   launch_axpby_identity<double>(N, P->d_E, NN, nw, 1.0, st);
   if (hw) {
     // Vbh[w] = Vb0 h[w]  (stored in d_tmp rows), then the rank-2 head / wing correction
@@ -679,8 +725,15 @@ gw_status gw_screen(gw_plan P, int32_t sys, int32_t q, gw_complex* wc_out) {
   GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
   launch_chol_inv_minus_I(N, P->d_E, nw, NN, P->d_work, P->d_status, st);
   // W^c = Vh (eps~^-1 - 1) Vh
-  launch_zgemm<double>(N, N, N, one, P->d_E, N, NN, OP_N, Vh, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
-  launch_zgemm<double>(N, N, N, one, Vh, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, P->d_Wc, N, NN, nw, st);
+  if (P->fp64) {
+    launch_zgemm<double>(N, N, N, one, P->d_E, N, NN, OP_N, Vh, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
+    launch_zgemm<double>(N, N, N, one, Vh, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, P->d_Wc, N, NN, nw, st);
+  } else {
+    launch_convert((int)(NN * nw), P->d_E, A32, st);
+    launch_zgemm<float>(N, N, N, one32, A32, N, NN, OP_N, Vh32, N, 0, OP_N, zero32, B32, N, NN, nw, st);
+    launch_zgemm<float>(N, N, N, one32, Vh32, N, 0, OP_N, B32, N, NN, OP_N, zero32, C32, N, NN, nw, st);
+    launch_convert_back((int)(NN * nw), C32, P->d_Wc, st);
+  }
   GW_TRY(check_launch(P, "gw_screen"));
   GW_TRY(read_status(P, "gw_screen"));
   if (wc_out) GW_CUDA(cudaMemcpyAsync(wc_out, P->d_Wc, sizeof(c128) * NN * nw, cudaMemcpyDeviceToDevice, st));
@@ -699,7 +752,8 @@ gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
   const c128* evec = reinterpret_cast<const c128*>(P->p.evec);
   c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
   const double pref = -1.0 / (2.0 * M_PI * P->NK);
-  if (!P->fp64) launch_convert((int)(NN * nw), P->d_Wc, reinterpret_cast<c64*>(P->d_work), st);
+  const int tf32 = P->prec == GW_3XTF32;
+  if (!P->fp64) tc_w_planes(N, nw, P->Kx, P->d_Wc, P->d_Wpl, tf32, st);
   for (int kk0 = 0; kk0 < P->NK; kk0 += P->sig_nkk) {
     const int nkk = std::min(P->sig_nkk, P->NK - kk0);
     const int R = nkk * nsig * NBd;
@@ -714,14 +768,26 @@ gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
         launch_rowdot<double>(R, N, U, A, N, nullptr, P->d_S_d, j, nw, st);
       }
     } else {
+      // rows a_r as an fp32 plane [R][Kx] (zero beyond n_aux), then the tensor-core contraction
       c64* A = static_cast<c64*>(P->d_A);
-      c64* U = static_cast<c64*>(P->d_U);
-      const c64* W32 = reinterpret_cast<const c64*>(P->d_work);
       launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK_MINUS_Q,
-                         P->p.sigma_lo, nsig, 0, NBd, A, N, 1, st);
-      for (int j = 0; j < nw; ++j) {
-        launch_zgemm<float>(R, N, N, c64{1, 0}, A, N, 0, OP_N, W32 + j * NN, N, 0, OP_N, c64{0, 0}, U, N, 0, 1, st);
-        launch_rowdot<float>(R, N, U, A, N, P->d_S_f, nullptr, j, nw, st);
+                         P->p.sigma_lo, nsig, 0, NBd, A, P->Kx, 1, st);
+      GW_CUDA(cudaMemsetAsync(P->d_S_f, 0, sizeof(float) * (size_t)R * nw, st));
+      TcSigmaArgs a{};
+      a.R = R;
+      a.N = N;
+      a.Kpad = P->Kx;
+      a.nw = nw;
+      a.raw = reinterpret_cast<const float*>(A);
+      for (int i = 0; i < 6; ++i) a.bpl[i] = P->d_Wpl.b[i];
+      a.S = P->d_S_f;
+      a.tf32 = tf32;
+      a.status = P->d_status;
+      std::string err;
+      gw_status ts = tc_sigma_run(a, P->tcws, st, err);
+      if (ts != GW_OK) {
+        P->err = 1;
+        return fail(ts, err);
       }
     }
     launch_sigma_conv_chunk(kk0, nkk, nsig, NBd, P->p.nk, q, P->p.eps, P->d_mu, P->d_S_f, P->d_S_d, P->d_freq,

@@ -11,6 +11,9 @@
 
 namespace gw {
 
+// number of kernels this library has launched (process-wide, host side)
+extern unsigned long long g_launch_count;
+
 // complex helpers (device and host)
 template <typename T> struct cplx { T re, im; };
 using c64 = cplx<float>;
@@ -135,7 +138,32 @@ struct TcChi0Args {
   int seg_rows;     // pair rows per FP64 promotion segment
   float* wtab;      // workspace [nw][Kpad] for the Lorentzian weights
 };
-gw_status tc_chi0_run(const TcChi0Args& a, cudaStream_t st, std::string& err);
+struct PlaneSet {
+  void* b[6];       // B1 pieces then B2 pieces
+};
+// device tables owned by a plan for the tensor-core launches
+struct TcWorkspace {
+  short2* tiles = nullptr;
+  int tile_cap = 0;
+  float* ones = nullptr;
+  int ones_cap = 0;
+  ~TcWorkspace();
+  gw_status ensure(int ntiles, int nones, cudaStream_t st, std::string& err);
+};
+struct TcSigmaArgs {
+  int R;            // rows a_r = C^mu_{nm}(k, k-q) of this chunk
+  int N;            // n_aux
+  int Kpad;         // n_aux rounded up to 32 (K = mu)
+  int nw;
+  const float* raw; // [R][2*Kpad] fp32 (re, im) of a_r (zero beyond n_aux)
+  const void* bpl[6];  // W^c planes [nw*N][2*Kpad] (B1 pieces then B2 pieces)
+  float* S;         // [R][nw] accumulated (zeroed by the caller)
+  int tf32;
+  int* status;
+};
+gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std::string& err);
+gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, std::string& err);
+void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st);
 bool tc_available();
 void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st);
 

@@ -78,7 +78,7 @@ void launch_zgemm(int m, int n, int k, cplx<T> alpha, const cplx<T>* A, long lon
                   const cplx<T>* B, long long ldb, long long sB, Op opB, cplx<T> beta, cplx<T>* C, long long ldc,
                   long long sC, int batch, cudaStream_t st) {
   dim3 grid((n + 63) / 64, (m + 63) / 64, batch);
-  k_zgemm<T><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, (int)opA, B, ldb, sB, (int)opB, beta, C, ldc, sC);
+  ++::gw::g_launch_count, k_zgemm<T><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, (int)opA, B, ldb, sB, (int)opB, beta, C, ldc, sC);
 }
 template void launch_zgemm<double>(int, int, int, c128, const c128*, long long, long long, Op, const c128*,
                                    long long, long long, Op, c128, c128*, long long, long long, int, cudaStream_t);
@@ -162,7 +162,7 @@ void launch_chi0_simt(int N, int K, const cplx<T>* Mt, long long ldm, const floa
                       const double* freq, int nw, double scale, c128* chi0, cudaStream_t st) {
   int nt = (N + 31) / 32;
   dim3 grid(nt * (nt + 1) / 2, nw);
-  k_chi0_simt<T><<<grid, 256, 0, st>>>(N, K, Mt, ldm, delta_f, delta_d, freq, scale, chi0);
+  ++::gw::g_launch_count, k_chi0_simt<T><<<grid, 256, 0, st>>>(N, K, Mt, ldm, delta_f, delta_d, freq, scale, chi0);
 }
 template void launch_chi0_simt<double>(int, int, const c128*, long long, const float*, const double*, const double*,
                                        int, double, c128*, cudaStream_t);
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_inv(int N, c128* __restri
 
 void launch_chol_inv_minus_I(int N, c128* A, int batch, long long stride, c128* work, int* status, cudaStream_t st) {
   size_t smem = sizeof(c128) * (size_t)N;
-  k_chol_inv<<<batch, CHOL_THREADS, smem, st>>>(N, A, stride, work, status);
+  ++::gw::g_launch_count, k_chol_inv<<<batch, CHOL_THREADS, smem, st>>>(N, A, stride, work, status);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -310,7 +310,7 @@ __global__ void k_axpby_identity(int N, cplx<T>* A, long long s, T diag) {
 }
 template <typename T> void launch_axpby_identity(int N, cplx<T>* A, long long s, int batch, T diag, cudaStream_t st) {
   dim3 grid((N + 255) / 256, batch);
-  k_axpby_identity<T><<<grid, 256, 0, st>>>(N, A, s, diag);
+  ++::gw::g_launch_count, k_axpby_identity<T><<<grid, 256, 0, st>>>(N, A, s, diag);
 }
 template void launch_axpby_identity<double>(int, c128*, long long, int, double, cudaStream_t);
 template void launch_axpby_identity<float>(int, c64*, long long, int, float, cudaStream_t);
@@ -324,10 +324,10 @@ __global__ void k_convert_back(int n, const c64* in, c128* out) {
     out[i] = c128{(double)in[i].re, (double)in[i].im};
 }
 void launch_convert(int n, const c128* in, c64* out, cudaStream_t st) {
-  k_convert<<<std::min((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, in, out);
+  ++::gw::g_launch_count, k_convert<<<std::min((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, in, out);
 }
 void launch_convert_back(int n, const c64* in, c128* out, cudaStream_t st) {
-  k_convert_back<<<std::min((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, in, out);
+  ++::gw::g_launch_count, k_convert_back<<<std::min((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, in, out);
 }
 
 // Dominant eigenpair by power iteration with a Rayleigh quotient (one block, FP64).
@@ -378,7 +378,7 @@ __global__ void k_power_iter(int N, const c128* __restrict__ A, c128* __restrict
   for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = cmul(v[i], ph);
 }
 void launch_power_iter(int N, const c128* A, c128* x, double* lam, int iters, cudaStream_t st) {
-  k_power_iter<<<1, 512, 2 * N * sizeof(c128), st>>>(N, A, x, lam, iters);
+  ++::gw::g_launch_count, k_power_iter<<<1, 512, 2 * N * sizeof(c128), st>>>(N, A, x, lam, iters);
 }
 
 __global__ void k_rank1(int N, c128* A, const c128* x, double alpha) {
@@ -391,7 +391,7 @@ __global__ void k_rank1(int N, c128* A, const c128* x, double alpha) {
   }
 }
 void launch_rank1(int N, c128* A, const c128* x, double alpha, cudaStream_t st) {
-  k_rank1<<<std::min((N * N + 255) / 256, 152 * 16), 256, 0, st>>>(N, A, x, alpha);
+  ++::gw::g_launch_count, k_rank1<<<std::min((N * N + 255) / 256, 152 * 16), 256, 0, st>>>(N, A, x, alpha);
 }
 
 // head[w] += pref * sum_r |pq_r|^2 2 / (D (D^2 + w^2));  h[w][nu] += sum_r conj(pq_r) Mt[nu][r] 2/(w^2 + D^2)
@@ -434,7 +434,7 @@ template <typename T>
 void launch_head_wings(int N, int K, const cplx<T>* Mt, long long ldm, const double* delta, const c128* pq,
                        const double* freq, int nw, double head_pref, double* head, c128* h, cudaStream_t st) {
   dim3 grid(N + 1, nw);
-  k_head_wings<T><<<grid, 256, 0, st>>>(N, K, Mt, ldm, delta, pq, freq, head_pref, head, h);
+  ++::gw::g_launch_count, k_head_wings<T><<<grid, 256, 0, st>>>(N, K, Mt, ldm, delta, pq, freq, head_pref, head, h);
 }
 template void launch_head_wings<double>(int, int, const c128*, long long, const double*, const c128*, const double*,
                                         int, double, double*, c128*, cudaStream_t);
@@ -474,7 +474,7 @@ void launch_pairs(int NK, int NBd, const int* nk, int q, int kk0, int nkk, int a
                   cudaStream_t st) {
   long long total = (long long)nkk * na * nb;
   int blocks = (int)std::min<long long>((total + 255) / 256, 152 * 32);
-  k_pairs<<<blocks, 256, 0, st>>>(NBd, nk[0], nk[1], nk[2], q, kk0, nkk, a0, na, b0, nb, eps, pmom,
+  ++::gw::g_launch_count, k_pairs<<<blocks, 256, 0, st>>>(NBd, nk[0], nk[1], nk[2], q, kk0, nkk, a0, na, b0, nb, eps, pmom,
                                   qhat ? qhat[0] : 0, qhat ? qhat[1] : 0, qhat ? qhat[2] : 0, delta, delta_f, pq);
 }
 
@@ -500,7 +500,7 @@ __global__ void k_q0_correction(int N, c128* eps_t, const c128* __restrict__ x1,
 void launch_q0_correction(int N, int nw, c128* eps_t, const c128* x1, const c128* Vbh, const double* head, double c,
                           cudaStream_t st) {
   dim3 grid(std::min((N * N + 255) / 256, 256), nw);
-  k_q0_correction<<<grid, 256, 0, st>>>(N, eps_t, x1, Vbh, head, c);
+  ++::gw::g_launch_count, k_q0_correction<<<grid, 256, 0, st>>>(N, eps_t, x1, Vbh, head, c);
 }
 
 __global__ void k_midgap(int NK, int NBd, int nocc, const double* eps, double* mu) {
@@ -523,7 +523,7 @@ __global__ void k_midgap(int NK, int NBd, int nocc, const double* eps, double* m
   if (threadIdx.x == 0) *mu = 0.5 * (hmax[0] + lmin[0]);
 }
 void launch_midgap(int NK, int NBd, int nocc, const double* eps, double* mu, cudaStream_t st) {
-  k_midgap<<<1, 256, 0, st>>>(NK, NBd, nocc, eps, mu);
+  ++::gw::g_launch_count, k_midgap<<<1, 256, 0, st>>>(NK, NBd, nocc, eps, mu);
 }
 
 }  // namespace gw

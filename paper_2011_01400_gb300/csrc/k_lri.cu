@@ -62,7 +62,7 @@ void launch_lri_halfT(const LriGeom& g, const double* ctil, const c128* evec, cp
   for (int A = 0; A < g.n_atoms; ++A) {
     long long total = (long long)g.NK * g.atom_nx[A] * g.atom_nb[A] * g.NBd;
     int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
-    k_lri_halfT<T><<<blocks, 256, 0, st>>>(ctil, evec, T1, A);
+    ++::gw::g_launch_count, k_lri_halfT<T><<<blocks, 256, 0, st>>>(ctil, evec, T1, A);
   }
 }
 template void launch_lri_halfT<double>(const LriGeom&, const double*, const c128*, c128*, c128*, cudaStream_t);
@@ -144,7 +144,7 @@ void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* /*T2*/, con
                  cudaStream_t st) {
   cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
   dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
-  k_mgen<T><<<grid, 256, 0, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r, s_mu);
+  ++::gw::g_launch_count, k_mgen<T><<<grid, 256, 0, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r, s_mu);
 }
 template void launch_mgen<double>(const LriGeom&, const c128*, const c128*, const c128*, int, int, int, MapMode, int,
                                   int, int, int, c128*, long long, long long, cudaStream_t);
@@ -209,7 +209,7 @@ void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q
   P.raw = raw;
   for (int i = 0; i < (tf32 ? 4 : 6); ++i) P.b[i] = bplanes[i];
   dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
-  k_mgen_planes<<<grid, 256, 0, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs, tf32);
+  ++::gw::g_launch_count, k_mgen_planes<<<grid, 256, 0, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs, tf32);
 }
 
 }  // namespace gw

@@ -24,7 +24,7 @@ template <typename T>
 void launch_rowdot(int R, int N, const cplx<T>* U, const cplx<T>* a, long long ld, float* S_f, double* S_d, int j,
                    int nw, cudaStream_t st) {
   int blocks = (R * 32 + 255) / 256;
-  k_rowdot<T><<<blocks, 256, 0, st>>>(R, N, U, a, ld, S_f, S_d, j, nw);
+  ++::gw::g_launch_count, k_rowdot<T><<<blocks, 256, 0, st>>>(R, N, U, a, ld, S_f, S_d, j, nw);
 }
 template void launch_rowdot<double>(int, int, const c128*, const c128*, long long, float*, double*, int, int,
                                     cudaStream_t);
@@ -89,10 +89,10 @@ void launch_sigma_conv_chunk(int kk0, int nkk, int nsig, int NBd, const int* nk,
   int total = nkk * nsig * nw;
   size_t smem = 2 * nw * sizeof(double);
   if (fp64)
-    k_sigma_conv<double><<<(total + 127) / 128, 128, smem, st>>>(nkk, kk0, nsig, NBd, nk[0], nk[1], nk[2], q, eps,
+    ++::gw::g_launch_count, k_sigma_conv<double><<<(total + 127) / 128, 128, smem, st>>>(nkk, kk0, nsig, NBd, nk[0], nk[1], nk[2], q, eps,
                                                                  mu, S_f, S_d, freq, gw, nw, pref, sigma);
   else
-    k_sigma_conv<float><<<(total + 127) / 128, 128, smem, st>>>(nkk, kk0, nsig, NBd, nk[0], nk[1], nk[2], q, eps,
+    ++::gw::g_launch_count, k_sigma_conv<float><<<(total + 127) / 128, 128, smem, st>>>(nkk, kk0, nsig, NBd, nk[0], nk[1], nk[2], q, eps,
                                                                 mu, S_f, S_d, freq, gw, nw, pref, sigma);
 }
 
@@ -214,7 +214,7 @@ __global__ void k_qp(int NK, int nsig, int NBd, int sig_lo, int nw, const c128* 
 void launch_qp(int NK, int nsig, int NBd, int sig_lo, int nw, const c128* sigma, const double* dxv, const double* eps,
                const double* mu, const double* freq, double* e_qp, int* conv, cudaStream_t st) {
   int total = NK * nsig;
-  k_qp<<<(total + 63) / 64, 64, 0, st>>>(NK, nsig, NBd, sig_lo, nw, sigma, dxv, eps, mu, freq, e_qp, conv);
+  ++::gw::g_launch_count, k_qp<<<(total + 63) / 64, 64, 0, st>>>(NK, nsig, NBd, sig_lo, nw, sigma, dxv, eps, mu, freq, e_qp, conv);
 }
 
 }  // namespace gw

@@ -1,14 +1,22 @@
-// Step (b) on the 5th-generation tensor cores: chi0(q, i w) as a weighted Hermitian rank-K
-// update in split precision (Eq. chi0_matrix, Hermitised, occupations restored):
+// Tensor-core (tcgen05) split-precision complex contractions of the G0W0 hot path.
 //
-//   chi0_{mu nu}(w) = scale * sum_r w_w(D_r) M^mu_r conj(M^nu_r),   w_w(D) = 2 D / (w^2 + D^2),
-//
-// r = (k, i occ, a unocc). Real form: with y = w M^mu (A side) and b = M^nu (B side), every
-// operand row interleaving (re, im) along K,
-//   Re chi0 = sum_r (y_re b_re + y_im b_im) = A . B1^T,  B1 = (b_re,  b_im),
-//   Im chi0 = sum_r (y_im b_re - y_re b_im) = A . B2^T,  B2 = (-b_im, b_re),
+// One kernel, two modes, both of the form  out_{m n} = sum_r y^m_r conj(b^n_r)  with
+//   y^m_r = w(r) x^m_r  (A side: rows of an fp32 plane, weight fused into the operand load)
+//   b^n_r               (B side: split planes streamed by TMA)
+// and every operand row interleaving (re, im) along K. Real form:
+//   Re out = sum_r (y_re b_re + y_im b_im) = A . B1^T,  B1 = (b_re,  b_im),
+//   Im out = sum_r (y_im b_re - y_re b_im) = A . B2^T,  B2 = (-b_im, b_re),
 // so one MMA against the stacked operand [B1; B2] (N = 2 x 64) yields Re and Im columns.
-// Operands are split into pieces (BF16: h + m + l, TF32: h + l) and the products of combined
+//
+// MODE 0, step (b), Eq. chi0_matrix (Hermitised, occupations restored):
+//   chi0_{mu nu}(w) = scale * sum_r w_w(D_r) M^mu_r conj(M^nu_r),  w_w(D) = 2 D / (w^2 + D^2),
+//   r = (k, i occ, a unocc); lower tiles only, FP64 accumulation into chi0[w].
+// MODE 1, step (d), Eq. GW_selfe_element with W^c:
+//   U_{r nu} = sum_mu a_{r mu} W^c_{mu nu}(w') = sum_mu a_{r mu} conj(W^c_{nu mu})  (W^c Hermitian),
+//   S_r(w') = Re sum_nu U_{r nu} conj(a_{r nu}),  a_r = C^mu_{nm}(k, k-q);  the row dot is
+//   fused into the epilogue and accumulated into S[r][w'].
+//
+// Operands are split into pieces (BF16: h + m + l, TF32: h + l); the products of combined
 // order >= 2^-16 (BF16: hh, hm, mh, hl, lh, mm) or 2^-11 (TF32: hh, hl, lh) are accumulated.
 //
 // Accumulation. The tensor-core FP32 accumulator rounds every addition toward zero, which
@@ -16,13 +24,13 @@
 //   * hh goes to accumulator D1, which is drained after every stage (4 MMAs per output)
 //     into FP32 running sums held in registers by the epilogue warps (round to nearest);
 //   * the correction products (2^-8 smaller) go to D2, drained once per segment;
-//   * after each segment the running sums are added in FP64 into the output.
+//   * after each segment the running sums are added in FP64 into the output (MODE 0), or
+//     dotted with a and added to S (MODE 1, one segment).
 //
 // Data flow per CTA (one 128 x 64 complex output tile from the host tile list, one frequency):
 //   * warp 0 (TMA):  B1 / B2 pieces, 64 rows x 128 B each per stage, SWIZZLE_128B
-//   * warps 2-5:     A rows: read the fp32 plane of the tile's mu rows, multiply by the
-//                    Lorentzian weight, split, write the A pieces in the UMMA K-major
-//                    128B-swizzled layout (the weight is fused into the operand load)
+//   * warps 2-5:     A rows: read the fp32 plane, multiply by the weight, split, write the A
+//                    pieces in the UMMA K-major 128B-swizzled layout
 //   * warp 1:        one elected thread issues tcgen05.mma (M = 128, N = 128) into TMEM
 //   * warps 6-13:    epilogue (two warps per TMEM lane quadrant, 32 complex columns each)
 // All mbarrier waits are bounded; on expiry the kernel sets ST_TIMEOUT and unwinds.
@@ -43,7 +51,7 @@ constexpr int TILE = 128 * ROWB;                   // 16 KB: A piece (128 rows) 
 constexpr int HALF = 64 * ROWB;                    // 8 KB: B1 or B2 part of a B piece
 constexpr int SMEM_BYTES = 192 * 1024 + 1024 + 256;
 constexpr int NTHREADS = 448;
-constexpr int MAX_TILES = 4096;
+constexpr int MAX_TILES = 8192;
 constexpr long long WAIT_LIMIT = 4000000000LL;     // clock64 ticks (~2 s) per wait
 // TMEM columns: D1 buffers at 0 and 128 (re: +0..63, im: +64..127); D2 buffers at 256 and 384
 constexpr uint32_t D1_COL = 0, D2_COL = 256, DBUF = 128;
@@ -54,8 +62,6 @@ template <bool TF32> struct Cfg {
   static constexpr int STAGES = (192 * 1024) / STAGE;
   static constexpr int RS = TF32 ? 16 : 32;        // complex pair rows per stage
 };
-
-__constant__ short2 c_tiles[MAX_TILES];            // (m0 / BM, n0 / BN) of each output tile
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -176,14 +182,19 @@ __device__ __forceinline__ float tf32_rn(float x) {
 
 __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t*>(&h); }
 
-struct Chi0Params {
-  int N, Kpad, nstage, seg;
-  const float* raw;   // [N][ldk] fp32 (re, im) planes of M, read by the A-side transform
-  long long ldk;      // elements per plane row
-  const float* wtab;  // [nw][Kpad] Lorentzian weights
-  int Kw;             // leading dim of wtab
+struct TcParams {
+  int Mrows, Ncols;   // A rows (mu or r), B rows (nu)
+  int nstage, seg;
+  const short2* tiles;  // (m0 / BM, n0 / BN) per blockIdx.x
+  const float* raw;   // [Mrows][ldk] fp32 (re, im) plane of the A side
+  long long ldk;      // floats per raw row
+  const float* wtab;  // weights: wtab[y * wstride + r]
+  long long wstride;
+  int brow_y;         // B row offset per blockIdx.y (MODE 1: one W^c per frequency)
   double scale;
-  c128* out;          // [nw][N][N]
+  c128* out;          // MODE 0: [nw][Ncols][Ncols]
+  float* S;           // MODE 1: [Mrows][nw]
+  int nw;
   int* status;
 };
 
@@ -191,8 +202,8 @@ struct Maps {
   CUtensorMap m[6];   // B1 pieces then B2 pieces
 };
 
-template <bool TF32>
-__global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc(const __grid_constant__ Maps maps, Chi0Params p) {
+template <bool TF32, int MODE>
+__global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps maps, TcParams p) {
   using C = Cfg<TF32>;
   constexpr int NP = C::NP, STAGES = C::STAGES, STAGE = C::STAGE, RS = C::RS;
   extern __shared__ uint8_t smem_raw[];
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc(const __grid_constant__
   uint32_t* tmem_base_p = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 9);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const short2 tl = c_tiles[blockIdx.x];
+  const short2 tl = p.tiles[blockIdx.x];
   const int m0 = tl.x * BM, n0 = tl.y * BN;
   const int w_i = blockIdx.y;
 
@@ -242,6 +253,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc(const __grid_constant__
   if (warp == 0) {
     // ---------------- TMA producer: B1 / B2 pieces ----------------
     if (lane == 0) {
+      const int yrow = w_i * p.brow_y + n0;
       for (int i = 0; i < nst; ++i) {
         const int s = i % STAGES;
         if (!mbar_wait(&empty[s], ((i / STAGES) & 1) ^ 1, p.status)) break;
@@ -250,8 +262,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc(const __grid_constant__
         const int x = i * (ROWB / (TF32 ? 4 : 2));
 #pragma unroll
         for (int pc = 0; pc < NP; ++pc) {
-          tma_load_2d(st + pc * TILE, &maps.m[pc], &full_b[s], x, n0);              // B1 rows 0..63
-          tma_load_2d(st + pc * TILE + HALF, &maps.m[NP + pc], &full_b[s], x, n0);  // B2 rows 64..127
+          tma_load_2d(st + pc * TILE, &maps.m[pc], &full_b[s], x, yrow);              // B1 rows 0..63
+          tma_load_2d(st + pc * TILE + HALF, &maps.m[NP + pc], &full_b[s], x, yrow);  // B2 rows 64..127
         }
       }
     }
@@ -302,15 +314,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc(const __grid_constant__
   } else if (warp >= 2 && warp <= 5) {
     // ---------------- transform: weighted, split A operand ----------------
     const int row = threadIdx.x - 64;          // 0..127
-    const int mu = m0 + row;
-    const float* wrow = p.wtab + (long long)w_i * p.Kw;
+    const int m = m0 + row;
+    const float* wrow = p.wtab + (long long)w_i * p.wstride;
     for (int i = 0; i < nst; ++i) {
       const int s = i % STAGES;
       if (!mbar_wait(&empty[s], ((i / STAGES) & 1) ^ 1, p.status)) break;
       uint8_t* at = smem + s * STAGE + NP * TILE;
       const int r0 = i * RS;
-      if (mu < p.N) {
-        const float4* g = reinterpret_cast<const float4*>(p.raw + (long long)mu * p.ldk + 2LL * r0);
+      if (m < p.Mrows) {
+        const float4* g = reinterpret_cast<const float4*>(p.raw + (long long)m * p.ldk + 2LL * r0);
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
           uint32_t o[NP][4];
@@ -340,11 +352,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc(const __grid_constant__
               const __nv_bfloat162 h = __floats2bfloat162_rn(yr, yi);
               const float2 hf = __bfloat1622float2(h);
               const float rr = yr - hf.x, ri = yi - hf.y;
-              const __nv_bfloat162 m = __floats2bfloat162_rn(rr, ri);
-              const float2 mf = __bfloat1622float2(m);
+              const __nv_bfloat162 mm = __floats2bfloat162_rn(rr, ri);
+              const float2 mf = __bfloat1622float2(mm);
               const __nv_bfloat162 l = __floats2bfloat162_rn(rr - mf.x, ri - mf.y);
               o[0][q] = bf2_bits(h);
-              o[1][q] = bf2_bits(m);
+              o[1][q] = bf2_bits(mm);
               o[NP - 1][q] = bf2_bits(l);
             }
           }
@@ -366,11 +378,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc(const __grid_constant__
       mbar_arrive(&full_a[s]);
     }
   } else {
-    // ---------------- epilogue: drain D1 per stage, D2 per segment, FP64 flush ----------------
+    // ---------------- epilogue: drain D1 per stage, D2 per segment, flush ----------------
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
     const int half = (warp - 6) >> 2;          // output columns half*32 .. half*32+31
     const int row = quad * 32 + lane;
-    const int mu = m0 + row;
+    const int m = m0 + row;
+    const int c0 = n0 + half * 32;
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     float sr[32], si[32];
 #pragma unroll
@@ -411,17 +424,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0_tc(const __grid_constant__
         }
         tc_fence_before();
         mbar_arrive(&t2empty[b2]);
-        if (mu < p.N) {
-          c128* orow = p.out + ((long long)w_i * p.N + mu) * p.N + n0 + half * 32;
-          const int nmax = p.N - (n0 + half * 32);
+        const int nmax = p.Ncols - c0;
+        if constexpr (MODE == 0) {
+          if (m < p.Mrows) {
+            c128* orow = p.out + ((long long)w_i * p.Ncols + m) * p.Ncols + c0;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            if (j < nmax) {
-              c128 o = orow[j];
-              o.re += p.scale * (double)sr[j];
-              o.im += p.scale * (double)si[j];
-              orow[j] = o;
+            for (int j = 0; j < 32; ++j) {
+              if (j < nmax) {
+                c128 o = orow[j];
+                o.re += p.scale * (double)sr[j];
+                o.im += p.scale * (double)si[j];
+                orow[j] = o;
+              }
             }
+          }
+        } else {
+          if (m < p.Mrows) {
+            // S_r += Re sum_nu U_{r nu} conj(a_{r nu}) over this thread's 32 columns
+            const float* arow = p.raw + (long long)m * p.ldk + 2LL * c0;
+            float acc = 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              if (j < nmax) {
+                const float2 a = *reinterpret_cast<const float2*>(arow + 2 * j);
+                acc = fmaf(sr[j], a.x, fmaf(si[j], a.y, acc));
+              }
+            }
+            atomicAdd(p.S + (long long)m * p.nw + w_i, acc);
           }
         }
 #pragma unroll
@@ -462,6 +491,48 @@ __global__ void k_herm_fill(int N, int nw, c128* chi0) {
   }
 }
 
+// B planes of W^c for the Sigma contraction: row (j, nu), K index 2 mu + {0, 1}:
+// B1 = split(Re W_{nu mu}, Im W_{nu mu}), B2 = split(-Im, Re); mu >= N is zero padding.
+__global__ void k_w_planes(int N, int nw, int Kpad, const c128* __restrict__ Wc, PlaneSet P, int tf32) {
+  const long long total = (long long)nw * N * Kpad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int mu = (int)(e % Kpad);
+    const long long row = e / Kpad;                 // j * N + nu
+    float v1[2] = {0.f, 0.f};
+    if (mu < N) {
+      const c128 w = Wc[row * N + mu];
+      v1[0] = (float)w.re;
+      v1[1] = (float)w.im;
+    }
+    const float v2[2] = {-v1[1], v1[0]};
+    const long long o = row * 2LL * Kpad + 2LL * mu;
+    for (int half = 0; half < 2; ++half) {
+      const float* v = half ? v2 : v1;
+      if (tf32) {
+        const float h0 = tf32_rn(v[0]), h1 = tf32_rn(v[1]);
+        *reinterpret_cast<float2*>(reinterpret_cast<float*>(P.b[2 * half]) + o) = make_float2(h0, h1);
+        *reinterpret_cast<float2*>(reinterpret_cast<float*>(P.b[2 * half + 1]) + o) = make_float2(v[0] - h0, v[1] - h1);
+      } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);
+        const float2 hf = __bfloat1622float2(h);
+        const float r0 = v[0] - hf.x, r1 = v[1] - hf.y;
+        const __nv_bfloat162 mm = __floats2bfloat162_rn(r0, r1);
+        const float2 mf = __bfloat1622float2(mm);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half]) + o) = h;
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half + 1]) + o) = mm;
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half + 2]) + o) = l;
+      }
+    }
+  }
+}
+
+__global__ void k_fill(float* p, long long n, float v) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    p[e] = v;
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -479,7 +550,7 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const void* base, int tf32, long long ldk, int rows, std::string& err) {
+bool make_map(CUtensorMap* m, const void* base, int tf32, long long ldk, long long rows, std::string& err) {
   EncodeTiledFn enc = get_encode();
   if (!enc) {
     err = "cuTensorMapEncodeTiled is unavailable";
@@ -500,81 +571,154 @@ bool make_map(CUtensorMap* m, const void* base, int tf32, long long ldk, int row
   return true;
 }
 
-// Lower-triangle tile list: every (mb, nb) with some nu <= mu inside, ordered by mb.
-int build_tiles(int N, std::vector<short2>& t) {
-  t.clear();
-  const int nmb = (N + BM - 1) / BM, nnb = (N + BN - 1) / BN;
-  for (int mb = 0; mb < nmb; ++mb)
-    for (int nb = 0; nb < nnb; ++nb) {
-      const int mu_max = std::min(N, (mb + 1) * BM) - 1;
-      if (nb * BN <= mu_max) t.push_back(make_short2((short)mb, (short)nb));
-    }
-  return (int)t.size();
-}
-
-template <bool TF32> void set_smem_attr() {
-  cudaFuncSetAttribute(k_chi0_tc<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+template <bool TF32, int MODE>
+gw_status launch_tc(const Maps& maps, const TcParams& p, int ntiles, int ny, cudaStream_t st, std::string& err) {
+  cudaFuncSetAttribute(k_tc<TF32, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  ++::gw::g_launch_count, k_tc<TF32, MODE><<<dim3(ntiles, ny), NTHREADS, SMEM_BYTES, st>>>(maps, p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("k_tc launch: ") + cudaGetErrorString(e);
+    return GW_ERR_CUDA;
+  }
+  return GW_OK;
 }
 
 }  // namespace
 
 bool tc_available() { return get_encode() != nullptr; }
 
-gw_status tc_chi0_run(const TcChi0Args& a, cudaStream_t st, std::string& err) {
-  const int RS = a.tf32 ? Cfg<true>::RS : Cfg<false>::RS;
-  const int NP = a.tf32 ? 2 : 3;
-  if (a.Kpad % 32 != 0 || a.N < 1) {
-    err = "tc_chi0: Kpad must be a multiple of 32";
-    return GW_ERR_ARG;
+TcWorkspace::~TcWorkspace() {
+  if (tiles) cudaFree(tiles);
+  if (ones) cudaFree(ones);
+}
+
+gw_status TcWorkspace::ensure(int ntiles_needed, int ones_needed, cudaStream_t st, std::string& err) {
+  if (ntiles_needed > tile_cap) {
+    if (tiles) cudaFree(tiles);
+    tiles = nullptr;
+    if (cudaMalloc(&tiles, sizeof(short2) * ntiles_needed) != cudaSuccess) {
+      err = "tile table allocation failed";
+      tile_cap = 0;
+      return GW_ERR_NOMEM;
+    }
+    tile_cap = ntiles_needed;
   }
-  std::vector<short2> tiles;
-  const int nt = build_tiles(a.N, tiles);
-  if (nt > MAX_TILES) {
-    err = "tc_chi0: n_aux too large for the tile table";
-    return GW_ERR_ARG;
-  }
-  Maps maps;
-  const long long ldk = 2LL * a.Kpad;
-  for (int i = 0; i < 2 * NP; ++i)
-    if (!make_map(&maps.m[i], a.bpl[i], a.tf32, ldk, a.N, err)) return GW_ERR_CUDA;
-  cudaError_t e = cudaMemcpyToSymbolAsync(c_tiles, tiles.data(), nt * sizeof(short2), 0, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) {
-    err = std::string("tc_chi0 tile table: ") + cudaGetErrorString(e);
-    return GW_ERR_CUDA;
-  }
-  k_weights<<<std::min<long long>(((long long)a.nw * a.Kpad + 255) / 256, 152 * 32), 256, 0, st>>>(
-      a.Kpad, a.nw, a.delta, a.freq, a.wtab);
-  Chi0Params p{};
-  p.N = a.N;
-  p.Kpad = a.Kpad;
-  p.nstage = a.Kpad / RS;
-  p.seg = std::max(1, a.seg_rows / RS);
-  p.raw = a.raw;
-  p.ldk = ldk;
-  p.wtab = a.wtab;
-  p.Kw = a.Kpad;
-  p.scale = a.scale;
-  p.out = a.chi0;
-  p.status = a.status;
-  dim3 grid(nt, a.nw);
-  if (a.tf32) {
-    set_smem_attr<true>();
-    k_chi0_tc<true><<<grid, NTHREADS, SMEM_BYTES, st>>>(maps, p);
-  } else {
-    set_smem_attr<false>();
-    k_chi0_tc<false><<<grid, NTHREADS, SMEM_BYTES, st>>>(maps, p);
-  }
-  e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    err = std::string("k_chi0_tc launch: ") + cudaGetErrorString(e);
-    return GW_ERR_CUDA;
+  if (ones_needed > ones_cap) {
+    if (ones) cudaFree(ones);
+    ones = nullptr;
+    if (cudaMalloc(&ones, sizeof(float) * ones_needed) != cudaSuccess) {
+      err = "weight table allocation failed";
+      ones_cap = 0;
+      return GW_ERR_NOMEM;
+    }
+    ++::gw::g_launch_count, k_fill<<<std::min(((long long)ones_needed + 255) / 256, 1024LL), 256, 0, st>>>(ones, ones_needed, 1.0f);
+    ones_cap = ones_needed;
   }
   return GW_OK;
 }
 
+gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std::string& err) {
+  const bool tf32 = a.tf32 != 0;
+  const int RS = tf32 ? Cfg<true>::RS : Cfg<false>::RS;
+  const int NP = tf32 ? 2 : 3;
+  if (a.Kpad % 32 != 0 || a.N < 1) {
+    err = "tc_chi0: Kpad must be a multiple of 32";
+    return GW_ERR_ARG;
+  }
+  // lower-triangle tiles: every (mb, nb) with some nu <= mu inside
+  std::vector<short2> tiles;
+  const int nmb = (a.N + BM - 1) / BM, nnb = (a.N + BN - 1) / BN;
+  for (int mb = 0; mb < nmb; ++mb)
+    for (int nb = 0; nb < nnb; ++nb)
+      if (nb * BN <= std::min(a.N, (mb + 1) * BM) - 1) tiles.push_back(make_short2((short)mb, (short)nb));
+  const int nt = (int)tiles.size();
+  gw_status s = ws.ensure(std::max(nt, MAX_TILES / 8), 1, st, err);
+  if (s != GW_OK) return s;
+  Maps maps;
+  const long long ldk = 2LL * a.Kpad;
+  for (int i = 0; i < 2 * NP; ++i)
+    if (!make_map(&maps.m[i], a.bpl[i], tf32, ldk, a.N, err)) return GW_ERR_CUDA;
+  cudaError_t e = cudaMemcpyAsync(ws.tiles, tiles.data(), nt * sizeof(short2), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    err = std::string("tc_chi0 tile table: ") + cudaGetErrorString(e);
+    return GW_ERR_CUDA;
+  }
+  ++::gw::g_launch_count, k_weights<<<std::min<long long>(((long long)a.nw * a.Kpad + 255) / 256, 152 * 32), 256, 0, st>>>(
+      a.Kpad, a.nw, a.delta, a.freq, a.wtab);
+  TcParams p{};
+  p.Mrows = a.N;
+  p.Ncols = a.N;
+  p.nstage = a.Kpad / RS;
+  p.seg = std::max(1, a.seg_rows / RS);
+  p.tiles = ws.tiles;
+  p.raw = a.raw;
+  p.ldk = ldk;
+  p.wtab = a.wtab;
+  p.wstride = a.Kpad;
+  p.brow_y = 0;
+  p.scale = a.scale;
+  p.out = a.chi0;
+  p.nw = a.nw;
+  p.status = a.status;
+  return tf32 ? launch_tc<true, 0>(maps, p, nt, a.nw, st, err) : launch_tc<false, 0>(maps, p, nt, a.nw, st, err);
+}
+
+gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, std::string& err) {
+  const bool tf32 = a.tf32 != 0;
+  const int RS = tf32 ? Cfg<true>::RS : Cfg<false>::RS;
+  const int NP = tf32 ? 2 : 3;
+  const int nmb = (a.R + BM - 1) / BM, nnb = (a.N + BN - 1) / BN;
+  const long long nt = (long long)nmb * nnb;
+  if (nt > 65535LL * 64) {
+    err = "tc_sigma: too many row tiles";
+    return GW_ERR_ARG;
+  }
+  std::vector<short2> tiles;
+  tiles.reserve(nt);
+  for (int mb = 0; mb < nmb; ++mb)
+    for (int nb = 0; nb < nnb; ++nb) tiles.push_back(make_short2((short)mb, (short)nb));
+  if (nmb > 32767) {
+    err = "tc_sigma: row chunk too large for the tile table";
+    return GW_ERR_ARG;
+  }
+  gw_status s = ws.ensure((int)nt, a.Kpad, st, err);
+  if (s != GW_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(ws.tiles, tiles.data(), nt * sizeof(short2), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    err = std::string("tc_sigma tile table: ") + cudaGetErrorString(e);
+    return GW_ERR_CUDA;
+  }
+  Maps maps;
+  const long long ldk = 2LL * a.Kpad;
+  for (int i = 0; i < 2 * NP; ++i)
+    if (!make_map(&maps.m[i], a.bpl[i], tf32, ldk, (long long)a.nw * a.N, err)) return GW_ERR_CUDA;
+  TcParams p{};
+  p.Mrows = a.R;
+  p.Ncols = a.N;
+  p.nstage = a.Kpad / RS;
+  p.seg = p.nstage;           // one segment: K = n_aux is short
+  p.tiles = ws.tiles;
+  p.raw = a.raw;
+  p.ldk = ldk;
+  p.wtab = ws.ones;
+  p.wstride = 0;
+  p.brow_y = a.N;
+  p.scale = 1.0;
+  p.S = a.S;
+  p.nw = a.nw;
+  p.status = a.status;
+  return tf32 ? launch_tc<true, 1>(maps, p, (int)nt, a.nw, st, err)
+              : launch_tc<false, 1>(maps, p, (int)nt, a.nw, st, err);
+}
+
+void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st) {
+  const long long total = (long long)nw * N * Kpad;
+  ++::gw::g_launch_count, k_w_planes<<<std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, st>>>(N, nw, Kpad, Wc, P, tf32);
+}
+
 void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st) {
   const long long total = (long long)nw * N * N;
-  k_herm_fill<<<std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, st>>>(N, nw, chi0);
+  ++::gw::g_launch_count, k_herm_fill<<<std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, st>>>(N, nw, chi0);
 }
 
 }  // namespace gw

@@ -22,7 +22,7 @@ PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16}
 
 # every symbol include/gw.h declares
 EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_qp",
-           "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_last_error")
+           "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_kernel_launches", "gw_last_error")
 
 
 class GwError(RuntimeError):
@@ -78,6 +78,7 @@ def load():
     lib.gw_plan_freq.argtypes = [vp, dp, dp]
     lib.gw_plan_mu.argtypes = [vp, dp]
     lib.gw_plan_last_chi0_stats.argtypes = [vp, dp, dp]
+    lib.gw_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.gw_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "gw_last_error":
@@ -145,6 +146,12 @@ def gw_plan_mu(plan):
     m = ctypes.c_double()
     _check(load().gw_plan_mu(plan, ctypes.byref(m)))
     return m.value
+
+
+def gw_kernel_launches():
+    n = ctypes.c_uint64()
+    _check(load().gw_kernel_launches(ctypes.byref(n)))
+    return n.value
 
 
 def gw_plan_last_chi0_stats(plan):
