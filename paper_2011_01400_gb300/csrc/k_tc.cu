@@ -1,6 +1,6 @@
 // Tensor-core (tcgen05) split-precision complex contractions of the G0W0 hot path.
 //
-// One kernel, two modes, both of the form  out_{m n} = sum_r y^m_r conj(b^n_r)  with
+// One persistent kernel, two modes, both of the form  out_{m n} = sum_r y^m_r conj(b^n_r)  with
 //   y^m_r = w(r) x^m_r  (A side: rows of an fp32 plane, weight fused into the operand load)
 //   b^n_r               (B side: split planes streamed by TMA)
 // and every operand row interleaving (re, im) along K. Real form:
@@ -25,20 +25,28 @@
 //     into FP32 running sums held in registers by the epilogue warps (round to nearest);
 //   * the correction products (2^-8 smaller) go to D2, drained once per segment;
 //   * after each segment the running sums are added in FP64 into the output (MODE 0), or
-//     dotted with a and added to S (MODE 1, one segment).
+//     dotted with a and added to S (MODE 1, one segment per work item).
 //
-// Data flow per CTA (one 128 x 64 complex output tile from the host tile list, one frequency):
-//   * warp 0 (TMA):  B1 / B2 pieces, 64 rows x 128 B each per stage, SWIZZLE_128B
-//   * warps 2-5:     A rows: read the fp32 plane, multiply by the weight, split, write the A
-//                    pieces in the UMMA K-major 128B-swizzled layout
-//   * warp 1:        one elected thread issues tcgen05.mma (M = 128, N = 128) into TMEM
-//   * warps 6-13:    epilogue (two warps per TMEM lane quadrant, 32 complex columns each)
+// Work distribution: one CTA per SM, each walking a static list of work items (output tile,
+// frequency); all pipelines (barrier phases, TMEM buffers) run on across items. Item order
+// keeps the data of concurrently running CTAs shared in L2 (MODE 0: frequency fastest; MODE 1:
+// column block fastest, then frequency, then row block).
+//
+// Roles (480 threads):
+//   * warp 0 (TMA):   B1 / B2 pieces, 64 rows x 128 B each per stage, SWIZZLE_128B
+//   * warp 14 (TMA):  A rows of the fp32 plane, 128 rows x 128 B per slot, into a ring that runs
+//                     ahead of the transform
+//   * warps 2-5:      transform: rebuild y = w x from the ring, split, write the A pieces in the
+//                     UMMA K-major 128B-swizzled layout
+//   * warp 1:         one elected thread issues tcgen05.mma (M = 128, N = 128) into TMEM
+//   * warps 6-13:     epilogue (two warps per TMEM lane quadrant, 32 complex columns each)
 // All mbarrier waits are bounded; on expiry the kernel sets ST_TIMEOUT and unwinds.
 #include "gw_internal.h"
 
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <cstdlib>
 #include <vector>
 
 namespace gw {
@@ -49,8 +57,8 @@ constexpr int BM = 128, BN = 64;                   // complex output tile
 constexpr int ROWB = 128;                          // bytes per operand row per stage (one swizzle atom)
 constexpr int TILE = 128 * ROWB;                   // 16 KB: A piece (128 rows) or B piece ([B1; B2], 128 rows)
 constexpr int HALF = 64 * ROWB;                    // 8 KB: B1 or B2 part of a B piece
-constexpr int SMEM_BYTES = 192 * 1024 + 1024 + 256;
-constexpr int NTHREADS = 448;
+constexpr int RAW = 128 * ROWB;                    // 16 KB: one ring slot = 16 complex pairs of 128 A rows
+constexpr int NTHREADS = 480;
 constexpr int MAX_TILES = 8192;
 constexpr long long WAIT_LIMIT = 4000000000LL;     // clock64 ticks (~2 s) per wait
 // TMEM columns: D1 buffers at 0 and 128 (re: +0..63, im: +64..127); D2 buffers at 256 and 384
@@ -59,9 +67,15 @@ constexpr uint32_t D1_COL = 0, D2_COL = 256, DBUF = 128;
 template <bool TF32> struct Cfg {
   static constexpr int NP = TF32 ? 2 : 3;          // pieces per operand
   static constexpr int STAGE = 2 * NP * TILE;      // B pieces then A pieces
-  static constexpr int STAGES = (192 * 1024) / STAGE;
-  static constexpr int RS = TF32 ? 16 : 32;        // complex pair rows per stage
+  static constexpr int STAGES = 2;
+  static constexpr int RPS = TF32 ? 1 : 2;         // ring slots per stage
+  static constexpr int RING = TF32 ? 4 : 2;        // ring slots
+  static constexpr int RS = 16 * RPS;              // complex pair rows per stage
+  static constexpr int BAR_OFF = STAGES * STAGE + RING * RAW;
+  static constexpr int SMEM = BAR_OFF + 256 + 1024;
 };
+static_assert(Cfg<false>::SMEM <= 232448, "shared memory budget");
+static_assert(Cfg<true>::SMEM <= 232448, "shared memory budget");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -184,31 +198,49 @@ __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 h) { return *reinter
 
 struct TcParams {
   int Mrows, Ncols;   // A rows (mu or r), B rows (nu)
-  int nstage, seg;
-  const short2* tiles;  // (m0 / BM, n0 / BN) per blockIdx.x
-  const float* raw;   // [Mrows][ldk] fp32 (re, im) plane of the A side
+  int nstage, seg;    // stages per work item; stages per promotion segment
+  int n_items, nw, nnb;
+  const short2* tiles;  // MODE 0: (m0 / BM, n0 / BN) per tile; work item = tile * nw + w
+  const float* raw;   // [Mrows][ldk] fp32 (re, im) plane of the A side (for the MODE 1 row dot)
   long long ldk;      // floats per raw row
-  const float* wtab;  // weights: wtab[y * wstride + r]
+  const float* wtab;  // weights: wtab[w * wstride + r]
   long long wstride;
-  int brow_y;         // B row offset per blockIdx.y (MODE 1: one W^c per frequency)
+  int brow_y;         // B row offset per frequency (MODE 1: one W^c per frequency)
   double scale;
   c128* out;          // MODE 0: [nw][Ncols][Ncols]
   float* S;           // MODE 1: [Mrows][nw]
-  int nw;
   int* status;
 };
 
 struct Maps {
-  CUtensorMap m[6];   // B1 pieces then B2 pieces
+  CUtensorMap b[6];   // B1 pieces then B2 pieces
+  CUtensorMap raw;    // A-side fp32 plane, 32 floats x 128 rows per box
 };
+
+template <int MODE>
+__device__ __forceinline__ void decode_item(const TcParams& p, int item, int& m0, int& n0, int& w) {
+  if constexpr (MODE == 0) {
+    const short2 t = p.tiles[item / p.nw];
+    w = item % p.nw;
+    m0 = t.x * BM;
+    n0 = t.y * BN;
+  } else {
+    const int nb = item % p.nnb;
+    const int rest = item / p.nnb;
+    w = rest % p.nw;
+    m0 = (rest / p.nw) * BM;
+    n0 = nb * BN;
+  }
+}
 
 template <bool TF32, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps maps, TcParams p) {
   using C = Cfg<TF32>;
-  constexpr int NP = C::NP, STAGES = C::STAGES, STAGE = C::STAGE, RS = C::RS;
+  constexpr int NP = C::NP, STAGES = C::STAGES, STAGE = C::STAGE, RS = C::RS, RPS = C::RPS, RING = C::RING;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint8_t* ring = smem + STAGES * STAGE;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
   uint64_t* full_b = bars;                   // [STAGES]
   uint64_t* full_a = bars + STAGES;          // [STAGES]
   uint64_t* empty = bars + 2 * STAGES;       // [STAGES]
@@ -217,12 +249,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
   uint64_t* t2full = bars + 3 * STAGES + 4;  // [2] D2 of a segment ready
   uint64_t* t2empty = bars + 3 * STAGES + 6; // [2] D2 drained
   uint64_t* done = bars + 3 * STAGES + 8;
-  uint32_t* tmem_base_p = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 9);
+  uint64_t* rfull = bars + 3 * STAGES + 9;           // [RING]
+  uint64_t* rempty = bars + 3 * STAGES + 9 + RING;   // [RING]
+  uint32_t* tmem_base_p = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 9 + 2 * RING);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const short2 tl = p.tiles[blockIdx.x];
-  const int m0 = tl.x * BM, n0 = tl.y * BN;
-  const int w_i = blockIdx.y;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -235,6 +266,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
       mbar_init(&t1empty[b], 256);
       mbar_init(&t2full[b], 1);
       mbar_init(&t2empty[b], 256);
+    }
+    for (int r = 0; r < RING; ++r) {
+      mbar_init(&rfull[r], 1);
+      mbar_init(&rempty[r], 128);
     }
     mbar_init(done, 1);
     fence_mbar_init();
@@ -253,17 +288,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
   if (warp == 0) {
     // ---------------- TMA producer: B1 / B2 pieces ----------------
     if (lane == 0) {
-      const int yrow = w_i * p.brow_y + n0;
-      for (int i = 0; i < nst; ++i) {
-        const int s = i % STAGES;
-        if (!mbar_wait(&empty[s], ((i / STAGES) & 1) ^ 1, p.status)) break;
-        uint8_t* st = smem + s * STAGE;
-        mbar_arrive_expect_tx(&full_b[s], NP * TILE);
-        const int x = i * (ROWB / (TF32 ? 4 : 2));
+      uint32_t gs = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        int m0, n0, w;
+        decode_item<MODE>(p, item, m0, n0, w);
+        const int yrow = w * p.brow_y + n0;
+        for (int i = 0; i < nst; ++i, ++gs) {
+          const int s = gs % STAGES;
+          if (!mbar_wait(&empty[s], ((gs / STAGES) & 1) ^ 1, p.status)) { ok = false; break; }
+          uint8_t* st = smem + s * STAGE;
+          mbar_arrive_expect_tx(&full_b[s], NP * TILE);
+          const int x = i * (ROWB / (TF32 ? 4 : 2));
 #pragma unroll
-        for (int pc = 0; pc < NP; ++pc) {
-          tma_load_2d(st + pc * TILE, &maps.m[pc], &full_b[s], x, yrow);              // B1 rows 0..63
-          tma_load_2d(st + pc * TILE + HALF, &maps.m[NP + pc], &full_b[s], x, yrow);  // B2 rows 64..127
+          for (int pc = 0; pc < NP; ++pc) {
+            tma_load_2d(st + pc * TILE, &maps.b[pc], &full_b[s], x, yrow);              // B1 rows 0..63
+            tma_load_2d(st + pc * TILE + HALF, &maps.b[NP + pc], &full_b[s], x, yrow);  // B2 rows 64..127
+          }
+        }
+      }
+    }
+  } else if (warp == 14) {
+    // ---------------- TMA producer: A rows of the fp32 plane into the ring ----------------
+    if (lane == 0) {
+      uint32_t gr = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        int m0, n0, w;
+        decode_item<MODE>(p, item, m0, n0, w);
+        for (int i = 0; i < nst * RPS; ++i, ++gr) {
+          const int slot = gr % RING;
+          if (!mbar_wait(&rempty[slot], ((gr / RING) & 1) ^ 1, p.status)) { ok = false; break; }
+          mbar_arrive_expect_tx(&rfull[slot], RAW);
+          tma_load_2d(ring + slot * RAW, &maps.raw, &rfull[slot], i * 32, m0);
         }
       }
     }
@@ -273,40 +330,50 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
       constexpr uint32_t fmt = TF32 ? 2u : 1u;
       const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)((2 * BN) >> 3) << 17) |
                              ((uint32_t)(BM >> 4) << 24);
-      for (int i = 0; i < nst; ++i) {
-        const int s = i % STAGES;
-        const int b = i & 1;
-        const int g = i / F, b2 = g & 1;
-        const bool seg_first = (i % F) == 0;
-        if (i >= 2 && !mbar_wait(&t1empty[b], ((i >> 1) - 1) & 1, p.status)) break;
-        if (seg_first && g >= 2 && !mbar_wait(&t2empty[b2], ((g >> 1) - 1) & 1, p.status)) break;
-        if (!mbar_wait(&full_b[s], (i / STAGES) & 1, p.status)) break;
-        if (!mbar_wait(&full_a[s], (i / STAGES) & 1, p.status)) break;
-        tc_fence_after();
-        const uint32_t bbase = smem_u32(smem + s * STAGE);
-        const uint32_t abase = bbase + NP * TILE;
-        const uint32_t d1 = tmem + D1_COL + b * DBUF;
-        const uint32_t d2 = tmem + D2_COL + b2 * DBUF;
+      uint32_t gs = 0, gseg = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        for (int i = 0; i < nst; ++i, ++gs) {
+          const int s = gs % STAGES;
+          const int b = gs & 1;
+          const int b2 = gseg & 1;
+          const bool seg_first = (i % F) == 0;
+          if (gs >= 2 && !mbar_wait(&t1empty[b], ((gs >> 1) - 1) & 1, p.status)) { ok = false; break; }
+          if (seg_first && gseg >= 2 && !mbar_wait(&t2empty[b2], ((gseg >> 1) - 1) & 1, p.status)) {
+            ok = false;
+            break;
+          }
+          if (!mbar_wait(&full_b[s], (gs / STAGES) & 1, p.status)) { ok = false; break; }
+          if (!mbar_wait(&full_a[s], (gs / STAGES) & 1, p.status)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t bbase = smem_u32(smem + s * STAGE);
+          const uint32_t abase = bbase + NP * TILE;
+          const uint32_t d1 = tmem + D1_COL + b * DBUF;
+          const uint32_t d2 = tmem + D2_COL + b2 * DBUF;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint32_t ko = kk * 32;
-          const uint32_t acc1 = kk == 0 ? 0u : 1u;
-          const uint32_t acc2 = (seg_first && kk == 0) ? 0u : 1u;
-          const uint64_t A0 = sdesc(abase + ko), B0 = sdesc(bbase + ko);
-          const uint64_t A1 = sdesc(abase + TILE + ko), B1 = sdesc(bbase + TILE + ko);
-          mma<TF32>(d1, A0, B0, idesc, acc1);
-          mma<TF32>(d2, A0, B1, idesc, acc2);
-          mma<TF32>(d2, A1, B0, idesc, 1u);
-          if constexpr (NP == 3) {
-            const uint64_t A2 = sdesc(abase + 2 * TILE + ko), B2 = sdesc(bbase + 2 * TILE + ko);
-            mma<TF32>(d2, A0, B2, idesc, 1u);
-            mma<TF32>(d2, A2, B0, idesc, 1u);
-            mma<TF32>(d2, A1, B1, idesc, 1u);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint32_t ko = kk * 32;
+            const uint32_t acc1 = kk == 0 ? 0u : 1u;
+            const uint32_t acc2 = (seg_first && kk == 0) ? 0u : 1u;
+            const uint64_t A0 = sdesc(abase + ko), B0 = sdesc(bbase + ko);
+            const uint64_t A1 = sdesc(abase + TILE + ko), B1 = sdesc(bbase + TILE + ko);
+            mma<TF32>(d1, A0, B0, idesc, acc1);
+            mma<TF32>(d2, A0, B1, idesc, acc2);
+            mma<TF32>(d2, A1, B0, idesc, 1u);
+            if constexpr (NP == 3) {
+              const uint64_t A2 = sdesc(abase + 2 * TILE + ko), B2 = sdesc(bbase + 2 * TILE + ko);
+              mma<TF32>(d2, A0, B2, idesc, 1u);
+              mma<TF32>(d2, A2, B0, idesc, 1u);
+              mma<TF32>(d2, A1, B1, idesc, 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+          mma_commit(&t1full[b]);
+          if ((i % F) == F - 1 || i == nst - 1) {
+            mma_commit(&t2full[b2]);
+            ++gseg;
           }
         }
-        mma_commit(&empty[s]);
-        mma_commit(&t1full[b]);
-        if ((i % F) == F - 1 || i == nst - 1) mma_commit(&t2full[b2]);
       }
       mma_commit(done);
       mbar_wait(done, 0, p.status);
@@ -314,105 +381,111 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
   } else if (warp >= 2 && warp <= 5) {
     // ---------------- transform: weighted, split A operand ----------------
     const int row = threadIdx.x - 64;          // 0..127
-    const int m = m0 + row;
-    const float* wrow = p.wtab + (long long)w_i * p.wstride;
-    for (int i = 0; i < nst; ++i) {
-      const int s = i % STAGES;
-      if (!mbar_wait(&empty[s], ((i / STAGES) & 1) ^ 1, p.status)) break;
-      uint8_t* at = smem + s * STAGE + NP * TILE;
-      const int r0 = i * RS;
-      if (m < p.Mrows) {
-        const float4* g = reinterpret_cast<const float4*>(p.raw + (long long)m * p.ldk + 2LL * r0);
+    uint32_t gs = 0, gr = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      int m0, n0, w;
+      decode_item<MODE>(p, item, m0, n0, w);
+      const float* wrow = p.wtab + (long long)w * p.wstride;
+      for (int i = 0; i < nst; ++i, ++gs) {
+        const int s = gs % STAGES;
+        if (!mbar_wait(&empty[s], ((gs / STAGES) & 1) ^ 1, p.status)) { ok = false; break; }
+        uint8_t* at = smem + s * STAGE + NP * TILE;
+        for (int h = 0; h < RPS; ++h, ++gr) {
+          const int slot = gr % RING;
+          if (!mbar_wait(&rfull[slot], (gr / RING) & 1, p.status)) { ok = false; break; }
+          // this thread's row: 16 complex pairs (8 chunks of 16 B, 128B-swizzled by TMA)
+          float x[32];
+          const uint8_t* rs = ring + slot * RAW;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          uint32_t o[NP][4];
+          for (int c = 0; c < 8; ++c) {
+            const float4 v = *reinterpret_cast<const float4*>(rs + swz(row, c));
+            x[4 * c] = v.x;
+            x[4 * c + 1] = v.y;
+            x[4 * c + 2] = v.z;
+            x[4 * c + 3] = v.w;
+          }
+          // order these generic-proxy reads before the TMA (async-proxy) refill of the slot
+          fence_proxy_async();
+          mbar_arrive(&rempty[slot]);
+          const int r0 = i * RS + 16 * h;      // first pair row of this slot
           if constexpr (TF32) {
-            // 16-B chunk c = 2 complex pairs
-            const float4 v = __ldg(g + c);
-            const float x[4] = {v.x, v.y, v.z, v.w};
+            // A row = 16 pairs = 8 chunks of 2 pairs
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-              const float wt = wrow[r0 + 2 * c + q];
+            for (int c = 0; c < 8; ++c) {
+              uint32_t o0[4], o1[4];
 #pragma unroll
-              for (int e = 0; e < 2; ++e) {
-                const float y = wt * x[2 * q + e];
-                const float h = tf32_rn(y);
-                o[0][2 * q + e] = __float_as_uint(h);
-                o[1][2 * q + e] = __float_as_uint(y - h);
+              for (int q = 0; q < 2; ++q) {
+                const float wt = wrow[r0 + 2 * c + q];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                  const float y = wt * x[4 * c + 2 * q + e];
+                  const float hh = tf32_rn(y);
+                  o0[2 * q + e] = __float_as_uint(hh);
+                  o1[2 * q + e] = __float_as_uint(y - hh);
+                }
               }
+              const uint32_t off = swz(row, c);
+              *reinterpret_cast<uint4*>(at + off) = make_uint4(o0[0], o0[1], o0[2], o0[3]);
+              *reinterpret_cast<uint4*>(at + TILE + off) = make_uint4(o1[0], o1[1], o1[2], o1[3]);
             }
           } else {
-            // 16-B chunk c = 4 complex pairs (8 bf16)
-            const float4 v0 = __ldg(g + 2 * c), v1 = __ldg(g + 2 * c + 1);
-            const float x[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            // A row = 32 pairs = 8 chunks of 4 pairs; this slot fills chunks 4h .. 4h+3
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float wt = wrow[r0 + 4 * c + q];
-              const float yr = wt * x[2 * q], yi = wt * x[2 * q + 1];
-              const __nv_bfloat162 h = __floats2bfloat162_rn(yr, yi);
-              const float2 hf = __bfloat1622float2(h);
-              const float rr = yr - hf.x, ri = yi - hf.y;
-              const __nv_bfloat162 mm = __floats2bfloat162_rn(rr, ri);
-              const float2 mf = __bfloat1622float2(mm);
-              const __nv_bfloat162 l = __floats2bfloat162_rn(rr - mf.x, ri - mf.y);
-              o[0][q] = bf2_bits(h);
-              o[1][q] = bf2_bits(mm);
-              o[NP - 1][q] = bf2_bits(l);
+            for (int cc = 0; cc < 4; ++cc) {
+              uint32_t o[3][4];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const int pr = 4 * cc + q;     // pair within the slot
+                const float wt = wrow[r0 + pr];
+                const float yr = wt * x[2 * pr], yi = wt * x[2 * pr + 1];
+                const __nv_bfloat162 hh = __floats2bfloat162_rn(yr, yi);
+                const float2 hf = __bfloat1622float2(hh);
+                const float rr = yr - hf.x, ri = yi - hf.y;
+                const __nv_bfloat162 mm = __floats2bfloat162_rn(rr, ri);
+                const float2 mf = __bfloat1622float2(mm);
+                const __nv_bfloat162 ll = __floats2bfloat162_rn(rr - mf.x, ri - mf.y);
+                o[0][q] = bf2_bits(hh);
+                o[1][q] = bf2_bits(mm);
+                o[2][q] = bf2_bits(ll);
+              }
+              const uint32_t off = swz(row, 4 * h + cc);
+#pragma unroll
+              for (int pc = 0; pc < 3; ++pc)
+                *reinterpret_cast<uint4*>(at + pc * TILE + off) = make_uint4(o[pc][0], o[pc][1], o[pc][2], o[pc][3]);
             }
           }
-          const uint32_t off = swz(row, c);
-#pragma unroll
-          for (int pc = 0; pc < NP; ++pc)
-            *reinterpret_cast<uint4*>(at + pc * TILE + off) = make_uint4(o[pc][0], o[pc][1], o[pc][2], o[pc][3]);
         }
-      } else {
-        const uint4 z = make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const uint32_t off = swz(row, c);
-#pragma unroll
-          for (int pc = 0; pc < NP; ++pc) *reinterpret_cast<uint4*>(at + pc * TILE + off) = z;
-        }
+        if (!ok) break;
+        fence_proxy_async();
+        mbar_arrive(&full_a[s]);
       }
-      fence_proxy_async();
-      mbar_arrive(&full_a[s]);
     }
-  } else {
+  } else if (warp >= 6 && warp <= 13) {
     // ---------------- epilogue: drain D1 per stage, D2 per segment, flush ----------------
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
     const int half = (warp - 6) >> 2;          // output columns half*32 .. half*32+31
     const int row = quad * 32 + lane;
-    const int m = m0 + row;
-    const int c0 = n0 + half * 32;
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-    float sr[32], si[32];
+    uint32_t gs = 0, gseg = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+      int m0, n0, w;
+      decode_item<MODE>(p, item, m0, n0, w);
+      const int m = m0 + row;
+      const int c0 = n0 + half * 32;
+      float sr[32], si[32];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
-    for (int i = 0; i < nst; ++i) {
-      const int b = i & 1;
-      if (!mbar_wait(&t1full[b], (i >> 1) & 1, p.status)) break;
-      tc_fence_after();
-      {
-        uint32_t vr[32], vi[32];
-        const uint32_t t = tmem + lane_off + D1_COL + b * DBUF + half * 32;
-        tmem_ld32_nowait(t, vr);
-        tmem_ld32_nowait(t + BN, vi);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          sr[j] += __uint_as_float(vr[j]);
-          si[j] += __uint_as_float(vi[j]);
-        }
-      }
-      tc_fence_before();
-      mbar_arrive(&t1empty[b]);
-      if ((i % F) == F - 1 || i == nst - 1) {
-        const int g = i / F, b2 = g & 1;
-        if (!mbar_wait(&t2full[b2], (g >> 1) & 1, p.status)) break;
+      for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
+      for (int i = 0; i < nst; ++i, ++gs) {
+        const int b = gs & 1;
+        // every lane polls the barrier; reconverge before the warp-wide (.sync.aligned) TMEM loads
+        ok = __all_sync(0xffffffffu, mbar_wait(&t1full[b], (gs >> 1) & 1, p.status));
+        if (!ok) break;
         tc_fence_after();
         {
           uint32_t vr[32], vi[32];
-          const uint32_t t = tmem + lane_off + D2_COL + b2 * DBUF + half * 32;
+          const uint32_t t = tmem + lane_off + D1_COL + b * DBUF + half * 32;
           tmem_ld32_nowait(t, vr);
           tmem_ld32_nowait(t + BN, vi);
           tmem_wait_ld();
@@ -423,38 +496,57 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
           }
         }
         tc_fence_before();
-        mbar_arrive(&t2empty[b2]);
-        const int nmax = p.Ncols - c0;
-        if constexpr (MODE == 0) {
-          if (m < p.Mrows) {
-            c128* orow = p.out + ((long long)w_i * p.Ncols + m) * p.Ncols + c0;
+        mbar_arrive(&t1empty[b]);
+        if ((i % F) == F - 1 || i == nst - 1) {
+          const int b2 = gseg & 1;
+          ok = __all_sync(0xffffffffu, mbar_wait(&t2full[b2], (gseg >> 1) & 1, p.status));
+          if (!ok) break;
+          tc_fence_after();
+          {
+            uint32_t vr[32], vi[32];
+            const uint32_t t = tmem + lane_off + D2_COL + b2 * DBUF + half * 32;
+            tmem_ld32_nowait(t, vr);
+            tmem_ld32_nowait(t + BN, vi);
+            tmem_wait_ld();
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              if (j < nmax) {
-                c128 o = orow[j];
-                o.re += p.scale * (double)sr[j];
-                o.im += p.scale * (double)si[j];
-                orow[j] = o;
-              }
+              sr[j] += __uint_as_float(vr[j]);
+              si[j] += __uint_as_float(vi[j]);
             }
           }
-        } else {
+          tc_fence_before();
+          mbar_arrive(&t2empty[b2]);
+          ++gseg;
+          const int nmax = p.Ncols - c0;
           if (m < p.Mrows) {
-            // S_r += Re sum_nu U_{r nu} conj(a_{r nu}) over this thread's 32 columns
-            const float* arow = p.raw + (long long)m * p.ldk + 2LL * c0;
-            float acc = 0.f;
+            if constexpr (MODE == 0) {
+              c128* orow = p.out + ((long long)w * p.Ncols + m) * p.Ncols + c0;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (j < nmax) {
-                const float2 a = *reinterpret_cast<const float2*>(arow + 2 * j);
-                acc = fmaf(sr[j], a.x, fmaf(si[j], a.y, acc));
+              for (int j = 0; j < 32; ++j) {
+                if (j < nmax) {
+                  c128 o = orow[j];
+                  o.re += p.scale * (double)sr[j];
+                  o.im += p.scale * (double)si[j];
+                  orow[j] = o;
+                }
               }
+            } else {
+              // S_r += Re sum_nu U_{r nu} conj(a_{r nu}) over this thread's 32 columns
+              const float* arow = p.raw + (long long)m * p.ldk + 2LL * c0;
+              float acc = 0.f;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                if (j < nmax) {
+                  const float2 a = *reinterpret_cast<const float2*>(arow + 2 * j);
+                  acc = fmaf(sr[j], a.x, fmaf(si[j], a.y, acc));
+                }
+              }
+              atomicAdd(p.S + (long long)m * p.nw + w, acc);
             }
-            atomicAdd(p.S + (long long)m * p.nw + w_i, acc);
           }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
         }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
       }
     }
   }
@@ -550,18 +642,21 @@ EncodeTiledFn get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const void* base, int tf32, long long ldk, long long rows, std::string& err) {
+// 2-D map over a row-major plane [rows][ldk] of 16-bit (bf16) or 32-bit (fp32/tf32) elements,
+// box = 128 B of one row x box_rows rows, 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* base, int four_byte, long long ldk, long long rows, int box_rows,
+              std::string& err) {
   EncodeTiledFn enc = get_encode();
   if (!enc) {
     err = "cuTensorMapEncodeTiled is unavailable";
     return false;
   }
-  const int esz = tf32 ? 4 : 2;
+  const int esz = four_byte ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(ldk * esz)};
-  cuuint32_t box[2] = {(cuuint32_t)(ROWB / esz), (cuuint32_t)BN};
+  cuuint32_t box[2] = {(cuuint32_t)(ROWB / esz), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  CUresult r = enc(m, four_byte ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -571,10 +666,22 @@ bool make_map(CUtensorMap* m, const void* base, int tf32, long long ldk, long lo
   return true;
 }
 
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
+}
+
 template <bool TF32, int MODE>
-gw_status launch_tc(const Maps& maps, const TcParams& p, int ntiles, int ny, cudaStream_t st, std::string& err) {
-  cudaFuncSetAttribute(k_tc<TF32, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  ++::gw::g_launch_count, k_tc<TF32, MODE><<<dim3(ntiles, ny), NTHREADS, SMEM_BYTES, st>>>(maps, p);
+gw_status launch_tc(const Maps& maps, const TcParams& p, cudaStream_t st, std::string& err) {
+  const int smem = Cfg<TF32>::SMEM;
+  cudaFuncSetAttribute(k_tc<TF32, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int grid = std::min(p.n_items, num_sms());
+  ++::gw::g_launch_count, k_tc<TF32, MODE><<<grid, NTHREADS, smem, st>>>(maps, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("k_tc launch: ") + cudaGetErrorString(e);
@@ -632,12 +739,17 @@ gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std
     for (int nb = 0; nb < nnb; ++nb)
       if (nb * BN <= std::min(a.N, (mb + 1) * BM) - 1) tiles.push_back(make_short2((short)mb, (short)nb));
   const int nt = (int)tiles.size();
+  if (nt > MAX_TILES) {
+    err = "tc_chi0: n_aux too large for the tile table";
+    return GW_ERR_ARG;
+  }
   gw_status s = ws.ensure(std::max(nt, MAX_TILES / 8), 1, st, err);
   if (s != GW_OK) return s;
   Maps maps;
   const long long ldk = 2LL * a.Kpad;
   for (int i = 0; i < 2 * NP; ++i)
-    if (!make_map(&maps.m[i], a.bpl[i], tf32, ldk, a.N, err)) return GW_ERR_CUDA;
+    if (!make_map(&maps.b[i], a.bpl[i], tf32, ldk, a.N, BN, err)) return GW_ERR_CUDA;
+  if (!make_map(&maps.raw, a.raw, 1, ldk, a.N, BM, err)) return GW_ERR_CUDA;
   cudaError_t e = cudaMemcpyAsync(ws.tiles, tiles.data(), nt * sizeof(short2), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) {
     err = std::string("tc_chi0 tile table: ") + cudaGetErrorString(e);
@@ -650,6 +762,9 @@ gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std
   p.Ncols = a.N;
   p.nstage = a.Kpad / RS;
   p.seg = std::max(1, a.seg_rows / RS);
+  p.n_items = nt * a.nw;
+  p.nw = a.nw;
+  p.nnb = nnb;
   p.tiles = ws.tiles;
   p.raw = a.raw;
   p.ldk = ldk;
@@ -658,45 +773,39 @@ gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std
   p.brow_y = 0;
   p.scale = a.scale;
   p.out = a.chi0;
-  p.nw = a.nw;
   p.status = a.status;
-  return tf32 ? launch_tc<true, 0>(maps, p, nt, a.nw, st, err) : launch_tc<false, 0>(maps, p, nt, a.nw, st, err);
+  return tf32 ? launch_tc<true, 0>(maps, p, st, err) : launch_tc<false, 0>(maps, p, st, err);
 }
 
 gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, std::string& err) {
   const bool tf32 = a.tf32 != 0;
   const int RS = tf32 ? Cfg<true>::RS : Cfg<false>::RS;
   const int NP = tf32 ? 2 : 3;
+  if (a.Kpad % 32 != 0) {
+    err = "tc_sigma: Kpad must be a multiple of 32";
+    return GW_ERR_ARG;
+  }
   const int nmb = (a.R + BM - 1) / BM, nnb = (a.N + BN - 1) / BN;
-  const long long nt = (long long)nmb * nnb;
-  if (nt > 65535LL * 64) {
-    err = "tc_sigma: too many row tiles";
+  const long long items = (long long)nmb * nnb * a.nw;
+  if (items > 0x7fffffffLL) {
+    err = "tc_sigma: too many work items";
     return GW_ERR_ARG;
   }
-  std::vector<short2> tiles;
-  tiles.reserve(nt);
-  for (int mb = 0; mb < nmb; ++mb)
-    for (int nb = 0; nb < nnb; ++nb) tiles.push_back(make_short2((short)mb, (short)nb));
-  if (nmb > 32767) {
-    err = "tc_sigma: row chunk too large for the tile table";
-    return GW_ERR_ARG;
-  }
-  gw_status s = ws.ensure((int)nt, a.Kpad, st, err);
+  gw_status s = ws.ensure(1, a.Kpad, st, err);
   if (s != GW_OK) return s;
-  cudaError_t e = cudaMemcpyAsync(ws.tiles, tiles.data(), nt * sizeof(short2), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) {
-    err = std::string("tc_sigma tile table: ") + cudaGetErrorString(e);
-    return GW_ERR_CUDA;
-  }
   Maps maps;
   const long long ldk = 2LL * a.Kpad;
   for (int i = 0; i < 2 * NP; ++i)
-    if (!make_map(&maps.m[i], a.bpl[i], tf32, ldk, (long long)a.nw * a.N, err)) return GW_ERR_CUDA;
+    if (!make_map(&maps.b[i], a.bpl[i], tf32, ldk, (long long)a.nw * a.N, BN, err)) return GW_ERR_CUDA;
+  if (!make_map(&maps.raw, a.raw, 1, ldk, a.R, BM, err)) return GW_ERR_CUDA;
   TcParams p{};
   p.Mrows = a.R;
   p.Ncols = a.N;
   p.nstage = a.Kpad / RS;
-  p.seg = p.nstage;           // one segment: K = n_aux is short
+  p.seg = p.nstage;           // one segment per work item: K = n_aux is short
+  p.n_items = (int)items;
+  p.nw = a.nw;
+  p.nnb = nnb;
   p.tiles = ws.tiles;
   p.raw = a.raw;
   p.ldk = ldk;
@@ -705,10 +814,8 @@ gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, s
   p.brow_y = a.N;
   p.scale = 1.0;
   p.S = a.S;
-  p.nw = a.nw;
   p.status = a.status;
-  return tf32 ? launch_tc<true, 1>(maps, p, (int)nt, a.nw, st, err)
-              : launch_tc<false, 1>(maps, p, (int)nt, a.nw, st, err);
+  return tf32 ? launch_tc<true, 1>(maps, p, st, err) : launch_tc<false, 1>(maps, p, st, err);
 }
 
 void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st) {
