@@ -122,6 +122,14 @@ gw_status gw_screen(gw_plan plan, int32_t sys, int32_t q, gw_complex* wc_out);
  *            or NULL to accumulate into the plan's own buffer (zeroed at plan creation). */
 gw_status gw_sigma(gw_plan plan, int32_t sys, int32_t q, gw_complex* sigma_acc);
 
+/* The whole q loop of the G0W0 pass in one call: for every q on the mesh, chi0 (as gw_chi0),
+ * eps~ and W^c (as gw_screen) and the Sigma_c term (as gw_sigma), accumulated into sigma_acc
+ * (device [N_k][n_sigma][n_freq], caller zeroes it) or, if NULL, the plan's own accumulator.
+ * q points are processed in groups whose FP64 factorisations of eps~ run as one batched launch;
+ * the group buffers (about 8 GB at most) are allocated on the first call and kept by the plan.
+ * Results equal those of the per-q calls. Errors: as gw_chi0 / gw_screen / gw_sigma. */
+gw_status gw_g0w0(gw_plan plan, int32_t sys, gw_complex* sigma_acc);
+
 /* Quasiparticle energies: Sigma_c(i w) continued with the two-pole model
  * (p1 z + p0)/(z^2 + q1 z + q0) fitted by linear least squares on all n_freq points,
  * then E = eps_n + Re Sigma_c(E - mu) + dxv_n by Newton (tolerance 1e-10 Ha; linearised

@@ -168,9 +168,43 @@ struct gw_plan_s {
   c64* d_Vh32 = nullptr;      // FP32 copies of V^1/2 for the split-precision screen
   c64* d_Vb32 = nullptr;
   TcWorkspace tcws;
-  // timing of the chi0 contraction
+  // q-group buffers of gw_g0w0
+  c128 *g_chi0 = nullptr, *g_E = nullptr, *g_work = nullptr;
+  int qb = 0;
+  // timing of the chi0 contraction launches of the last call (CUDA events on the plan's stream)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  double last_chi0_ms = 0.0, last_chi0_flops = 0.0;
+  double last_chi0_ms = 0.0, last_chi0_flops = 0.0, chi0_flops_acc = 0.0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+  size_t ev_used = 0;
+  gw_status event_pair(cudaEvent_t& a, cudaEvent_t& b) {
+    if (ev_used == evs.size()) {
+      cudaEvent_t x, y;
+      if (cudaEventCreate(&x) != cudaSuccess || cudaEventCreate(&y) != cudaSuccess)
+        return fail(GW_ERR_CUDA, "cudaEventCreate failed");
+      evs.push_back({x, y});
+    }
+    a = evs[ev_used].first;
+    b = evs[ev_used].second;
+    ++ev_used;
+    return GW_OK;
+  }
+  void reset_timing() {
+    ev_used = 0;
+    chi0_flops_acc = 0.0;
+  }
+  gw_status collect_timing() {
+    double ms = 0.0;
+    for (size_t i = 0; i < ev_used; ++i) {
+      float t = 0.f;
+      cudaError_t e = cudaEventSynchronize(evs[i].second);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, evs[i].first, evs[i].second);
+      if (e != cudaSuccess) return fail(GW_ERR_CUDA, std::string("chi0 timing: ") + cudaGetErrorString(e));
+      ms += t;
+    }
+    last_chi0_ms = ms;
+    last_chi0_flops = chi0_flops_acc;
+    return GW_OK;
+  }
 };
 
 namespace {
@@ -563,6 +597,10 @@ gw_status gw_plan_destroy(gw_plan P) {
   for (void* a : P->allocs) cudaFree(a);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
+  for (auto& e : P->evs) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   delete P;
   return GW_OK;
 }
@@ -587,27 +625,31 @@ gw_status gw_plan_last_chi0_stats(gw_plan P, double* ms, double* flops) {
   return GW_OK;
 }
 
-gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
-  gw_status s;
-  if (!plan_ok(P, sys, &s)) return s;
-  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
+}  // extern "C"
+
+namespace {
+
+// chi0(q) into `chi0` ([nw][N][N], FP64). Records CUDA events around the contraction launches.
+gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
   cudaStream_t st = P->st;
   const int N = P->N, nw = P->nw;
   const size_t NN = (size_t)N * N;
   const c128* evec = reinterpret_cast<const c128*>(P->p.evec);
-  GW_CUDA(cudaMemsetAsync(P->d_chi0, 0, sizeof(c128) * NN * nw, st));
+  GW_CUDA(cudaMemsetAsync(chi0, 0, sizeof(c128) * NN * nw, st));
   const bool hw = P->p.head_wings && q == 0;
   if (hw) {
     std::vector<double> ones(nw, 1.0);
     GW_CUDA(cudaMemcpyAsync(P->d_head, ones.data(), nw * sizeof(double), cudaMemcpyHostToDevice, st));
+    GW_CUDA(cudaStreamSynchronize(st));
     GW_CUDA(cudaMemsetAsync(P->d_h, 0, sizeof(c128) * nw * N, st));
   }
   const double scale = -P->p.spin / P->NK;
   const int na = P->nunocc, nb = P->nocc;
-  float total_ms = 0.f;
   for (int kk0 = 0; kk0 < P->NK; kk0 += P->chi_nkk) {
     const int nkk = std::min(P->chi_nkk, P->NK - kk0);
     const int K = nkk * na * nb;
+    cudaEvent_t e0, e1;
+    GW_TRY(P->event_pair(e0, e1));
     launch_pairs(P->NK, P->NBd, P->p.nk, q, kk0, nkk, P->nocc, na, 0, nb, P->p.eps,
                  reinterpret_cast<const c128*>(P->p.pmom), P->p.qhat, P->d_delta, P->d_delta_f,
                  hw ? P->d_pq : nullptr, st);
@@ -615,9 +657,9 @@ gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
       c128* M = static_cast<c128*>(P->d_M);
       launch_mgen<double>(P->geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK,
                           P->nocc, na, 0, nb, M, 1, P->ldm, st);
-      GW_CUDA(cudaEventRecord(P->ev0, st));
-      launch_chi0_simt<double>(N, K, M, P->ldm, nullptr, P->d_delta, P->d_freq, nw, scale, P->d_chi0, st);
-      GW_CUDA(cudaEventRecord(P->ev1, st));
+      GW_CUDA(cudaEventRecord(e0, st));
+      launch_chi0_simt<double>(N, K, M, P->ldm, nullptr, P->d_delta, P->d_freq, nw, scale, chi0, st);
+      GW_CUDA(cudaEventRecord(e1, st));
       if (hw)
         launch_head_wings<double>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
                                   4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
@@ -647,20 +689,19 @@ gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
       a.freq = P->d_freq;
       a.nw = nw;
       a.scale = scale;
-      a.chi0 = P->d_chi0;
+      a.chi0 = chi0;
       a.tf32 = tf32;
       a.status = P->d_status;
       a.seg_rows = P->seg_rows;
       a.wtab = P->d_wtab;
       std::string err;
-      GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
-      GW_CUDA(cudaEventRecord(P->ev0, st));
+      GW_CUDA(cudaEventRecord(e0, st));
       gw_status ts = tc_chi0_run(a, P->tcws, st, err);
       if (ts != GW_OK) {
         P->err = 1;
         return fail(ts, err);
       }
-      GW_CUDA(cudaEventRecord(P->ev1, st));
+      GW_CUDA(cudaEventRecord(e1, st));
       if (hw) {
         c64* M = static_cast<c64*>(P->d_M);
         launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK,
@@ -668,29 +709,16 @@ gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
         launch_head_wings<float>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
                                  4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
       }
-      GW_TRY(read_status(P, "gw_chi0"));
     }
-    GW_TRY(check_launch(P, "gw_chi0"));
-    GW_CUDA(cudaEventSynchronize(P->ev1));
-    float ms = 0.f;
-    GW_CUDA(cudaEventElapsedTime(&ms, P->ev0, P->ev1));
-    total_ms += ms;
+    GW_TRY(check_launch(P, "chi0"));
   }
-  if (!P->fp64) tc_herm_fill(N, nw, P->d_chi0, st);
-  P->last_chi0_ms = total_ms;
-  P->last_chi0_flops = 8.0 * (double)P->NK * na * nb * ((double)N * (N + 1) / 2) * nw;
-  if (chi0_out)
-    GW_CUDA(cudaMemcpyAsync(chi0_out, P->d_chi0, sizeof(c128) * NN * nw, cudaMemcpyDeviceToDevice, st));
-  P->chi0_q = q;
-  P->wc_q = -1;
+  if (!P->fp64) tc_herm_fill(N, nw, chi0, st);
+  P->chi0_flops_acc += 8.0 * (double)P->NK * na * nb * ((double)N * (N + 1) / 2) * nw;
   return GW_OK;
 }
 
-gw_status gw_screen(gw_plan P, int32_t sys, int32_t q, gw_complex* wc_out) {
-  gw_status s;
-  if (!plan_ok(P, sys, &s)) return s;
-  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
-  if (P->chi0_q != q) return fail(GW_ERR_STATE, "gw_screen needs gw_chi0 for the same q first");
+// eps~(q) = 1 - V^1/2 chi0 V^1/2 (head and wings at q = 0) into E ([nw][N][N], FP64)
+gw_status eps_core(gw_plan_s* P, int q, const c128* chi0, c128* E) {
   cudaStream_t st = P->st;
   const int N = P->N, nw = P->nw;
   const long long NN = (long long)N * N;
@@ -699,61 +727,63 @@ gw_status gw_screen(gw_plan P, int32_t sys, int32_t q, gw_complex* wc_out) {
   const c128* Vin = hw ? P->d_Vb0 : Vh;     // V^1/2 entering eps~ (body only at q = 0)
   const c128 one{1, 0}, zero{0, 0}, mone{-1, 0};
   const c64 one32{1, 0}, zero32{0, 0}, mone32{-1, 0};
-  // FP32 scratch for the split-precision path: two halves of d_work and d_tmp
   c64* A32 = reinterpret_cast<c64*>(P->d_work);
   c64* B32 = A32 + NN * nw;
   c64* C32 = reinterpret_cast<c64*>(P->d_tmp);
-  const c64* Vh32 = P->fp64 ? nullptr : P->d_Vh32 + (long long)q * NN;
-  const c64* Vin32 = P->fp64 ? nullptr : (hw ? P->d_Vb32 : Vh32);
-  // eps~ = 1 - Vin chi0 Vin
   if (P->fp64) {
-    launch_zgemm<double>(N, N, N, one, P->d_chi0, N, NN, OP_N, Vin, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
-    launch_zgemm<double>(N, N, N, mone, Vin, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, P->d_E, N, NN, nw, st);
+    launch_zgemm<double>(N, N, N, one, chi0, N, NN, OP_N, Vin, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
+    launch_zgemm<double>(N, N, N, mone, Vin, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, E, N, NN, nw, st);
   } else {
-    launch_convert((int)(NN * nw), P->d_chi0, A32, st);
+    const c64* Vh32 = P->d_Vh32 + (long long)q * NN;
+    const c64* Vin32 = hw ? P->d_Vb32 : Vh32;
+    launch_convert((int)(NN * nw), chi0, A32, st);
     launch_zgemm<float>(N, N, N, one32, A32, N, NN, OP_N, Vin32, N, 0, OP_N, zero32, B32, N, NN, nw, st);
     launch_zgemm<float>(N, N, N, mone32, Vin32, N, 0, OP_N, B32, N, NN, OP_N, zero32, C32, N, NN, nw, st);
-    launch_convert_back((int)(NN * nw), C32, P->d_E, st);
+    launch_convert_back((int)(NN * nw), C32, E, st);
   }
-  launch_axpby_identity<double>(N, P->d_E, NN, nw, 1.0, st);
+  launch_axpby_identity<double>(N, E, NN, nw, 1.0, st);
   if (hw) {
-    // Vbh[w] = Vb0 h[w]  (stored in d_tmp rows), then the rank-2 head / wing correction
+    // Vbh[w] = Vb0 h[w], then the rank-2 head / wing correction
     launch_zgemm<double>(nw, N, N, one, P->d_h, N, 0, OP_N, P->d_Vb0, N, 0, OP_T, zero, P->d_tmp, N, 0, 1, st);
     const double c = (P->p.spin / P->NK) * std::sqrt(4.0 * M_PI / P->p.omega_cell);
-    launch_q0_correction(N, nw, P->d_E, P->d_x1, P->d_tmp, P->d_head, c, st);
+    launch_q0_correction(N, nw, E, P->d_x1, P->d_tmp, P->d_head, c, st);
   }
-  GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
-  launch_chol_inv_minus_I(N, P->d_E, nw, NN, P->d_work, P->d_status, st);
-  // W^c = Vh (eps~^-1 - 1) Vh
-  if (P->fp64) {
-    launch_zgemm<double>(N, N, N, one, P->d_E, N, NN, OP_N, Vh, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
-    launch_zgemm<double>(N, N, N, one, Vh, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, P->d_Wc, N, NN, nw, st);
-  } else {
-    launch_convert((int)(NN * nw), P->d_E, A32, st);
-    launch_zgemm<float>(N, N, N, one32, A32, N, NN, OP_N, Vh32, N, 0, OP_N, zero32, B32, N, NN, nw, st);
-    launch_zgemm<float>(N, N, N, one32, Vh32, N, 0, OP_N, B32, N, NN, OP_N, zero32, C32, N, NN, nw, st);
-    launch_convert_back((int)(NN * nw), C32, P->d_Wc, st);
-  }
-  GW_TRY(check_launch(P, "gw_screen"));
-  GW_TRY(read_status(P, "gw_screen"));
-  if (wc_out) GW_CUDA(cudaMemcpyAsync(wc_out, P->d_Wc, sizeof(c128) * NN * nw, cudaMemcpyDeviceToDevice, st));
-  P->wc_q = q;
-  return GW_OK;
+  return check_launch(P, "eps~");
 }
 
-gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
-  gw_status s;
-  if (!plan_ok(P, sys, &s)) return s;
-  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
-  if (P->wc_q != q) return fail(GW_ERR_STATE, "gw_sigma needs gw_screen for the same q first");
+// W^c(q) = V^1/2 X V^1/2 with X = eps~^-1 - 1 ([nw][N][N], FP64 in and out)
+gw_status w_core(gw_plan_s* P, int q, const c128* X, c128* Wc) {
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw;
+  const long long NN = (long long)N * N;
+  const c128* Vh = P->d_Vh + (long long)q * NN;
+  const c128 one{1, 0}, zero{0, 0};
+  const c64 one32{1, 0}, zero32{0, 0};
+  c64* A32 = reinterpret_cast<c64*>(P->d_work);
+  c64* B32 = A32 + NN * nw;
+  c64* C32 = reinterpret_cast<c64*>(P->d_tmp);
+  if (P->fp64) {
+    launch_zgemm<double>(N, N, N, one, X, N, NN, OP_N, Vh, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
+    launch_zgemm<double>(N, N, N, one, Vh, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, Wc, N, NN, nw, st);
+  } else {
+    const c64* Vh32 = P->d_Vh32 + (long long)q * NN;
+    launch_convert((int)(NN * nw), X, A32, st);
+    launch_zgemm<float>(N, N, N, one32, A32, N, NN, OP_N, Vh32, N, 0, OP_N, zero32, B32, N, NN, nw, st);
+    launch_zgemm<float>(N, N, N, one32, Vh32, N, 0, OP_N, B32, N, NN, OP_N, zero32, C32, N, NN, nw, st);
+    launch_convert_back((int)(NN * nw), C32, Wc, st);
+  }
+  return check_launch(P, "W^c");
+}
+
+// q term of Sigma_c from W^c(q), accumulated into sig ([N_k][n_sigma][nw])
+gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig) {
   cudaStream_t st = P->st;
   const int N = P->N, nw = P->nw, NBd = P->NBd, nsig = P->nsig;
   const long long NN = (long long)N * N;
   const c128* evec = reinterpret_cast<const c128*>(P->p.evec);
-  c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
   const double pref = -1.0 / (2.0 * M_PI * P->NK);
   const int tf32 = P->prec == GW_3XTF32;
-  if (!P->fp64) tc_w_planes(N, nw, P->Kx, P->d_Wc, P->d_Wpl, tf32, st);
+  if (!P->fp64) tc_w_planes(N, nw, P->Kx, Wc, P->d_Wpl, tf32, st);
   for (int kk0 = 0; kk0 < P->NK; kk0 += P->sig_nkk) {
     const int nkk = std::min(P->sig_nkk, P->NK - kk0);
     const int R = nkk * nsig * NBd;
@@ -763,8 +793,7 @@ gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
       launch_mgen<double>(P->geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk,
                           MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, N, 1, st);
       for (int j = 0; j < nw; ++j) {
-        launch_zgemm<double>(R, N, N, c128{1, 0}, A, N, 0, OP_N, P->d_Wc + j * NN, N, 0, OP_N, c128{0, 0}, U, N, 0,
-                             1, st);
+        launch_zgemm<double>(R, N, N, c128{1, 0}, A, N, 0, OP_N, Wc + j * NN, N, 0, OP_N, c128{0, 0}, U, N, 0, 1, st);
         launch_rowdot<double>(R, N, U, A, N, nullptr, P->d_S_d, j, nw, st);
       }
     } else {
@@ -792,10 +821,91 @@ gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
     }
     launch_sigma_conv_chunk(kk0, nkk, nsig, NBd, P->p.nk, q, P->p.eps, P->d_mu, P->d_S_f, P->d_S_d, P->d_freq,
                             P->d_fw, nw, pref, sig, P->fp64, st);
-    GW_TRY(check_launch(P, "gw_sigma"));
+    GW_TRY(check_launch(P, "Sigma_c"));
   }
   return GW_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
+  cudaStream_t st = P->st;
+  const size_t n = (size_t)P->N * P->N * P->nw;
+  P->reset_timing();
+  GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+  GW_TRY(chi0_core(P, q, P->d_chi0));
+  GW_TRY(read_status(P, "gw_chi0"));
+  GW_TRY(P->collect_timing());
+  if (chi0_out) GW_CUDA(cudaMemcpyAsync(chi0_out, P->d_chi0, sizeof(c128) * n, cudaMemcpyDeviceToDevice, st));
+  P->chi0_q = q;
+  P->wc_q = -1;
+  return GW_OK;
+}
+
+gw_status gw_screen(gw_plan P, int32_t sys, int32_t q, gw_complex* wc_out) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
+  if (P->chi0_q != q) return fail(GW_ERR_STATE, "gw_screen needs gw_chi0 for the same q first");
+  cudaStream_t st = P->st;
+  const long long NN = (long long)P->N * P->N;
+  GW_TRY(eps_core(P, q, P->d_chi0, P->d_E));
+  GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+  launch_chol_inv_minus_I(P->N, P->d_E, P->nw, NN, P->d_work, P->d_status, st);
+  GW_TRY(w_core(P, q, P->d_E, P->d_Wc));
+  GW_TRY(read_status(P, "gw_screen"));
+  if (wc_out) GW_CUDA(cudaMemcpyAsync(wc_out, P->d_Wc, sizeof(c128) * NN * P->nw, cudaMemcpyDeviceToDevice, st));
+  P->wc_q = q;
+  return GW_OK;
+}
+
+gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
+  if (P->wc_q != q) return fail(GW_ERR_STATE, "gw_sigma needs gw_screen for the same q first");
+  c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
+  GW_TRY(sigma_core(P, q, P->d_Wc, sig));
+  return GW_OK;
+}
+
+gw_status gw_g0w0(gw_plan P, int32_t sys, gw_complex* sigma_acc) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw;
+  const long long NN = (long long)N * N;
+  const long long slot = NN * nw;
+  if (!P->g_chi0) {
+    // q-group buffers: chi0 (then W^c), eps~ (then eps~^-1 - 1), Cholesky scratch
+    const double per_q = 3.0 * sizeof(c128) * (double)slot;
+    P->qb = (int)std::max(1.0, std::min((double)P->NK, std::floor(8.0e9 / per_q)));
+    GW_TRY(dalloc(P, &P->g_chi0, (size_t)slot * P->qb));
+    GW_TRY(dalloc(P, &P->g_E, (size_t)slot * P->qb));
+    GW_TRY(dalloc(P, &P->g_work, (size_t)slot * P->qb));
+  }
+  c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
+  P->reset_timing();
+  for (int q0 = 0; q0 < P->NK; q0 += P->qb) {
+    const int nq = std::min(P->qb, P->NK - q0);
+    GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+    for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q0 + j, P->g_chi0 + j * slot));
+    for (int j = 0; j < nq; ++j) GW_TRY(eps_core(P, q0 + j, P->g_chi0 + j * slot, P->g_E + j * slot));
+    launch_chol_inv_minus_I(N, P->g_E, nq * nw, NN, P->g_work, P->d_status, st);
+    for (int j = 0; j < nq; ++j) GW_TRY(w_core(P, q0 + j, P->g_E + j * slot, P->g_chi0 + j * slot));
+    for (int j = 0; j < nq; ++j) GW_TRY(sigma_core(P, q0 + j, P->g_chi0 + j * slot, sig));
+    GW_TRY(read_status(P, "gw_g0w0"));
+  }
+  GW_TRY(P->collect_timing());
+  P->chi0_q = P->wc_q = -1;
+  return GW_OK;
+}
+
 
 gw_status gw_qp(gw_plan P, int32_t sys, const gw_complex* sigma, const double* dxv, double* e_qp, double* gap,
                 int32_t* n_conv) {

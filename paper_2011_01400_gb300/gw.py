@@ -21,7 +21,7 @@ GW_FP64, GW_3XTF32, GW_3XBF16 = 0, 1, 2
 PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16}
 
 # every symbol include/gw.h declares
-EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_qp",
+EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_g0w0", "gw_qp",
            "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_kernel_launches", "gw_last_error")
 
 
@@ -74,6 +74,7 @@ def load():
     lib.gw_chi0.argtypes = [vp, i32, i32, vp]
     lib.gw_screen.argtypes = [vp, i32, i32, vp]
     lib.gw_sigma.argtypes = [vp, i32, i32, vp]
+    lib.gw_g0w0.argtypes = [vp, i32, vp]
     lib.gw_qp.argtypes = [vp, i32, vp, vp, dp, dp, ctypes.POINTER(i32)]
     lib.gw_plan_freq.argtypes = [vp, dp, dp]
     lib.gw_plan_mu.argtypes = [vp, dp]
@@ -123,6 +124,10 @@ def gw_screen(plan, sys, q, wc_out=None):
 
 def gw_sigma(plan, sys, q, sigma_acc=None):
     _check(load().gw_sigma(plan, sys, q, _ptr(sigma_acc)))
+
+
+def gw_g0w0(plan, sys, sigma_acc=None):
+    _check(load().gw_g0w0(plan, sys, _ptr(sigma_acc)))
 
 
 def gw_qp(plan, sys, n_k, n_sigma, sigma=None, dxv=None):

@@ -115,3 +115,27 @@ def test_sigma_qp_gap_cfg0(cfg0, prec, tol_mev):
     print(f"{prec}: Sigma_c max err {err_sig:.3e} meV, E_qp {err_e:.3e} meV, gap {err_gap:.3e} meV")
     assert nconv == s.n_k * (s.sigma_hi - s.sigma_lo) and ref["converged"].all()
     assert err_sig <= tol_mev and err_e <= tol_mev and err_gap <= tol_mev
+
+
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32"])
+def test_g0w0_driver_matches_per_q_calls(cfg0, prec):
+    """gw_g0w0 (q groups, batched FP64 factorisations) gives the per-q result and the oracle's."""
+    from paper_2011_01400_gb300 import gw
+    s, ref = cfg0
+    sig_q, e_q, gap_q, _ = run_gpu_sigma(s, prec, range(s.n_k))
+    pb = gw.Problem(s, prec)
+    plan = gw.gw_plan_create(pb.prob)
+    nsig = s.sigma_hi - s.sigma_lo
+    acc = torch.zeros((s.n_k, nsig, s.n_freq), dtype=torch.complex128, device="cuda")
+    try:
+        gw.gw_g0w0(plan, 0, acc)
+        e, gap, nconv = gw.gw_qp(plan, 0, s.n_k, nsig, sigma=acc)
+        ms, fl = gw.gw_plan_last_chi0_stats(plan)
+    finally:
+        gw.gw_plan_destroy(plan)
+    sig = acc.cpu().numpy()
+    tol = 1e-12 if prec == "fp64" else 1e-9
+    assert np.abs(sig - sig_q).max() <= tol * np.abs(sig_q).max() * 100
+    assert np.abs(sig - ref["sigma"]).max() * HA_MEV < (1e-6 if prec == "fp64" else 1.0)
+    assert abs(gap - ref["gap"]) * HA_MEV < (1e-6 if prec == "fp64" else 1.0)
+    assert ms > 0 and fl > 0
