@@ -101,13 +101,16 @@ __device__ __forceinline__ void mgen_body(const cplx<T>* __restrict__ T1, const 
   const int mu_begin = blockIdx.y * MGEN_MU;
   const int mu_end = min(mu_begin + MGEN_MU, g.N);
   const int npair = na * nb;
-  for (int mu = mu_begin; mu < mu_end; ++mu) {
+  // (ABF, pair) flattened over the block's threads so that no lanes idle on a ragged pair count
+  for (int idx = threadIdx.x; idx < (mu_end - mu_begin) * npair; idx += blockDim.x) {
+    const int mu = mu_begin + idx / npair;
+    const int p = idx % npair;
     const int A = aux_atom_of(g, mu);
     const int nbA = g.atom_nb[A], b0A = g.atom_b0[A];
     const int mul = mu - g.atom_x0[A];
     const cplx<T>* t1k = T1 + g.t_off[A] + (((long long)kp * g.atom_nx[A] + mul) * nbA) * g.NBd;
     const cplx<T>* t1kq = T1 + g.t_off[A] + (((long long)kpq * g.atom_nx[A] + mul) * nbA) * g.NBd;
-    for (int p = threadIdx.x; p < npair; p += blockDim.x) {
+    {
       const int a = a0 + p / nb, b = b0 + p % nb;
       T sr = 0, si = 0;
       for (int j = 0; j < nbA; ++j) {

@@ -64,18 +64,19 @@ constexpr long long WAIT_LIMIT = 4000000000LL;     // clock64 ticks (~2 s) per w
 // TMEM columns: D1 buffers at 0 and 128 (re: +0..63, im: +64..127); D2 buffers at 256 and 384
 constexpr uint32_t D1_COL = 0, D2_COL = 256, DBUF = 128;
 
-template <bool TF32> struct Cfg {
-  static constexpr int NP = TF32 ? 2 : 3;          // pieces per operand
+template <bool TF32, int NP_> struct Cfg {
+  static constexpr int NP = NP_;                   // pieces per operand (TF32: 2; BF16: 2 or 3)
   static constexpr int STAGE = 2 * NP * TILE;      // B pieces then A pieces
   static constexpr int STAGES = 2;
   static constexpr int RPS = TF32 ? 1 : 2;         // ring slots per stage
-  static constexpr int RING = TF32 ? 4 : 2;        // ring slots
+  static constexpr int RING = (NP_ == 3) ? 2 : 4;  // ring slots
   static constexpr int RS = 16 * RPS;              // complex pair rows per stage
   static constexpr int BAR_OFF = STAGES * STAGE + RING * RAW;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;
 };
-static_assert(Cfg<false>::SMEM <= 232448, "shared memory budget");
-static_assert(Cfg<true>::SMEM <= 232448, "shared memory budget");
+static_assert(Cfg<false, 3>::SMEM <= 232448, "shared memory budget");
+static_assert(Cfg<false, 2>::SMEM <= 232448, "shared memory budget");
+static_assert(Cfg<true, 2>::SMEM <= 232448, "shared memory budget");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -210,6 +211,7 @@ struct TcParams {
   c128* out;          // MODE 0: [nw][Ncols][Ncols]
   float* S;           // MODE 1: [Mrows][nw]
   int* status;
+  int tri;            // MODE 1: use the Hermitian triangle of W^c
 };
 
 struct Maps {
@@ -233,9 +235,27 @@ __device__ __forceinline__ void decode_item(const TcParams& p, int item, int& m0
   }
 }
 
-template <bool TF32, int MODE>
+
+// MODE 1 with `tri`: W^c is Hermitian, so column block nb needs K = mu from its own block on;
+// the block's own 64 ABFs form one segment (counted once), the rest a second one (counted twice).
+template <int MODE, int RS>
+__device__ __forceinline__ int first_stage(const TcParams& p, int n0) {
+  return (MODE == 1 && p.tri) ? n0 / RS : 0;
+}
+template <int MODE, int RS>
+__device__ __forceinline__ bool is_seg_first(const TcParams& p, int i, int i0, int F) {
+  if (MODE == 1 && p.tri) return i == i0 || i == i0 + BN / RS;
+  return (i % F) == 0;
+}
+template <int MODE, int RS>
+__device__ __forceinline__ bool is_seg_end(const TcParams& p, int i, int i0, int F, int nst) {
+  if (MODE == 1 && p.tri) return i == nst - 1 || i == i0 + BN / RS - 1;
+  return (i % F) == F - 1 || i == nst - 1;
+}
+
+template <bool TF32, int NPC, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps maps, TcParams p) {
-  using C = Cfg<TF32>;
+  using C = Cfg<TF32, NPC>;
   constexpr int NP = C::NP, STAGES = C::STAGES, STAGE = C::STAGE, RS = C::RS, RPS = C::RPS, RING = C::RING;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -294,7 +314,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
         int m0, n0, w;
         decode_item<MODE>(p, item, m0, n0, w);
         const int yrow = w * p.brow_y + n0;
-        for (int i = 0; i < nst; ++i, ++gs) {
+        for (int i = first_stage<MODE, RS>(p, n0); i < nst; ++i, ++gs) {
           const int s = gs % STAGES;
           if (!mbar_wait(&empty[s], ((gs / STAGES) & 1) ^ 1, p.status)) { ok = false; break; }
           uint8_t* st = smem + s * STAGE;
@@ -316,7 +336,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         int m0, n0, w;
         decode_item<MODE>(p, item, m0, n0, w);
-        for (int i = 0; i < nst * RPS; ++i, ++gr) {
+        for (int i = first_stage<MODE, RS>(p, n0) * RPS; i < nst * RPS; ++i, ++gr) {
           const int slot = gr % RING;
           if (!mbar_wait(&rempty[slot], ((gr / RING) & 1) ^ 1, p.status)) { ok = false; break; }
           mbar_arrive_expect_tx(&rfull[slot], RAW);
@@ -333,11 +353,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
       uint32_t gs = 0, gseg = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
-        for (int i = 0; i < nst; ++i, ++gs) {
+        int m0, n0, w;
+        decode_item<MODE>(p, item, m0, n0, w);
+        const int i0 = first_stage<MODE, RS>(p, n0);
+        for (int i = i0; i < nst; ++i, ++gs) {
           const int s = gs % STAGES;
           const int b = gs & 1;
           const int b2 = gseg & 1;
-          const bool seg_first = (i % F) == 0;
+          const bool seg_first = is_seg_first<MODE, RS>(p, i, i0, F);
           if (gs >= 2 && !mbar_wait(&t1empty[b], ((gs >> 1) - 1) & 1, p.status)) { ok = false; break; }
           if (seg_first && gseg >= 2 && !mbar_wait(&t2empty[b2], ((gseg >> 1) - 1) & 1, p.status)) {
             ok = false;
@@ -369,7 +392,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
           }
           mma_commit(&empty[s]);
           mma_commit(&t1full[b]);
-          if ((i % F) == F - 1 || i == nst - 1) {
+          if (is_seg_end<MODE, RS>(p, i, i0, F, nst)) {
             mma_commit(&t2full[b2]);
             ++gseg;
           }
@@ -387,7 +410,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
       int m0, n0, w;
       decode_item<MODE>(p, item, m0, n0, w);
       const float* wrow = p.wtab + (long long)w * p.wstride;
-      for (int i = 0; i < nst; ++i, ++gs) {
+      for (int i = first_stage<MODE, RS>(p, n0); i < nst; ++i, ++gs) {
         const int s = gs % STAGES;
         if (!mbar_wait(&empty[s], ((gs / STAGES) & 1) ^ 1, p.status)) { ok = false; break; }
         uint8_t* at = smem + s * STAGE + NP * TILE;
@@ -433,7 +456,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
             // A row = 32 pairs = 8 chunks of 4 pairs; this slot fills chunks 4h .. 4h+3
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
-              uint32_t o[3][4];
+              uint32_t o[NP][4];
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
                 const int pr = 4 * cc + q;     // pair within the slot
@@ -446,12 +469,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
                 const float2 mf = __bfloat1622float2(mm);
                 const __nv_bfloat162 ll = __floats2bfloat162_rn(rr - mf.x, ri - mf.y);
                 o[0][q] = bf2_bits(hh);
-                o[1][q] = bf2_bits(mm);
-                o[2][q] = bf2_bits(ll);
+                if constexpr (NP == 3) {
+                  o[1][q] = bf2_bits(mm);
+                  o[2][q] = bf2_bits(ll);
+                } else {
+                  o[1][q] = bf2_bits(__floats2bfloat162_rn(rr, ri));
+                }
               }
               const uint32_t off = swz(row, 4 * h + cc);
 #pragma unroll
-              for (int pc = 0; pc < 3; ++pc)
+              for (int pc = 0; pc < NP; ++pc)
                 *reinterpret_cast<uint4*>(at + pc * TILE + off) = make_uint4(o[pc][0], o[pc][1], o[pc][2], o[pc][3]);
             }
           }
@@ -477,7 +504,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
       float sr[32], si[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
-      for (int i = 0; i < nst; ++i, ++gs) {
+      for (int i = first_stage<MODE, RS>(p, n0); i < nst; ++i, ++gs) {
         const int b = gs & 1;
         // every lane polls the barrier; reconverge before the warp-wide (.sync.aligned) TMEM loads
         ok = __all_sync(0xffffffffu, mbar_wait(&t1full[b], (gs >> 1) & 1, p.status));
@@ -497,7 +524,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
         }
         tc_fence_before();
         mbar_arrive(&t1empty[b]);
-        if ((i % F) == F - 1 || i == nst - 1) {
+        if (is_seg_end<MODE, RS>(p, i, first_stage<MODE, RS>(p, n0), F, nst)) {
           const int b2 = gseg & 1;
           ok = __all_sync(0xffffffffu, mbar_wait(&t2full[b2], (gseg >> 1) & 1, p.status));
           if (!ok) break;
@@ -541,7 +568,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
                   acc = fmaf(sr[j], a.x, fmaf(si[j], a.y, acc));
                 }
               }
-              atomicAdd(p.S + (long long)m * p.nw + w, acc);
+              // triangle: the diagonal block counts once, the strictly lower blocks twice (2 Re)
+              const float wgt = (p.tri && i > first_stage<MODE, RS>(p, n0) + (BN / RS) - 1) ? 2.f : 1.f;
+              atomicAdd(p.S + (long long)m * p.nw + w, wgt * acc);
             }
           }
 #pragma unroll
@@ -585,7 +614,7 @@ __global__ void k_herm_fill(int N, int nw, c128* chi0) {
 
 // B planes of W^c for the Sigma contraction: row (j, nu), K index 2 mu + {0, 1}:
 // B1 = split(Re W_{nu mu}, Im W_{nu mu}), B2 = split(-Im, Re); mu >= N is zero padding.
-__global__ void k_w_planes(int N, int nw, int Kpad, const c128* __restrict__ Wc, PlaneSet P, int tf32) {
+__global__ void k_w_planes(int N, int nw, int Kpad, const c128* __restrict__ Wc, PlaneSet P, int tf32, int np) {
   const long long total = (long long)nw * N * Kpad;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -610,11 +639,13 @@ __global__ void k_w_planes(int N, int nw, int Kpad, const c128* __restrict__ Wc,
         const float2 hf = __bfloat1622float2(h);
         const float r0 = v[0] - hf.x, r1 = v[1] - hf.y;
         const __nv_bfloat162 mm = __floats2bfloat162_rn(r0, r1);
-        const float2 mf = __bfloat1622float2(mm);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
-        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half]) + o) = h;
-        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half + 1]) + o) = mm;
-        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half + 2]) + o) = l;
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[np * half]) + o) = h;
+        *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[np * half + 1]) + o) = mm;
+        if (np == 3) {
+          const float2 mf = __bfloat1622float2(mm);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+          *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[np * half + 2]) + o) = l;
+        }
       }
     }
   }
@@ -676,12 +707,12 @@ int num_sms() {
   return n;
 }
 
-template <bool TF32, int MODE>
+template <bool TF32, int NPC, int MODE>
 gw_status launch_tc(const Maps& maps, const TcParams& p, cudaStream_t st, std::string& err) {
-  const int smem = Cfg<TF32>::SMEM;
-  cudaFuncSetAttribute(k_tc<TF32, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int smem = Cfg<TF32, NPC>::SMEM;
+  cudaFuncSetAttribute(k_tc<TF32, NPC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int grid = std::min(p.n_items, num_sms());
-  ++::gw::g_launch_count, k_tc<TF32, MODE><<<grid, NTHREADS, smem, st>>>(maps, p);
+  ++::gw::g_launch_count, k_tc<TF32, NPC, MODE><<<grid, NTHREADS, smem, st>>>(maps, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("k_tc launch: ") + cudaGetErrorString(e);
@@ -726,7 +757,7 @@ gw_status TcWorkspace::ensure(int ntiles_needed, int ones_needed, cudaStream_t s
 
 gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std::string& err) {
   const bool tf32 = a.tf32 != 0;
-  const int RS = tf32 ? Cfg<true>::RS : Cfg<false>::RS;
+  const int RS = tf32 ? Cfg<true, 2>::RS : Cfg<false, 3>::RS;
   const int NP = tf32 ? 2 : 3;
   if (a.Kpad % 32 != 0 || a.N < 1) {
     err = "tc_chi0: Kpad must be a multiple of 32";
@@ -774,13 +805,14 @@ gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std
   p.scale = a.scale;
   p.out = a.chi0;
   p.status = a.status;
-  return tf32 ? launch_tc<true, 0>(maps, p, st, err) : launch_tc<false, 0>(maps, p, st, err);
+  return tf32 ? launch_tc<true, 2, 0>(maps, p, st, err) : launch_tc<false, 3, 0>(maps, p, st, err);
 }
 
 gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, std::string& err) {
   const bool tf32 = a.tf32 != 0;
-  const int RS = tf32 ? Cfg<true>::RS : Cfg<false>::RS;
-  const int NP = tf32 ? 2 : 3;
+  // Sigma_c needs ~1e-5 relative accuracy: two pieces per operand (hh, hl, lh) in both kinds
+  const int RS = tf32 ? Cfg<true, 2>::RS : Cfg<false, 2>::RS;
+  const int NP = 2;
   if (a.Kpad % 32 != 0) {
     err = "tc_sigma: Kpad must be a multiple of 32";
     return GW_ERR_ARG;
@@ -814,13 +846,14 @@ gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, s
   p.brow_y = a.N;
   p.scale = 1.0;
   p.S = a.S;
+  p.tri = 1;
   p.status = a.status;
-  return tf32 ? launch_tc<true, 1>(maps, p, st, err) : launch_tc<false, 1>(maps, p, st, err);
+  return tf32 ? launch_tc<true, 2, 1>(maps, p, st, err) : launch_tc<false, 2, 1>(maps, p, st, err);
 }
 
 void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st) {
   const long long total = (long long)nw * N * Kpad;
-  ++::gw::g_launch_count, k_w_planes<<<std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, st>>>(N, nw, Kpad, Wc, P, tf32);
+  ++::gw::g_launch_count, k_w_planes<<<std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, st>>>(N, nw, Kpad, Wc, P, tf32, 2);
 }
 
 void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st) {
