@@ -182,16 +182,55 @@ def run_reference(args, system, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def g0w0_step(gw, plan_prob, s, torch, chi_ms):
-    """One complete pass: plan, the whole q loop in one native call, QP. Returns (e_qp, gap)."""
+def g0w0_step(gw, plan_prob, s, torch, chi_ms, qloop="g0w0"):
+    """One complete pass: plan, the q loop (one native call, or per-q calls), QP. Returns (e_qp, gap)."""
     plan = gw.gw_plan_create(plan_prob)
     try:
-        gw.gw_g0w0(plan, 0)
-        chi_ms.append(gw.gw_plan_last_chi0_stats(plan))
+        if qloop == "g0w0":
+            gw.gw_g0w0(plan, 0)
+            chi_ms.append(gw.gw_plan_last_chi0_stats(plan))
+        else:
+            tot = [0.0, 0.0]
+            for q in range(s.n_k):
+                gw.gw_chi0(plan, 0, q)
+                ms, fl = gw.gw_plan_last_chi0_stats(plan)
+                tot[0] += ms
+                tot[1] += fl
+                gw.gw_screen(plan, 0, q)
+                gw.gw_sigma(plan, 0, q)
+            chi_ms.append(tuple(tot))
         e, gap, nconv = gw.gw_qp(plan, 0, s.n_k, s.sigma_hi - s.sigma_lo)
     finally:
         gw.gw_plan_destroy(plan)
     return e, gap
+
+
+def q_slice_ms(gw, s, prec, torch, q=1, reps=2):
+    """Device time (ms, CUDA events) of plan creation and of chi0 -> screen -> Sigma_c for one q."""
+    stream = torch.cuda.current_stream()
+    pb = gw.Problem(s, prec)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    plan = gw.gw_plan_create(pb.prob)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    plan_ms = ev[0].elapsed_time(ev[1])
+    try:
+        q = q % s.n_k
+        best = None
+        for _ in range(reps):
+            ev[0].record(stream)
+            gw.gw_chi0(plan, 0, q)
+            gw.gw_screen(plan, 0, q)
+            gw.gw_sigma(plan, 0, q)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            t = ev[0].elapsed_time(ev[1])
+            best = t if best is None else min(best, t)
+    finally:
+        gw.gw_plan_destroy(plan)
+    return plan_ms, best
 
 
 def run_device(args, system, world, rank):
@@ -214,7 +253,7 @@ def run_device(args, system, world, rank):
 
     chi_ms = []
     for _ in range(args.warmup):
-        g0w0_step(gw, pb.prob, s, torch, chi_ms)
+        g0w0_step(gw, pb.prob, s, torch, chi_ms, args.qloop)
     torch.cuda.synchronize()
     # device-resident timed region
     chi_ms.clear()
@@ -226,7 +265,7 @@ def run_device(args, system, world, rank):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        e, gap = g0w0_step(gw, pb.prob, s, torch, chi_ms)
+        e, gap = g0w0_step(gw, pb.prob, s, torch, chi_ms, args.qloop)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -238,14 +277,26 @@ def run_device(args, system, world, rank):
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     chi_e2e = []
-    e0.record(stream)
-    for _ in range(args.steps):
-        pb.upload()
-        e_qp, gap = g0w0_step(gw, pb.prob, s, torch, chi_e2e)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    ms_e2e = e0.elapsed_time(e1) / args.steps
+    ms_e2e = float("nan")
+    if not args.no_e2e:
+        e0.record(stream)
+        for _ in range(args.steps):
+            pb.upload()
+            e_qp, gap = g0w0_step(gw, pb.prob, s, torch, chi_e2e, args.qloop)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e2e = e0.elapsed_time(e1) / args.steps
+    # matched-accuracy comparison with the plain FP64 method on the GPU: one q slice each
+    fp64 = None
+    if not args.no_fp64_slice:
+        p64, q64 = q_slice_ms(gw, s, "fp64", torch)
+        psp, qsp = q_slice_ms(gw, s, args.prec, torch)
+        fp64 = dict(q_slice="q = 1: chi0 -> eps~/W^c -> Sigma_c through the per-q C ABI calls (best of 2)",
+                    fp64_plan_ms=p64, fp64_q_ms=q64, split_plan_ms=psp, split_q_ms=qsp,
+                    speedup_q=q64 / qsp,
+                    fp64_step_s_extrapolated=(p64 + s.n_k * q64) / 1e3,
+                    speedup_step_extrapolated=(p64 + s.n_k * q64) / ms)
     t = torch.tensor([ms, ms_e2e], dtype=torch.float64)
     if world > 1:
         t = t.cuda()
@@ -270,7 +321,8 @@ def run_device(args, system, world, rank):
         higher_is_better=False, scaling="weak", vs_baseline=None,
         dtype={"3xbf16": "bf16x3-split/f32-acc/f64", "3xtf32": "tf32x2-split/f32-acc/f64", "fp64": "f64"}[args.prec],
         data="synthetic",
-        config=dict(workload=WORKLOADS[args.config], name=args.config, precision=args.prec, systems_per_step=world,
+        config=dict(workload=WORKLOADS[args.config] + (f" (k mesh overridden to {args.nk})" if args.nk else ""),
+                    name=args.config, precision=args.prec, systems_per_step=world, q_loop=args.qloop,
                     global_batch=world, seq_len=0, parallelism="replicas" if world > 1 else "single",
                     l2="inputs larger than L2 (chi0 operand planes 0.8 GB per q)"),
         chi0_tflops=achieved,
@@ -284,6 +336,7 @@ def run_device(args, system, world, rank):
                  d2h_bytes_per_step=s.n_k * (s.sigma_hi - s.sigma_lo) * 8 + 8),
         gpu_launches=launches,
         clocks=ck,
+        fp64_gpu=fp64,
         gap_ha=gap,
     )
     if not args.no_cpu_baseline:
@@ -300,6 +353,11 @@ def main():
     ap.add_argument("--config", default="cfg1", choices=list(WORKLOADS))
     ap.add_argument("--prec", default="3xbf16", choices=["3xbf16", "3xtf32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-slice", action="store_true")
+    ap.add_argument("--qloop", default="g0w0", choices=["g0w0", "perq"],
+                    help="q loop in one gw_g0w0 call (default) or as per-q gw_chi0/gw_screen/gw_sigma calls")
+    ap.add_argument("--nk", default=None, help="override the k mesh, e.g. 4,4,4 (profiling captures)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -307,7 +365,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2011_01400_gb300.synth import make_system
-    system = make_system(args.config, seed=1000 * int(args.config[-1]) + rank)
+    over = {}
+    if args.nk:
+        over["nk"] = tuple(int(x) for x in args.nk.split(","))
+    system = make_system(args.config, seed=1000 * int(args.config[-1]) + rank, **over)
     if args.impl == "reference":
         run_reference(args, system, world, rank)
     else:
