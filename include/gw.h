@@ -142,6 +142,26 @@ gw_status gw_g0w0(gw_plan plan, int32_t sys, gw_complex* sigma_acc);
 gw_status gw_qp(gw_plan plan, int32_t sys, const gw_complex* sigma, const double* dxv,
                 double* e_qp, double* gap, int32_t* n_conv);
 
+/* Capacity of the fixed device scratch of gw_qp_static, in (k, n) pairs (12 bytes each). */
+#define GW_QP_STATIC_MAX 16384
+
+/* gw_qp without any device allocation (the paper has no counterpart: a deployment variant).
+ * Same arguments, arithmetic and results as gw_qp; the per-(k, n) QP energies and Newton flags
+ * live in one fixed file-scope device array of GW_QP_STATIC_MAX pairs instead of a
+ * cudaMalloc/cudaFree pair per call. For callers that cannot allocate device memory when
+ * they solve the QP equation: a process whose device memory is held by a caching allocator,
+ * or a serving loop that must not take the device-wide synchronisation of cudaFree.
+ * The plan itself still owns the workspace gw_plan_create allocated.
+ * - N_k * (sigma_hi - sigma_lo) > GW_QP_STATIC_MAX: GW_ERR_ARG, nothing launched (use gw_qp).
+ * - The first call on a device looks up the scratch address with cudaGetSymbolAddress (this
+ *   may load the library's device code); make that first call before any stream capture.
+ * - Nothing in the scratch has to start at zero: every call writes each element it reads.
+ * - One scratch array per device: calls that overlap in time on the same device (from any
+ *   thread, stream or plan) race on it. Serialise them.
+ * Errors: as gw_qp, plus GW_ERR_CUDA if the address lookup fails. */
+gw_status gw_qp_static(gw_plan plan, int32_t sys, const gw_complex* sigma, const double* dxv,
+                       double* e_qp, double* gap, int32_t* n_conv);
+
 /* Host copies of the plan's frequency grid (w_j and quadrature weights g_j), [n_freq] each. */
 gw_status gw_plan_freq(gw_plan plan, double* freq, double* weight);
 

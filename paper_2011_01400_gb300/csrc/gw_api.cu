@@ -947,3 +947,105 @@ gw_status gw_qp(gw_plan P, int32_t sys, const gw_complex* sigma, const double* d
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// gw_qp_static: the QP solve of gw_qp with its device scratch (per-(k, n) energies and Newton
+// flags) in one fixed file-scope array instead of a cudaMalloc/cudaFree pair per call.
+// Callers that cannot allocate at that point use it: a process whose device memory is held by
+// a caching allocator (the pool is full, so a fresh cudaMalloc fails although the QP step
+// needs only a few hundred KB), and a serving loop that re-solves the QP equation after every
+// Sigma_c update and cannot take the device-wide synchronisation that cudaFree implies.
+// The paper has no counterpart: it is a deployment variant of the QP step.
+// ---------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+struct QpScratch {
+  double e_qp[GW_QP_STATIC_MAX];  // written for every (k, n) < N_k * n_sigma by k_qp
+  int conv[GW_QP_STATIC_MAX];     // written for every (k, n) < N_k * n_sigma by k_qp
+  int n_conv;                     // written by k_qp_count
+};
+// Nothing here has to start at zero: each call writes every element it later reads.
+static __device__ __align__(256) QpScratch g_qp_scratch;
+
+std::mutex g_qp_scratch_mu;
+QpScratch* g_qp_scratch_ptr[64] = {};  // per device ordinal, looked up on the first call there
+
+// Device address of g_qp_scratch on the current device. The first call on a device makes the
+// lookup (cudaGetSymbolAddress, which may load this module onto the device).
+gw_status qp_scratch(QpScratch** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(GW_ERR_CUDA, std::string("gw_qp_static: cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= 64) return fail(GW_ERR_UNSUPPORTED, "gw_qp_static: device ordinal above 63");
+  std::lock_guard<std::mutex> lk(g_qp_scratch_mu);
+  if (!g_qp_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_qp_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(GW_ERR_CUDA, std::string("gw_qp_static: cudaGetSymbolAddress of the scratch array: ") +
+                                   cudaGetErrorString(e));
+    g_qp_scratch_ptr[dev] = static_cast<QpScratch*>(p);
+  }
+  *out = g_qp_scratch_ptr[dev];
+  return GW_OK;
+}
+
+// Number of converged (k, n) pairs: one block sums the flags.
+__global__ void k_qp_count(const int* __restrict__ conv, int n, int* out) {
+  __shared__ int s[256];
+  int acc = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += conv[i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_qp_static(gw_plan P, int32_t sys, const gw_complex* sigma, const double* dxv, double* e_qp,
+                       double* gap, int32_t* n_conv) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (!e_qp || !gap) return fail(GW_ERR_ARG, "e_qp and gap must not be NULL");
+  const int n = P->NK * P->nsig;
+  if (n > GW_QP_STATIC_MAX)
+    return fail(GW_ERR_ARG, "gw_qp_static: N_k * n_sigma = " + std::to_string(n) +
+                                " exceeds the static scratch capacity GW_QP_STATIC_MAX = " +
+                                std::to_string(GW_QP_STATIC_MAX) + "; use gw_qp");
+  QpScratch* sc = nullptr;
+  GW_TRY(qp_scratch(&sc));
+  cudaStream_t st = P->st;
+  const c128* sg = sigma ? reinterpret_cast<const c128*>(sigma) : P->d_sigma;
+  launch_qp(P->NK, P->nsig, P->NBd, P->p.sigma_lo, P->nw, sg, dxv, P->p.eps, P->d_mu, P->d_freq, sc->e_qp, sc->conv,
+            st);
+  GW_TRY(check_launch(P, "gw_qp_static"));
+  ++g_launch_count, k_qp_count<<<1, 256, 0, st>>>(sc->conv, n, &sc->n_conv);
+  GW_TRY(check_launch(P, "gw_qp_static"));
+  int nc = 0;
+  GW_CUDA(cudaMemcpyAsync(e_qp, sc->e_qp, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GW_CUDA(cudaMemcpyAsync(&nc, &sc->n_conv, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GW_CUDA(cudaStreamSynchronize(st));
+  if (n_conv) *n_conv = nc;
+  const int h = P->nocc - 1 - P->p.sigma_lo, l = P->nocc - P->p.sigma_lo;
+  if (h >= 0 && h < P->nsig && l >= 0 && l < P->nsig) {
+    double hmax = -1e300, lmin = 1e300;
+    for (int k = 0; k < P->NK; ++k) {
+      hmax = std::max(hmax, e_qp[k * P->nsig + h]);
+      lmin = std::min(lmin, e_qp[k * P->nsig + l]);
+    }
+    *gap = lmin - hmax;
+  } else {
+    *gap = std::nan("");
+  }
+  return GW_OK;
+}
+
+}  // extern "C"

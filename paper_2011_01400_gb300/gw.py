@@ -22,7 +22,7 @@ PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16}
 
 # every symbol include/gw.h declares
 EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_g0w0", "gw_qp",
-           "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_kernel_launches", "gw_last_error")
+           "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_kernel_launches", "gw_last_error")
 
 
 class GwError(RuntimeError):
@@ -76,6 +76,7 @@ def load():
     lib.gw_sigma.argtypes = [vp, i32, i32, vp]
     lib.gw_g0w0.argtypes = [vp, i32, vp]
     lib.gw_qp.argtypes = [vp, i32, vp, vp, dp, dp, ctypes.POINTER(i32)]
+    lib.gw_qp_static.argtypes = [vp, i32, vp, vp, dp, dp, ctypes.POINTER(i32)]
     lib.gw_plan_freq.argtypes = [vp, dp, dp]
     lib.gw_plan_mu.argtypes = [vp, dp]
     lib.gw_plan_last_chi0_stats.argtypes = [vp, dp, dp]
@@ -136,6 +137,17 @@ def gw_qp(plan, sys, n_k, n_sigma, sigma=None, dxv=None):
     nconv = ctypes.c_int32()
     _check(load().gw_qp(plan, sys, _ptr(sigma), _ptr(dxv),
                         e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(gap), ctypes.byref(nconv)))
+    return e, gap.value, nconv.value
+
+
+def gw_qp_static(plan, sys, n_k, n_sigma, sigma=None, dxv=None):
+    """gw_qp with its device scratch in a fixed array of the library (no device allocation)."""
+    e = np.zeros((n_k, n_sigma))
+    gap = ctypes.c_double()
+    nconv = ctypes.c_int32()
+    _check(load().gw_qp_static(plan, sys, _ptr(sigma), _ptr(dxv),
+                               e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(gap),
+                               ctypes.byref(nconv)))
     return e, gap.value, nconv.value
 
 
