@@ -175,6 +175,68 @@ gw_status gw_plan_last_chi0_stats(gw_plan plan, double* ms, double* flops);
 /* Number of CUDA kernels this library has launched in the calling process so far (host-side count). */
 gw_status gw_kernel_launches(uint64_t* count);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned frequency surrogate (no counterpart in the paper).
+ *
+ * The plain method evaluates chi0 and eps~^-1 at every imaginary frequency of the grid.
+ * With a surrogate attached, only a coarse subset C of the grid is computed. X = eps~^-1 - 1
+ * on the other ("fine") frequencies F is reconstructed as
+ *   X(w_m) = sum_c L_mc X(w_c) + U diag(sigma_l g_l(w_m)) U^H,
+ * where U are Ritz modes of eps~(w_ref) - 1 (w_ref = the first coarse frequency),
+ * d_l(w) = u_l^H X(w) u_l is the mode diagonal, sigma_l = |d_l(w_ref)|, and the network maps
+ * x_l = d_l(C)/sigma_l to f(x) = L x + g(x), the predicted d_l(F)/sigma_l.
+ *   g(x) = s * (W4 h3 + b4), h3 = silu(W3 h2 + b3), h2 = silu(W2 h1 + b2), h1 = silu(W1 x + b1).
+ * Parameters: one fp32 vector in this order (row-major):
+ *   W1 [H][I], b1 [H], W2 [H][H], b2 [H], W3 [H][H], b3 [H], W4 [O][H], b4 [O], L [O][I], s [1]
+ * with I = n_in (coarse frequencies), H = n_hidden, O = n_out (fine frequencies).
+ * Matrix products use bf16 copies of W1..W4 (round to nearest even) with fp32 accumulation;
+ * biases, L and s stay fp32. All model calls are ordered on the caller's stream given at
+ * creation (the model works on its own stream, joined by events).
+ * ------------------------------------------------------------------------------------------ */
+typedef struct gw_surrogate_s* gw_surrogate;
+
+typedef struct {
+  int32_t n_in;      /* coarse frequencies, 1..64          */
+  int32_t n_hidden;  /* hidden width, 1..4096               */
+  int32_t n_out;     /* fine frequencies, 1..1024           */
+} gw_surrogate_dims;
+
+/* Length of the parameter vector for dims (host scalar). */
+gw_status gw_surrogate_param_count(const gw_surrogate_dims* dims, int64_t* count);
+
+/* New model with parameters copied from `params` (device fp32 [count]); Adam state zeroed.
+ * `stream`: the caller's cudaStream_t (NULL = legacy default). */
+gw_status gw_surrogate_create(const gw_surrogate_dims* dims, const float* params, void* stream, gw_surrogate* out);
+gw_status gw_surrogate_destroy(gw_surrogate model);
+/* Copy the fp32 parameters out (device [count]) / in (device [count]; the bf16 copies and s follow). */
+gw_status gw_surrogate_get_params(gw_surrogate model, float* params);
+gw_status gw_surrogate_set_params(gw_surrogate model, const float* params);
+
+/* f = L x + g(x) and/or g(x) for n rows: x device [n][I]; f, g device [n][O] (either may be NULL). */
+gw_status gw_surrogate_forward(gw_surrogate model, const float* x, int64_t n, float* f, float* g);
+
+/* Mean squared error of f(x) against y over all n*O outputs, and its gradient with respect to
+ * every parameter (device [count]; the entry of s is 0: s is fixed). 1 <= n <= 65536.
+ * loss: host scalar. Weights enter through their bf16 copies (gradient of the rounded weights). */
+gw_status gw_surrogate_loss_grad(gw_surrogate model, const float* x, const float* y, int64_t n, double* loss,
+                                 float* grad);
+
+/* Closed-form ridge fit of L: L = argmin |x L^T - y|^2 + ridge*n*|L|^2, normal equations
+ * accumulated and solved in FP64 (Cholesky). Then s = rms of the residual y - x L^T
+ * (s = 1 if that is 0); rms: host output (may be NULL). Errors: GW_ERR_NOT_PD. */
+gw_status gw_surrogate_fit_linear(gw_surrogate model, const float* x, const float* y, int64_t n, double ridge,
+                                  double* rms);
+
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on W1..b4 over `epochs` passes of
+ * mini-batches of `batch` rows (1..min(n, 4096)), rows shuffled every epoch with a generator
+ * seeded by `seed` (the last n % batch rows of each shuffled epoch are skipped). L and s are
+ * not changed. The MLP is fitted to the residual targets (y - x L^T)/s, whose mean squared
+ * error is the loss of f divided by s^2 (the same minimiser; Adam is invariant to that scale).
+ * One step (gather, forward, backward, Adam) runs as a captured CUDA graph. Adam's moments and
+ * step count persist across calls. loss_hist: host [epochs] mean loss of f per epoch, or NULL. */
+gw_status gw_surrogate_train(gw_surrogate model, const float* x, const float* y, int64_t n, int32_t epochs,
+                             int32_t batch, double lr, uint64_t seed, double* loss_hist);
+
 /* Text of the last error on the calling thread ("" if none). Never NULL. */
 const char* gw_last_error(void);
 

@@ -25,6 +25,14 @@ gw_status fail(gw_status s, const std::string& msg) {
   return s;
 }
 
+}  // namespace
+
+namespace gw {
+void gw_set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace gw
+
+namespace {
+
 #define GW_CUDA(call)                                                                                  \
   do {                                                                                                 \
     cudaError_t e_ = (call);                                                                           \

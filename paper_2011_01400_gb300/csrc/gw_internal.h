@@ -167,4 +167,13 @@ void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int
 bool tc_available();
 void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st);
 
+// text returned by gw_last_error() on this thread
+void gw_set_last_error(const std::string& msg);
+
+// learned frequency surrogate (k_mlp.cu): g = s * MLP(x) for n <= 4096 rows on stream st
+gw_status sur_correction(gw_surrogate_s* m, const float* x, int n, float* g_out, cudaStream_t st);
+int sur_n_in(const gw_surrogate_s* m);
+int sur_n_out(const gw_surrogate_s* m);
+const float* sur_linear(const gw_surrogate_s* m);   // device [n_out][n_in] fp32
+
 }  // namespace gw

@@ -22,13 +22,20 @@ PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16}
 
 # every symbol include/gw.h declares
 EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_g0w0", "gw_qp",
-           "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_kernel_launches", "gw_last_error")
+           "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_kernel_launches",
+           "gw_surrogate_param_count", "gw_surrogate_create", "gw_surrogate_destroy", "gw_surrogate_get_params",
+           "gw_surrogate_set_params", "gw_surrogate_forward", "gw_surrogate_loss_grad", "gw_surrogate_fit_linear",
+           "gw_surrogate_train", "gw_last_error")
 
 
 class GwError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"gw status {status}: {msg}")
         self.status = status
+
+
+class gw_surrogate_dims(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int32), ("n_hidden", ctypes.c_int32), ("n_out", ctypes.c_int32)]
 
 
 class gw_problem(ctypes.Structure):
@@ -81,6 +88,17 @@ def load():
     lib.gw_plan_mu.argtypes = [vp, dp]
     lib.gw_plan_last_chi0_stats.argtypes = [vp, dp, dp]
     lib.gw_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    i64, u64, dpp = ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)
+    dimp = ctypes.POINTER(gw_surrogate_dims)
+    lib.gw_surrogate_param_count.argtypes = [dimp, ctypes.POINTER(i64)]
+    lib.gw_surrogate_create.argtypes = [dimp, vp, vp, ctypes.POINTER(vp)]
+    lib.gw_surrogate_destroy.argtypes = [vp]
+    lib.gw_surrogate_get_params.argtypes = [vp, vp]
+    lib.gw_surrogate_set_params.argtypes = [vp, vp]
+    lib.gw_surrogate_forward.argtypes = [vp, vp, i64, vp, vp]
+    lib.gw_surrogate_loss_grad.argtypes = [vp, vp, vp, i64, dpp, vp]
+    lib.gw_surrogate_fit_linear.argtypes = [vp, vp, vp, i64, ctypes.c_double, dpp]
+    lib.gw_surrogate_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_double, u64, dpp]
     lib.gw_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "gw_last_error":
@@ -175,6 +193,62 @@ def gw_plan_last_chi0_stats(plan):
     ms, fl = ctypes.c_double(), ctypes.c_double()
     _check(load().gw_plan_last_chi0_stats(plan, ctypes.byref(ms), ctypes.byref(fl)))
     return ms.value, fl.value
+
+
+def _dims(n_in, n_hidden, n_out):
+    return gw_surrogate_dims(int(n_in), int(n_hidden), int(n_out))
+
+
+def gw_surrogate_param_count(n_in, n_hidden, n_out):
+    c = ctypes.c_int64()
+    _check(load().gw_surrogate_param_count(ctypes.byref(_dims(n_in, n_hidden, n_out)), ctypes.byref(c)))
+    return c.value
+
+
+def gw_surrogate_create(n_in, n_hidden, n_out, params, stream=None):
+    """params: device float32 tensor [count]."""
+    import torch
+    h = ctypes.c_void_p()
+    s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+    _check(load().gw_surrogate_create(ctypes.byref(_dims(n_in, n_hidden, n_out)), _ptr(params), ctypes.c_void_p(s),
+                                      ctypes.byref(h)))
+    return h
+
+
+def gw_surrogate_destroy(model):
+    _check(load().gw_surrogate_destroy(model))
+
+
+def gw_surrogate_get_params(model, out):
+    _check(load().gw_surrogate_get_params(model, _ptr(out)))
+    return out
+
+
+def gw_surrogate_set_params(model, params):
+    _check(load().gw_surrogate_set_params(model, _ptr(params)))
+
+
+def gw_surrogate_forward(model, x, f=None, g=None):
+    _check(load().gw_surrogate_forward(model, _ptr(x), x.shape[0], _ptr(f), _ptr(g)))
+
+
+def gw_surrogate_loss_grad(model, x, y, grad):
+    loss = ctypes.c_double()
+    _check(load().gw_surrogate_loss_grad(model, _ptr(x), _ptr(y), x.shape[0], ctypes.byref(loss), _ptr(grad)))
+    return loss.value
+
+
+def gw_surrogate_fit_linear(model, x, y, ridge):
+    rms = ctypes.c_double()
+    _check(load().gw_surrogate_fit_linear(model, _ptr(x), _ptr(y), x.shape[0], float(ridge), ctypes.byref(rms)))
+    return rms.value
+
+
+def gw_surrogate_train(model, x, y, epochs, batch, lr, seed):
+    hist = np.zeros(max(int(epochs), 1))
+    _check(load().gw_surrogate_train(model, _ptr(x), _ptr(y), x.shape[0], int(epochs), int(batch), float(lr),
+                                     int(seed), hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return hist[:epochs]
 
 
 # ---------------------------------------------------------------------------------------------

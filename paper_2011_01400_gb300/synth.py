@@ -220,3 +220,17 @@ def make_system(cfg="cfg0", seed=0, *, trs=True, n_freq=None, nk=None, n_bands=N
                   ctil_R=ctil, V=V, pmom=pm, omega_cell=float(p["omega_cell"]),
                   qhat=np.array([1.0, 0.0, 0.0]), n_freq=int(p["n_freq"]), omega0=omega0,
                   sigma_lo=int(lo), sigma_hi=int(hi), spin=2.0, head_wings=head_wings, seed=seed)
+
+
+def surrogate_init(n_in, n_hidden, n_out, seed=0, out_gain=0.01):
+    """Seeded initial parameter vector of the frequency surrogate (fp32, the layout of
+    gw_surrogate_create): weights N(0, 1/fan_in), the last layer scaled by out_gain so that
+    the network starts close to its linear part, biases and L zero, output scale 1."""
+    rng = np.random.default_rng(seed)
+    H, I, O = n_hidden, n_in, n_out
+    parts = [rng.standard_normal((H, I)) / np.sqrt(I), np.zeros(H),
+             rng.standard_normal((H, H)) / np.sqrt(H), np.zeros(H),
+             rng.standard_normal((H, H)) / np.sqrt(H), np.zeros(H),
+             out_gain * rng.standard_normal((O, H)) / np.sqrt(H), np.zeros(O),
+             np.zeros((O, I)), np.ones(1)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
