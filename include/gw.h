@@ -237,6 +237,42 @@ gw_status gw_surrogate_fit_linear(gw_surrogate model, const float* x, const floa
 gw_status gw_surrogate_train(gw_surrogate model, const float* x, const float* y, int64_t n, int32_t epochs,
                              int32_t batch, double lr, uint64_t seed, double* loss_hist);
 
+/* Surrogate configuration of a plan. */
+typedef struct {
+  int32_t n_coarse;          /* coarse frequencies computed exactly (= the model's n_in), 1..64   */
+  const int32_t* coarse;     /* host [n_coarse]: ascending grid indices; coarse[0] is w_ref        */
+  int32_t n_modes;           /* modes the network corrects, 1..n_block                            */
+  int32_t n_block;           /* subspace iteration block width, n_modes..min(64, n_aux); it must
+                                not exceed the rank of eps~(w_ref) - 1                          */
+  int32_t n_iter;            /* subspace iteration steps, 0..1000                                 */
+  const gw_complex* start;   /* device [n_aux][n_block]: start block of the iteration (caller's
+                                seeded random numbers); copied                                  */
+} gw_surrogate_cfg;
+
+/* Attach a surrogate to the plan. With a model, gw_g0w0 computes chi0, eps~ and W^c on the
+ * coarse frequencies only: per q it finds U, the n_modes Ritz vectors of eps~(w_ref) - 1 of
+ * largest Ritz value after n_iter steps of subspace iteration (two Cholesky-QR passes per step,
+ * FP64) and Rayleigh-Ritz, forms the mode diagonal d on the coarse frequencies, evaluates the
+ * network, and adds to Sigma_c the fine frequencies through
+ *   S_nm(w_m) = sum_c L_mc S_nm(w_c) + sum_l |(a^T V^1/2 U)_l|^2 sigma_l g_l(w_m),
+ * which is the S of the reconstructed X above (S is linear in X). The quadrature, the
+ * continuation and the QP solve use the full grid. The per-q calls (gw_chi0, gw_screen,
+ * gw_sigma) keep the full grid. model NULL with cfg: only gw_surrogate_modes is enabled;
+ * model and cfg NULL: detach. The model's n_in / n_out must be n_coarse / n_freq - n_coarse,
+ * and it must not be used elsewhere while the plan runs. Sizes cannot change once set. */
+gw_status gw_surrogate_enable(gw_plan plan, gw_surrogate model, const gw_surrogate_cfg* cfg);
+
+/* Training data from the plain method: after gw_chi0(q) on the full grid, eps~ and eps~^-1 - 1
+ * at every frequency, the modes U of eps~(w_coarse[0]) - 1 (as above), and (device outputs,
+ * each may be NULL, not all):
+ *   d_out     fp32 [n_modes][n_freq]: d_l(w_j) = u_l^H (eps~^-1(w_j) - 1) u_l
+ *   theta_out [n_modes] Ritz values, descending
+ *   x_out     fp32 [n_modes][n_coarse]: network inputs d_l(C) / sigma_l, sigma_l = |d_l(w_coarse[0])|
+ *   y_out     fp32 [n_modes][n_freq - n_coarse]: targets d_l(F) / sigma_l
+ * Needs gw_surrogate_enable. */
+gw_status gw_surrogate_modes(gw_plan plan, int32_t sys, int32_t q, float* d_out, double* theta_out, float* x_out,
+                             float* y_out);
+
 /* Text of the last error on the calling thread ("" if none). Never NULL. */
 const char* gw_last_error(void);
 

@@ -124,6 +124,31 @@ __global__ void k_ns_final(int N, const cplx<T>* Y, long long s, const double* c
 
 }  // namespace
 
+// learned frequency surrogate attached to a plan (gw_surrogate_enable)
+struct SurState {
+  gw_surrogate_s* model = nullptr;
+  bool on = false;
+  int nc = 0, nf = 0, k = 0, nb = 0, iters = 0;
+  std::vector<int> coarse, fine;
+  int* d_jmap = nullptr;       // [nw]: coarse position, or -(fine position + 1)
+  double* d_freq_c = nullptr;  // [nc]
+  c128* d_start = nullptr;     // [N][nb]
+  c128 *d_Y = nullptr, *d_Q = nullptr, *d_T = nullptr;               // [N][nb]
+  c128 *d_G = nullptr, *d_Linv = nullptr, *d_H = nullptr, *d_Z = nullptr;  // [nb][nb]
+  double* d_theta = nullptr;   // [nb]
+  c128* d_A1 = nullptr;        // [N][N] eps~(w_ref) - 1 of gw_surrogate_modes
+  c128* d_U1 = nullptr;        // [N][k]
+  c128* d_XU = nullptr;        // [max(nw, nc)][N][k]
+  c128* d_B = nullptr;         // [N][k] V^1/2 U (c128, or c64 in its first half)
+  void* d_P = nullptr;         // [sig_rows][k] projections (c64 or c128)
+  float* d_Sc = nullptr;       // [sig_rows][nc]
+  double* d_Sc_d = nullptr;    // [sig_rows][nc]
+  // q-group buffers of the surrogate pass
+  int qbs = 0;
+  c128 *g_chi0 = nullptr, *g_E = nullptr, *g_work = nullptr, *g_A = nullptr, *g_U = nullptr;
+  float *d_d = nullptr, *d_x = nullptr, *d_sig = nullptr, *d_g = nullptr, *d_coef = nullptr;
+};
+
 struct gw_plan_s {
   gw_problem p{};
   gw_precision prec;
@@ -179,6 +204,7 @@ struct gw_plan_s {
   // q-group buffers of gw_g0w0
   c128 *g_chi0 = nullptr, *g_E = nullptr, *g_work = nullptr;
   int qb = 0;
+  SurState sur;
   // timing of the chi0 contraction launches of the last call (CUDA events on the plan's stream)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double last_chi0_ms = 0.0, last_chi0_flops = 0.0, chi0_flops_acc = 0.0;
@@ -834,6 +860,8 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig) {
   return GW_OK;
 }
 
+gw_status g0w0_sur(gw_plan_s* P, c128* sig);  // the surrogate pass, defined below
+
 }  // namespace
 
 extern "C" {
@@ -885,6 +913,8 @@ gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
 gw_status gw_g0w0(gw_plan P, int32_t sys, gw_complex* sigma_acc) {
   gw_status s;
   if (!plan_ok(P, sys, &s)) return s;
+  if (P->sur.on && P->sur.model)
+    return g0w0_sur(P, sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma);
   cudaStream_t st = P->st;
   const int N = P->N, nw = P->nw;
   const long long NN = (long long)N * N;
@@ -1054,6 +1084,304 @@ gw_status gw_qp_static(gw_plan P, int32_t sys, const gw_complex* sigma, const do
     *gap = std::nan("");
   }
   return GW_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Learned frequency surrogate on the plan (the paper has no counterpart): chi0 / eps~ only on
+// the coarse frequencies C, X = eps~^-1 - 1 on the fine frequencies F from
+//   X(w_m) = sum_c L_mc X(w_c) + U diag(sigma_l g_l(w_m)) U^H,
+// U the Ritz modes of eps~(w_ref) - 1. Sigma_c needs only S_nm(w') = a^T V^1/2 X V^1/2 a^*,
+// which is linear in X:  S(w_m) = sum_c L_mc S(w_c) + sum_l |p_l|^2 sigma_l g_l(w_m),
+// p = a^T (V^1/2 U). So the W^c contraction runs on the coarse frequencies only, plus one
+// projection of the rows a onto V^1/2 U.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// plan views of the frequency grid: nw and d_freq replaced while alive
+struct FreqView {
+  gw_plan_s* P;
+  int nw;
+  double* freq;
+  FreqView(gw_plan_s* P_, int nw_, double* f_) : P(P_), nw(P_->nw), freq(P_->d_freq) {
+    P->nw = nw_;
+    P->d_freq = f_;
+  }
+  ~FreqView() {
+    P->nw = nw;
+    P->d_freq = freq;
+  }
+};
+
+// Q = orth(Y) by two Cholesky-QR passes (Y and T are overwritten)
+void cholqr2(gw_plan_s* P, c128* Y, c128* Q) {
+  SurState& S = P->sur;
+  const int N = P->N, nb = S.nb;
+  const c128 one{1, 0}, zero{0, 0};
+  c128* in = Y;
+  c128* outs[2] = {S.d_T, Q};
+  for (int pass = 0; pass < 2; ++pass) {
+    launch_zgemm<double>(nb, nb, N, one, in, nb, 0, OP_C, in, nb, 0, OP_N, zero, S.d_G, nb, 0, 1, P->st);
+    launch_small_chol_linv(nb, S.d_G, S.d_Linv, P->d_status, P->st);
+    launch_zgemm<double>(N, nb, nb, one, in, nb, 0, OP_N, S.d_Linv, nb, 0, OP_C, zero, outs[pass], nb, 0, 1, P->st);
+    in = outs[pass];
+  }
+}
+
+// Ritz modes of the Hermitian A [N][N]: subspace iteration from the start block, Rayleigh-Ritz;
+// U_out [N][k] = the k Ritz vectors of largest Ritz value (S.d_theta holds all nb, descending)
+gw_status modes_core(gw_plan_s* P, const c128* A, c128* U_out) {
+  SurState& S = P->sur;
+  const int N = P->N, nb = S.nb, k = S.k;
+  const c128 one{1, 0}, zero{0, 0};
+  cudaStream_t st = P->st;
+  GW_CUDA(cudaMemcpyAsync(S.d_Y, S.d_start, sizeof(c128) * N * nb, cudaMemcpyDeviceToDevice, st));
+  cholqr2(P, S.d_Y, S.d_Q);
+  for (int it = 0; it < S.iters; ++it) {
+    launch_zgemm<double>(N, nb, N, one, A, N, 0, OP_N, S.d_Q, nb, 0, OP_N, zero, S.d_Y, nb, 0, 1, st);
+    cholqr2(P, S.d_Y, S.d_Q);
+  }
+  launch_zgemm<double>(N, nb, N, one, A, N, 0, OP_N, S.d_Q, nb, 0, OP_N, zero, S.d_Y, nb, 0, 1, st);
+  launch_zgemm<double>(nb, nb, N, one, S.d_Q, nb, 0, OP_C, S.d_Y, nb, 0, OP_N, zero, S.d_H, nb, 0, 1, st);
+  launch_small_jacobi(nb, S.d_H, S.d_theta, S.d_Z, st);
+  launch_zgemm<double>(N, k, nb, one, S.d_Q, nb, 0, OP_N, S.d_Z, nb, 0, OP_N, zero, U_out, k, 0, 1, st);
+  return check_launch(P, "surrogate modes");
+}
+
+// d [k][ldd] (columns c0 ..) = mode diagonal of the nx matrices X [nx][N][N] in the basis U
+void mode_diag(gw_plan_s* P, const c128* X, int nx, const c128* U, float* d, int ldd, int c0) {
+  SurState& S = P->sur;
+  const int N = P->N, k = S.k;
+  const long long NN = (long long)N * N;
+  const c128 one{1, 0}, zero{0, 0};
+  launch_zgemm<double>(N, k, N, one, X, N, NN, OP_N, U, k, 0, OP_N, zero, S.d_XU, k, (long long)N * k, nx, P->st);
+  launch_mode_diag(N, k, nx, U, S.d_XU, (long long)N * k, d, ldd, c0, P->st);
+}
+
+// q term of Sigma_c with W^c on the coarse frequencies (Wc_c [nc][N][N]), the modes U [N][k]
+// and the network's correction coef [k][nf] (sigma_l g_l(w_m)); full-grid convolution.
+gw_status sigma_core_sur(gw_plan_s* P, int q, const c128* Wc_c, const c128* U, const float* coef, c128* sig) {
+  SurState& S = P->sur;
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw, nc = S.nc, nf = S.nf, k = S.k, NBd = P->NBd, nsig = P->nsig;
+  const long long NN = (long long)N * N;
+  const c128* evec = reinterpret_cast<const c128*>(P->p.evec);
+  const double pref = -1.0 / (2.0 * M_PI * P->NK);
+  const int tf32 = P->prec == GW_3XTF32;
+  const float* Lmat = sur_linear(S.model);
+  // B = V^1/2 U
+  launch_zgemm<double>(N, k, N, c128{1, 0}, P->d_Vh + (long long)q * NN, N, 0, OP_N, U, k, 0, OP_N, c128{0, 0}, S.d_B,
+                       k, 0, 1, st);
+  c64* B32 = reinterpret_cast<c64*>(S.d_XU);
+  if (!P->fp64) {
+    launch_convert(N * k, S.d_B, B32, st);
+    tc_w_planes(N, nc, P->Kx, Wc_c, P->d_Wpl, tf32, st);
+  }
+  for (int kk0 = 0; kk0 < P->NK; kk0 += P->sig_nkk) {
+    const int nkk = std::min(P->sig_nkk, P->NK - kk0);
+    const int R = nkk * nsig * NBd;
+    if (P->fp64) {
+      c128* A = static_cast<c128*>(P->d_A);
+      c128* Ut = static_cast<c128*>(P->d_U);
+      launch_mgen<double>(P->geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk,
+                          MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, N, 1, st);
+      for (int c = 0; c < nc; ++c) {
+        launch_zgemm<double>(R, N, N, c128{1, 0}, A, N, 0, OP_N, Wc_c + c * NN, N, 0, OP_N, c128{0, 0}, Ut, N, 0, 1, st);
+        launch_rowdot<double>(R, N, Ut, A, N, nullptr, S.d_Sc_d, c, nc, st);
+      }
+      c128* Pm = static_cast<c128*>(S.d_P);
+      launch_zgemm<double>(R, k, N, c128{1, 0}, A, N, 0, OP_N, S.d_B, k, 0, OP_N, c128{0, 0}, Pm, k, 0, 1, st);
+      launch_sur_assemble<double>(R, nc, nw, k, S.d_jmap, S.d_Sc_d, Pm, coef, nf, Lmat, P->d_S_d, st);
+    } else {
+      c64* A = static_cast<c64*>(P->d_A);
+      launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK_MINUS_Q,
+                         P->p.sigma_lo, nsig, 0, NBd, A, P->Kx, 1, st);
+      GW_CUDA(cudaMemsetAsync(S.d_Sc, 0, sizeof(float) * (size_t)R * nc, st));
+      TcSigmaArgs a{};
+      a.R = R;
+      a.N = N;
+      a.Kpad = P->Kx;
+      a.nw = nc;
+      a.raw = reinterpret_cast<const float*>(A);
+      for (int i = 0; i < 6; ++i) a.bpl[i] = P->d_Wpl.b[i];
+      a.S = S.d_Sc;
+      a.tf32 = tf32;
+      a.status = P->d_status;
+      std::string err;
+      gw_status ts = tc_sigma_run(a, P->tcws, st, err);
+      if (ts != GW_OK) {
+        P->err = 1;
+        return fail(ts, err);
+      }
+      c64* Pm = static_cast<c64*>(S.d_P);
+      launch_zgemm<float>(R, k, N, c64{1, 0}, A, P->Kx, 0, OP_N, B32, k, 0, OP_N, c64{0, 0}, Pm, k, 0, 1, st);
+      launch_sur_assemble<float>(R, nc, nw, k, S.d_jmap, S.d_Sc, Pm, coef, nf, Lmat, P->d_S_f, st);
+    }
+    launch_sigma_conv_chunk(kk0, nkk, nsig, NBd, P->p.nk, q, P->p.eps, P->d_mu, P->d_S_f, P->d_S_d, P->d_freq,
+                            P->d_fw, nw, pref, sig, P->fp64, st);
+    GW_TRY(check_launch(P, "Sigma_c (surrogate)"));
+  }
+  return GW_OK;
+}
+
+// the whole q loop with the surrogate: q groups as gw_g0w0, coarse frequencies only
+gw_status g0w0_sur(gw_plan_s* P, c128* sig) {
+  SurState& S = P->sur;
+  cudaStream_t st = P->st;
+  const int N = P->N, nc = S.nc, nf = S.nf, k = S.k;
+  const long long NN = (long long)N * N;
+  const long long slot = NN * nc;
+  if (!S.g_chi0) {
+    const double per_q = 3.0 * sizeof(c128) * (double)slot + sizeof(c128) * (double)(NN + (long long)N * k);
+    S.qbs = (int)std::max(1.0, std::min({(double)P->NK, std::floor(6.0e9 / per_q), std::floor(4096.0 / k)}));
+    GW_TRY(dalloc(P, &S.g_chi0, (size_t)slot * S.qbs));
+    GW_TRY(dalloc(P, &S.g_E, (size_t)slot * S.qbs));
+    GW_TRY(dalloc(P, &S.g_work, (size_t)slot * S.qbs));
+    GW_TRY(dalloc(P, &S.g_A, (size_t)NN * S.qbs));
+    GW_TRY(dalloc(P, &S.g_U, (size_t)N * k * S.qbs));
+    const size_t rows = (size_t)S.qbs * k;
+    GW_TRY(dalloc(P, &S.d_d, rows * nc));
+    GW_TRY(dalloc(P, &S.d_x, rows * nc));
+    GW_TRY(dalloc(P, &S.d_sig, rows));
+    GW_TRY(dalloc(P, &S.d_g, rows * nf));
+    GW_TRY(dalloc(P, &S.d_coef, rows * nf));
+  }
+  P->reset_timing();
+  for (int q0 = 0; q0 < P->NK; q0 += S.qbs) {
+    const int nq = std::min(S.qbs, P->NK - q0);
+    GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+    {
+      FreqView fv(P, nc, S.d_freq_c);
+      for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q0 + j, S.g_chi0 + j * slot));
+      for (int j = 0; j < nq; ++j) {
+        GW_TRY(eps_core(P, q0 + j, S.g_chi0 + j * slot, S.g_E + j * slot));
+        GW_CUDA(cudaMemcpyAsync(S.g_A + j * NN, S.g_E + j * slot, sizeof(c128) * NN, cudaMemcpyDeviceToDevice, st));
+      }
+      launch_axpby_identity<double>(N, S.g_A, NN, nq, -1.0, st);
+      launch_chol_inv_minus_I(N, S.g_E, nq * nc, NN, S.g_work, P->d_status, st);
+      for (int j = 0; j < nq; ++j) {
+        c128* U = S.g_U + (long long)j * N * k;
+        GW_TRY(modes_core(P, S.g_A + j * NN, U));
+        mode_diag(P, S.g_E + j * slot, nc, U, S.d_d + (long long)j * k * nc, nc, 0);
+      }
+      launch_sur_inputs(nq * k, nc, S.d_d, S.d_x, S.d_sig, st);
+      GW_TRY(sur_correction(S.model, S.d_x, nq * k, S.d_g, st));
+      launch_sur_coef(nq * k, nf, S.d_sig, S.d_g, S.d_coef, st);
+      for (int j = 0; j < nq; ++j) GW_TRY(w_core(P, q0 + j, S.g_E + j * slot, S.g_chi0 + j * slot));
+    }
+    for (int j = 0; j < nq; ++j)
+      GW_TRY(sigma_core_sur(P, q0 + j, S.g_chi0 + j * slot, S.g_U + (long long)j * N * k,
+                            S.d_coef + (long long)j * k * nf, sig));
+    GW_TRY(read_status(P, "gw_g0w0 (surrogate)"));
+  }
+  GW_TRY(P->collect_timing());
+  P->chi0_q = P->wc_q = -1;
+  return GW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_surrogate_enable(gw_plan P, gw_surrogate model, const gw_surrogate_cfg* cfg) {
+  gw_status s;
+  if (!plan_ok(P, 0, &s)) return s;
+  SurState& S = P->sur;
+  if (!cfg) {
+    if (model) return fail(GW_ERR_ARG, "gw_surrogate_enable: a model needs a configuration");
+    S.on = false;
+    S.model = nullptr;
+    return GW_OK;
+  }
+  const int N = P->N, nw = P->nw;
+  const int nc = cfg->n_coarse, k = cfg->n_modes, nb = cfg->n_block;
+  if (nc < 1 || nc > nw || nc > 64 || !cfg->coarse) return fail(GW_ERR_ARG, "gw_surrogate_enable: bad n_coarse / coarse");
+  for (int i = 0; i < nc; ++i) {
+    if (cfg->coarse[i] < 0 || cfg->coarse[i] >= nw || (i && cfg->coarse[i] <= cfg->coarse[i - 1]))
+      return fail(GW_ERR_ARG, "gw_surrogate_enable: coarse indices must be ascending grid indices");
+  }
+  if (nb < 1 || nb > 64 || nb > N || k < 1 || k > nb) return fail(GW_ERR_ARG, "gw_surrogate_enable: need 1 <= n_modes <= n_block <= min(64, n_aux)");
+  if (cfg->n_iter < 0 || cfg->n_iter > 1000 || !cfg->start) return fail(GW_ERR_ARG, "gw_surrogate_enable: bad n_iter or start");
+  if (model && (sur_n_in(model) != nc || sur_n_out(model) != nw - nc))
+    return fail(GW_ERR_ARG, "gw_surrogate_enable: the model's n_in / n_out must be n_coarse / n_freq - n_coarse");
+  if (S.d_jmap && (S.nc != nc || S.k != k || S.nb != nb))
+    return fail(GW_ERR_UNSUPPORTED, "gw_surrogate_enable: sizes cannot change once set on a plan");
+  cudaStream_t st = P->st;
+  S.coarse.assign(cfg->coarse, cfg->coarse + nc);
+  S.fine.clear();
+  std::vector<int> jmap(nw);
+  for (int j = 0, c = 0; j < nw; ++j) {
+    if (c < nc && S.coarse[c] == j) {
+      jmap[j] = c++;
+    } else {
+      jmap[j] = -(int)S.fine.size() - 1;
+      S.fine.push_back(j);
+    }
+  }
+  S.nc = nc;
+  S.nf = nw - nc;
+  S.k = k;
+  S.nb = nb;
+  S.iters = cfg->n_iter;
+  if (!S.d_jmap) {
+    const size_t rows = (size_t)P->sig_rows;
+    GW_TRY(dalloc(P, &S.d_jmap, nw));
+    GW_TRY(dalloc(P, &S.d_freq_c, nc));
+    GW_TRY(dalloc(P, &S.d_start, (size_t)N * nb));
+    GW_TRY(dalloc(P, &S.d_Y, (size_t)N * nb));
+    GW_TRY(dalloc(P, &S.d_Q, (size_t)N * nb));
+    GW_TRY(dalloc(P, &S.d_T, (size_t)N * nb));
+    GW_TRY(dalloc(P, &S.d_G, (size_t)nb * nb));
+    GW_TRY(dalloc(P, &S.d_Linv, (size_t)nb * nb));
+    GW_TRY(dalloc(P, &S.d_H, (size_t)nb * nb));
+    GW_TRY(dalloc(P, &S.d_Z, (size_t)nb * nb));
+    GW_TRY(dalloc(P, &S.d_theta, nb));
+    GW_TRY(dalloc(P, &S.d_A1, (size_t)N * N));
+    GW_TRY(dalloc(P, &S.d_U1, (size_t)N * k));
+    GW_TRY(dalloc(P, &S.d_XU, (size_t)std::max(nw, nc) * N * k));
+    GW_TRY(dalloc(P, &S.d_B, (size_t)N * k));
+    c128* pp = nullptr;
+    GW_TRY(dalloc(P, &pp, rows * k));
+    S.d_P = pp;
+    GW_TRY(dalloc(P, &S.d_Sc, rows * nc));
+    GW_TRY(dalloc(P, &S.d_Sc_d, rows * nc));
+  }
+  std::vector<double> fc(nc);
+  for (int i = 0; i < nc; ++i) fc[i] = P->freq[S.coarse[i]];
+  GW_CUDA(cudaMemcpyAsync(S.d_jmap, jmap.data(), sizeof(int) * nw, cudaMemcpyHostToDevice, st));
+  GW_CUDA(cudaMemcpyAsync(S.d_freq_c, fc.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st));
+  GW_CUDA(cudaMemcpyAsync(S.d_start, cfg->start, sizeof(c128) * N * nb, cudaMemcpyDeviceToDevice, st));
+  GW_CUDA(cudaStreamSynchronize(st));
+  S.model = model;
+  S.on = true;
+  return GW_OK;
+}
+
+gw_status gw_surrogate_modes(gw_plan P, int32_t sys, int32_t q, float* d_out, double* theta_out, float* x_out,
+                             float* y_out) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  SurState& S = P->sur;
+  if (!S.on) return fail(GW_ERR_STATE, "gw_surrogate_modes needs gw_surrogate_enable first");
+  if (q < 0 || q >= P->NK || (!d_out && !x_out && !y_out)) return fail(GW_ERR_ARG, "gw_surrogate_modes: bad q or no output");
+  if (y_out && S.nf < 1) return fail(GW_ERR_ARG, "gw_surrogate_modes: no fine frequencies for y_out");
+  if (P->chi0_q != q) return fail(GW_ERR_STATE, "gw_surrogate_modes needs gw_chi0 for the same q first");
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw;
+  const long long NN = (long long)N * N;
+  GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+  GW_TRY(eps_core(P, q, P->d_chi0, P->d_E));
+  GW_CUDA(cudaMemcpyAsync(S.d_A1, P->d_E + S.coarse[0] * NN, sizeof(c128) * NN, cudaMemcpyDeviceToDevice, st));
+  launch_axpby_identity<double>(N, S.d_A1, NN, 1, -1.0, st);
+  launch_chol_inv_minus_I(N, P->d_E, nw, NN, P->d_work, P->d_status, st);
+  GW_TRY(modes_core(P, S.d_A1, S.d_U1));
+  float* d = d_out ? d_out : reinterpret_cast<float*>(P->d_tmp);
+  mode_diag(P, P->d_E, nw, S.d_U1, d, nw, 0);
+  if (x_out || y_out) launch_sur_features(S.k, nw, S.coarse[0], S.d_jmap, d, S.nc, S.nf, x_out, y_out, st);
+  if (theta_out) GW_CUDA(cudaMemcpyAsync(theta_out, S.d_theta, sizeof(double) * S.k, cudaMemcpyDeviceToDevice, st));
+  GW_TRY(check_launch(P, "gw_surrogate_modes"));
+  return read_status(P, "gw_surrogate_modes");
 }
 
 }  // extern "C"

@@ -25,7 +25,7 @@ EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigm
            "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_kernel_launches",
            "gw_surrogate_param_count", "gw_surrogate_create", "gw_surrogate_destroy", "gw_surrogate_get_params",
            "gw_surrogate_set_params", "gw_surrogate_forward", "gw_surrogate_loss_grad", "gw_surrogate_fit_linear",
-           "gw_surrogate_train", "gw_last_error")
+           "gw_surrogate_train", "gw_surrogate_enable", "gw_surrogate_modes", "gw_last_error")
 
 
 class GwError(RuntimeError):
@@ -36,6 +36,12 @@ class GwError(RuntimeError):
 
 class gw_surrogate_dims(ctypes.Structure):
     _fields_ = [("n_in", ctypes.c_int32), ("n_hidden", ctypes.c_int32), ("n_out", ctypes.c_int32)]
+
+
+class gw_surrogate_cfg(ctypes.Structure):
+    _fields_ = [("n_coarse", ctypes.c_int32), ("coarse", ctypes.POINTER(ctypes.c_int32)),
+                ("n_modes", ctypes.c_int32), ("n_block", ctypes.c_int32), ("n_iter", ctypes.c_int32),
+                ("start", ctypes.c_void_p)]
 
 
 class gw_problem(ctypes.Structure):
@@ -99,6 +105,8 @@ def load():
     lib.gw_surrogate_loss_grad.argtypes = [vp, vp, vp, i64, dpp, vp]
     lib.gw_surrogate_fit_linear.argtypes = [vp, vp, vp, i64, ctypes.c_double, dpp]
     lib.gw_surrogate_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_double, u64, dpp]
+    lib.gw_surrogate_enable.argtypes = [vp, vp, ctypes.POINTER(gw_surrogate_cfg)]
+    lib.gw_surrogate_modes.argtypes = [vp, i32, i32, vp, vp, vp, vp]
     lib.gw_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "gw_last_error":
@@ -249,6 +257,22 @@ def gw_surrogate_train(model, x, y, epochs, batch, lr, seed):
     _check(load().gw_surrogate_train(model, _ptr(x), _ptr(y), x.shape[0], int(epochs), int(batch), float(lr),
                                      int(seed), hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return hist[:epochs]
+
+
+def gw_surrogate_enable(plan, model, coarse=None, n_modes=0, n_block=0, n_iter=0, start=None):
+    """coarse: host int list; start: device complex128 tensor [n_aux][n_block]. coarse None: detach."""
+    if coarse is None:
+        _check(load().gw_surrogate_enable(plan, model, None))
+        return None
+    c = np.ascontiguousarray(coarse, dtype=np.int32)
+    cfg = gw_surrogate_cfg(len(c), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(n_modes), int(n_block),
+                           int(n_iter), _ptr(start))
+    _check(load().gw_surrogate_enable(plan, model, ctypes.byref(cfg)))
+    return c
+
+
+def gw_surrogate_modes(plan, sys, q, d_out=None, theta_out=None, x_out=None, y_out=None):
+    _check(load().gw_surrogate_modes(plan, sys, q, _ptr(d_out), _ptr(theta_out), _ptr(x_out), _ptr(y_out)))
 
 
 # ---------------------------------------------------------------------------------------------

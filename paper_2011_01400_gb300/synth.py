@@ -234,3 +234,9 @@ def surrogate_init(n_in, n_hidden, n_out, seed=0, out_gain=0.01):
              out_gain * rng.standard_normal((O, H)) / np.sqrt(H), np.zeros(O),
              np.zeros((O, I)), np.ones(1)]
     return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def surrogate_start(n_aux, n_block, seed=0):
+    """Seeded complex Gaussian start block [n_aux][n_block] of the surrogate's subspace iteration."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((n_aux, n_block)) + 1j * rng.standard_normal((n_aux, n_block))
