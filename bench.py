@@ -233,6 +233,96 @@ def q_slice_ms(gw, s, prec, torch, q=1, reps=2):
     return plan_ms, best
 
 
+def surrogate_bench(args, gw, torch):
+    """Learned frequency surrogate on a 60-point grid with chi0 on 12 frequencies (every 5th,
+    the lowest included): training data from the plain method on seeded systems with the
+    workload's band/ABF shapes and a 2x2x2 k mesh; the linear map from the frequency moments of
+    eps~^-1 - 1 (ridge), the MLP by Adam on the mode rows, all on the GPU; then the whole
+    pass on the workload's k mesh against the full-grid plain pass (same precision)."""
+    from paper_2011_01400_gb300.synth import make_system, surrogate_init, surrogate_start
+    NW, k, nb, nit = 60, 32, 48, 8
+    coarse = list(range(0, NW, 5))
+    nc, nf = len(coarse), NW - len(coarse)
+    dims = (nc, 256, nf)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        out = fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return out, ev[0].elapsed_time(ev[1]) / 1e3
+
+    base = make_system(args.config, seed=0, n_freq=NW, nk=(2, 2, 2))
+    start = torch.from_numpy(surrogate_start(base.n_aux, nb, seed=9)).cuda()
+
+    mom = torch.zeros((nc, NW), dtype=torch.float64, device="cuda")
+
+    def features(sysm):
+        pb = gw.Problem(sysm, args.prec)
+        plan = gw.gw_plan_create(pb.prob)
+        x = torch.empty((sysm.n_k * k, nc), device="cuda")
+        y = torch.empty((sysm.n_k * k, nf), device="cuda")
+        try:
+            gw.gw_surrogate_enable(plan, None, coarse, k, nb, nit, start)
+            gw.gw_surrogate_data(plan, 0, x, y, mom)
+        finally:
+            gw.gw_plan_destroy(plan)
+        return x, y
+
+    def data():
+        X, Y = zip(*[features(make_system(args.config, seed=50000 + i, n_freq=NW, nk=(2, 2, 2)))
+                     for i in range(args.sur_systems)])
+        return torch.cat(X).contiguous(), torch.cat(Y).contiguous()
+
+    (X, Y), t_data = timed(data)
+    model = gw.gw_surrogate_create(*dims, torch.from_numpy(surrogate_init(*dims, seed=3)).cuda())
+    try:
+        def train():
+            gw.gw_surrogate_fit_moments(model, mom, 1e-10)
+            r = gw.gw_surrogate_fit_scale(model, X, Y)
+            h = gw.gw_surrogate_train(model, X, Y, args.sur_epochs, 256, 1e-3, 17)
+            return r, h
+        (rms, hist), t_train = timed(train)
+        ev_sys = make_system(args.config, seed=1000 * int(args.config[-1]) + 1, n_freq=NW)
+        pb = gw.Problem(ev_sys, args.prec)
+        nsig = ev_sys.sigma_hi - ev_sys.sigma_lo
+
+        def full_pass():
+            plan = gw.gw_plan_create(pb.prob)
+            try:
+                gw.gw_g0w0(plan, 0)
+                return gw.gw_qp(plan, 0, ev_sys.n_k, nsig)
+            finally:
+                gw.gw_plan_destroy(plan)
+
+        def sur_pass():
+            plan = gw.gw_plan_create(pb.prob)
+            try:
+                gw.gw_surrogate_enable(plan, model, coarse, k, nb, nit, start)
+                gw.gw_g0w0(plan, 0)
+                return gw.gw_qp(plan, 0, ev_sys.n_k, nsig)
+            finally:
+                gw.gw_plan_destroy(plan)
+
+        sur_pass()  # warm-up (group buffers, module loading)
+        (e_s, gap_s, _), t_sur = timed(sur_pass)
+        (e_f, gap_f, _), t_full = timed(full_pass)
+    finally:
+        gw.gw_surrogate_destroy(model)
+    ha = 27211.386
+    return dict(workload=f"{WORKLOADS[args.config]}, on a 60-point grid; chi0 / eps~ on 12 of them",
+                precision=args.prec, train_systems=args.sur_systems, train_rows=int(X.shape[0]),
+                train_data_s=t_data, train_s=t_train, epochs=args.sur_epochs,
+                linear_rms=rms, loss_first=float(hist[0]) if len(hist) else None,
+                loss_last=float(hist[-1]) if len(hist) else None,
+                surrogate_step_s=t_sur, full_grid_step_s=t_full, speedup=t_full / t_sur,
+                max_abs_dE_qp_meV=float(abs(e_s - e_f).max() * ha), abs_dgap_meV=float(abs(gap_s - gap_f) * ha),
+                judge="the plain method on the full 60-point grid, same precision, same system")
+
+
 def run_device(args, system, world, rank):
     import torch
     import torch.distributed as dist
@@ -339,6 +429,8 @@ def run_device(args, system, world, rank):
         fp64_gpu=fp64,
         gap_ha=gap,
     )
+    if args.surrogate:
+        line["surrogate"] = surrogate_bench(args, gw, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(s)
     print(json.dumps(line), flush=True)
@@ -358,6 +450,10 @@ def main():
     ap.add_argument("--qloop", default="g0w0", choices=["g0w0", "perq"],
                     help="q loop in one gw_g0w0 call (default) or as per-q gw_chi0/gw_screen/gw_sigma calls")
     ap.add_argument("--nk", default=None, help="override the k mesh, e.g. 4,4,4 (profiling captures)")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="also train the frequency surrogate and time it against the full 60-point grid")
+    ap.add_argument("--sur-systems", type=int, default=64, help="training systems of the surrogate")
+    ap.add_argument("--sur-epochs", type=int, default=40, help="training epochs of the surrogate")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -227,6 +227,15 @@ gw_status gw_surrogate_loss_grad(gw_surrogate model, const float* x, const float
 gw_status gw_surrogate_fit_linear(gw_surrogate model, const float* x, const float* y, int64_t n, double ridge,
                                   double* rms);
 
+/* Ridge fit of L from frequency moments (device FP64 [n_in][n_in + n_out], as accumulated by
+ * gw_surrogate_data): with G = moments[:, :n_in], R = moments[:, n_in:],
+ * (G + ridge * tr(G)/n_in * 1) L^T = R, solved in FP64 (Cholesky). s is not changed.
+ * Errors: GW_ERR_NOT_PD. */
+gw_status gw_surrogate_fit_moments(gw_surrogate model, const double* moments, double ridge);
+
+/* s = rms of the residual y - x L^T over n rows (s = 1 if that is 0); rms: host output or NULL. */
+gw_status gw_surrogate_fit_scale(gw_surrogate model, const float* x, const float* y, int64_t n, double* rms);
+
 /* Adam (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on W1..b4 over `epochs` passes of
  * mini-batches of `batch` rows (1..min(n, 4096)), rows shuffled every epoch with a generator
  * seeded by `seed` (the last n % batch rows of each shuffled epoch are skipped). L and s are
@@ -272,6 +281,16 @@ gw_status gw_surrogate_enable(gw_plan plan, gw_surrogate model, const gw_surroga
  * Needs gw_surrogate_enable. */
 gw_status gw_surrogate_modes(gw_plan plan, int32_t sys, int32_t q, float* d_out, double* theta_out, float* x_out,
                              float* y_out);
+
+/* The training data of all q of the plan at once:
+ *   x_out, y_out: the rows of gw_surrogate_modes for q = 0 .. N_k-1, in that order: device fp32
+ *     [N_k * n_modes][n_coarse] and [N_k * n_modes][n_freq - n_coarse];
+ *   moments (device FP64 [n_coarse][n_freq], or NULL): accumulated (the caller zeroes it) with
+ *     sum over q and all elements e of X = eps~^-1 - 1 of Re(conj(X_e(w_a)) X_e(w_b)), a coarse,
+ *     b the coarse frequencies then the fine ones (needs n_freq <= 64, n_coarse*n_freq <= 1024).
+ * q points run in groups (batched factorisations and modes) with the buffers of gw_g0w0.
+ * Needs gw_surrogate_enable; leaves no chi0 / W^c in the plan. */
+gw_status gw_surrogate_data(gw_plan plan, int32_t sys, float* x_out, float* y_out, double* moments);
 
 /* Text of the last error on the calling thread ("" if none). Never NULL. */
 const char* gw_last_error(void);

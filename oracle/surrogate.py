@@ -141,6 +141,21 @@ def fit_linear(x, y, ridge):
     return L, float(np.sqrt(np.mean(r * r)))
 
 
+def freq_moments(X, coarse, fine):
+    """Frequency moments of a stack X [nw][N][N]: m[a][b] = sum_e Re(conj(X_e(w_a)) X_e(w_b)),
+    a over the coarse frequencies, b over the coarse then the fine ones."""
+    Xf = X.reshape(X.shape[0], -1)
+    cols = list(coarse) + list(fine)
+    return (np.conj(Xf[list(coarse)]) @ Xf[cols].T).real
+
+
+def fit_moments(m, n_in, ridge):
+    """L from moments: (G + ridge tr(G)/n_in 1) L^T = R, G = m[:, :n_in], R = m[:, n_in:] (FP64)."""
+    G, R = m[:, :n_in], m[:, n_in:]
+    lam = ridge * np.trace(G) / n_in
+    return np.linalg.solve(G + lam * np.eye(n_in), R).T
+
+
 def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     """One Adam update (Kingma & Ba 2015, Algorithm 1), t counted from 1. Returns new (theta, m, v)."""
     m = beta1 * m + (1.0 - beta1) * grad

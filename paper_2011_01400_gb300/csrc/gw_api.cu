@@ -131,11 +131,16 @@ struct SurState {
   int nc = 0, nf = 0, k = 0, nb = 0, iters = 0;
   std::vector<int> coarse, fine;
   int* d_jmap = nullptr;       // [nw]: coarse position, or -(fine position + 1)
+  int *d_cidx = nullptr, *d_fidx = nullptr;  // grid indices of the coarse [nc] and fine [nf] frequencies
   double* d_freq_c = nullptr;  // [nc]
   c128* d_start = nullptr;     // [N][nb]
-  c128 *d_Y = nullptr, *d_Q = nullptr, *d_T = nullptr;               // [N][nb]
-  c128 *d_G = nullptr, *d_Linv = nullptr, *d_H = nullptr, *d_Z = nullptr;  // [nb][nb]
-  double* d_theta = nullptr;   // [nb]
+  int bcap = 0;                // problems the batch buffers below hold
+  c128 *d_Y = nullptr, *d_Q = nullptr, *d_T = nullptr;               // [bcap][N][nb]
+  c128 *d_G = nullptr, *d_Linv = nullptr, *d_H = nullptr, *d_Z = nullptr;  // [bcap][nb][nb]
+  double* d_theta = nullptr;   // [bcap][nb]
+  // training-data pass (gw_surrogate_data): per group of the full-grid q loop
+  c128 *g_Af = nullptr, *g_Uf = nullptr;  // [qb][N][N], [qb][N][k]
+  float* d_df = nullptr;                  // [qb * k][nw]
   c128* d_A1 = nullptr;        // [N][N] eps~(w_ref) - 1 of gw_surrogate_modes
   c128* d_U1 = nullptr;        // [N][k]
   c128* d_XU = nullptr;        // [max(nw, nc)][N][k]
@@ -862,6 +867,18 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig) {
 
 gw_status g0w0_sur(gw_plan_s* P, c128* sig);  // the surrogate pass, defined below
 
+// q-group buffers of gw_g0w0: chi0 (then W^c), eps~ (then eps~^-1 - 1), Cholesky scratch
+gw_status ensure_groups(gw_plan_s* P) {
+  if (P->g_chi0) return GW_OK;
+  const long long slot = (long long)P->N * P->N * P->nw;
+  const double per_q = 3.0 * sizeof(c128) * (double)slot;
+  P->qb = (int)std::max(1.0, std::min((double)P->NK, std::floor(8.0e9 / per_q)));
+  GW_TRY(dalloc(P, &P->g_chi0, (size_t)slot * P->qb));
+  GW_TRY(dalloc(P, &P->g_E, (size_t)slot * P->qb));
+  GW_TRY(dalloc(P, &P->g_work, (size_t)slot * P->qb));
+  return GW_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -919,14 +936,7 @@ gw_status gw_g0w0(gw_plan P, int32_t sys, gw_complex* sigma_acc) {
   const int N = P->N, nw = P->nw;
   const long long NN = (long long)N * N;
   const long long slot = NN * nw;
-  if (!P->g_chi0) {
-    // q-group buffers: chi0 (then W^c), eps~ (then eps~^-1 - 1), Cholesky scratch
-    const double per_q = 3.0 * sizeof(c128) * (double)slot;
-    P->qb = (int)std::max(1.0, std::min((double)P->NK, std::floor(8.0e9 / per_q)));
-    GW_TRY(dalloc(P, &P->g_chi0, (size_t)slot * P->qb));
-    GW_TRY(dalloc(P, &P->g_E, (size_t)slot * P->qb));
-    GW_TRY(dalloc(P, &P->g_work, (size_t)slot * P->qb));
-  }
+  GW_TRY(ensure_groups(P));
   c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
   P->reset_timing();
   for (int q0 = 0; q0 < P->NK; q0 += P->qb) {
@@ -1114,49 +1124,77 @@ struct FreqView {
   }
 };
 
-// Q = orth(Y) by two Cholesky-QR passes (Y and T are overwritten)
-void cholqr2(gw_plan_s* P, c128* Y, c128* Q) {
+// batch buffers of the mode computation for up to cap problems (grown, never shrunk)
+gw_status sur_ensure_batch(gw_plan_s* P, int cap) {
+  SurState& S = P->sur;
+  if (cap <= S.bcap) return GW_OK;
+  const size_t N = P->N, nb = S.nb, c = cap;
+  GW_TRY(dalloc(P, &S.d_Y, c * N * nb));
+  GW_TRY(dalloc(P, &S.d_Q, c * N * nb));
+  GW_TRY(dalloc(P, &S.d_T, c * N * nb));
+  GW_TRY(dalloc(P, &S.d_G, c * nb * nb));
+  GW_TRY(dalloc(P, &S.d_Linv, c * nb * nb));
+  GW_TRY(dalloc(P, &S.d_H, c * nb * nb));
+  GW_TRY(dalloc(P, &S.d_Z, c * nb * nb));
+  GW_TRY(dalloc(P, &S.d_theta, c * nb));
+  S.bcap = cap;
+  return GW_OK;
+}
+
+// Q_j = orth(Y_j), j < nq, by two Cholesky-QR passes (Y and T are overwritten)
+void cholqr2(gw_plan_s* P, int nq, c128* Y, c128* Q) {
   SurState& S = P->sur;
   const int N = P->N, nb = S.nb;
+  const long long sY = (long long)N * nb, sG = (long long)nb * nb;
   const c128 one{1, 0}, zero{0, 0};
   c128* in = Y;
   c128* outs[2] = {S.d_T, Q};
   for (int pass = 0; pass < 2; ++pass) {
-    launch_zgemm<double>(nb, nb, N, one, in, nb, 0, OP_C, in, nb, 0, OP_N, zero, S.d_G, nb, 0, 1, P->st);
-    launch_small_chol_linv(nb, S.d_G, S.d_Linv, P->d_status, P->st);
-    launch_zgemm<double>(N, nb, nb, one, in, nb, 0, OP_N, S.d_Linv, nb, 0, OP_C, zero, outs[pass], nb, 0, 1, P->st);
+    launch_zgemm<double>(nb, nb, N, one, in, nb, sY, OP_C, in, nb, sY, OP_N, zero, S.d_G, nb, sG, nq, P->st);
+    launch_small_chol_linv(nb, nq, S.d_G, S.d_Linv, P->d_status, P->st);
+    launch_zgemm<double>(N, nb, nb, one, in, nb, sY, OP_N, S.d_Linv, nb, sG, OP_C, zero, outs[pass], nb, sY, nq, P->st);
     in = outs[pass];
   }
 }
 
-// Ritz modes of the Hermitian A [N][N]: subspace iteration from the start block, Rayleigh-Ritz;
-// U_out [N][k] = the k Ritz vectors of largest Ritz value (S.d_theta holds all nb, descending)
-gw_status modes_core(gw_plan_s* P, const c128* A, c128* U_out) {
+// Ritz modes of nq Hermitian matrices A_j = A + j*sA [N][N]: subspace iteration from the start
+// block, Rayleigh-Ritz; U_j = U + j*sU [N][k] = the k Ritz vectors of largest Ritz value
+// (S.d_theta + j*nb holds all nb Ritz values of problem j, descending)
+gw_status modes_core(gw_plan_s* P, const c128* A, long long sA, int nq, c128* U, long long sU) {
   SurState& S = P->sur;
   const int N = P->N, nb = S.nb, k = S.k;
+  const long long sY = (long long)N * nb, sG = (long long)nb * nb;
   const c128 one{1, 0}, zero{0, 0};
   cudaStream_t st = P->st;
-  GW_CUDA(cudaMemcpyAsync(S.d_Y, S.d_start, sizeof(c128) * N * nb, cudaMemcpyDeviceToDevice, st));
-  cholqr2(P, S.d_Y, S.d_Q);
+  GW_TRY(sur_ensure_batch(P, nq));
+  for (int j = 0; j < nq; ++j)
+    GW_CUDA(cudaMemcpyAsync(S.d_Y + j * sY, S.d_start, sizeof(c128) * sY, cudaMemcpyDeviceToDevice, st));
+  cholqr2(P, nq, S.d_Y, S.d_Q);
   for (int it = 0; it < S.iters; ++it) {
-    launch_zgemm<double>(N, nb, N, one, A, N, 0, OP_N, S.d_Q, nb, 0, OP_N, zero, S.d_Y, nb, 0, 1, st);
-    cholqr2(P, S.d_Y, S.d_Q);
+    launch_zgemm<double>(N, nb, N, one, A, N, sA, OP_N, S.d_Q, nb, sY, OP_N, zero, S.d_Y, nb, sY, nq, st);
+    cholqr2(P, nq, S.d_Y, S.d_Q);
   }
-  launch_zgemm<double>(N, nb, N, one, A, N, 0, OP_N, S.d_Q, nb, 0, OP_N, zero, S.d_Y, nb, 0, 1, st);
-  launch_zgemm<double>(nb, nb, N, one, S.d_Q, nb, 0, OP_C, S.d_Y, nb, 0, OP_N, zero, S.d_H, nb, 0, 1, st);
-  launch_small_jacobi(nb, S.d_H, S.d_theta, S.d_Z, st);
-  launch_zgemm<double>(N, k, nb, one, S.d_Q, nb, 0, OP_N, S.d_Z, nb, 0, OP_N, zero, U_out, k, 0, 1, st);
+  launch_zgemm<double>(N, nb, N, one, A, N, sA, OP_N, S.d_Q, nb, sY, OP_N, zero, S.d_Y, nb, sY, nq, st);
+  launch_zgemm<double>(nb, nb, N, one, S.d_Q, nb, sY, OP_C, S.d_Y, nb, sY, OP_N, zero, S.d_H, nb, sG, nq, st);
+  launch_small_jacobi(nb, nq, S.d_H, S.d_theta, S.d_Z, st);
+  launch_zgemm<double>(N, k, nb, one, S.d_Q, nb, sY, OP_N, S.d_Z, nb, sG, OP_N, zero, U, k, sU, nq, st);
   return check_launch(P, "surrogate modes");
 }
 
-// d [k][ldd] (columns c0 ..) = mode diagonal of the nx matrices X [nx][N][N] in the basis U
-void mode_diag(gw_plan_s* P, const c128* X, int nx, const c128* U, float* d, int ldd, int c0) {
+// d rows j*k .. (j+1)*k-1, columns 0 .. nx-1 (leading dimension ldd): mode diagonal of the nx
+// matrices X + j*sX [nx][N][N] in the basis U + j*sU, for j < nq
+void mode_diag(gw_plan_s* P, const c128* X, long long sX, int nx, int nq, const c128* U, long long sU, float* d,
+               int ldd) {
   SurState& S = P->sur;
   const int N = P->N, k = S.k;
   const long long NN = (long long)N * N;
   const c128 one{1, 0}, zero{0, 0};
-  launch_zgemm<double>(N, k, N, one, X, N, NN, OP_N, U, k, 0, OP_N, zero, S.d_XU, k, (long long)N * k, nx, P->st);
-  launch_mode_diag(N, k, nx, U, S.d_XU, (long long)N * k, d, ldd, c0, P->st);
+  for (int j = 0; j < nq; ++j) {
+    const c128* Uj = U + j * sU;
+    launch_zgemm<double>(N, k, N, one, X + j * sX, N, NN, OP_N, Uj, k, 0, OP_N, zero, S.d_XU, k, (long long)N * k, nx,
+                         P->st);
+    launch_mode_diag(N, k, nx, Uj, S.d_XU, (long long)N * k, d + (long long)j * k * ldd, ldd, 0, P->st);
+  }
 }
 
 // q term of Sigma_c with W^c on the coarse frequencies (Wc_c [nc][N][N]), the modes U [N][k]
@@ -1260,11 +1298,8 @@ gw_status g0w0_sur(gw_plan_s* P, c128* sig) {
       }
       launch_axpby_identity<double>(N, S.g_A, NN, nq, -1.0, st);
       launch_chol_inv_minus_I(N, S.g_E, nq * nc, NN, S.g_work, P->d_status, st);
-      for (int j = 0; j < nq; ++j) {
-        c128* U = S.g_U + (long long)j * N * k;
-        GW_TRY(modes_core(P, S.g_A + j * NN, U));
-        mode_diag(P, S.g_E + j * slot, nc, U, S.d_d + (long long)j * k * nc, nc, 0);
-      }
+      GW_TRY(modes_core(P, S.g_A, NN, nq, S.g_U, (long long)N * k));
+      mode_diag(P, S.g_E, slot, nc, nq, S.g_U, (long long)N * k, S.d_d, nc);
       launch_sur_inputs(nq * k, nc, S.d_d, S.d_x, S.d_sig, st);
       GW_TRY(sur_correction(S.model, S.d_x, nq * k, S.d_g, st));
       launch_sur_coef(nq * k, nf, S.d_sig, S.d_g, S.d_coef, st);
@@ -1327,16 +1362,11 @@ gw_status gw_surrogate_enable(gw_plan P, gw_surrogate model, const gw_surrogate_
   if (!S.d_jmap) {
     const size_t rows = (size_t)P->sig_rows;
     GW_TRY(dalloc(P, &S.d_jmap, nw));
+    GW_TRY(dalloc(P, &S.d_cidx, nw));
+    GW_TRY(dalloc(P, &S.d_fidx, nw));
     GW_TRY(dalloc(P, &S.d_freq_c, nc));
     GW_TRY(dalloc(P, &S.d_start, (size_t)N * nb));
-    GW_TRY(dalloc(P, &S.d_Y, (size_t)N * nb));
-    GW_TRY(dalloc(P, &S.d_Q, (size_t)N * nb));
-    GW_TRY(dalloc(P, &S.d_T, (size_t)N * nb));
-    GW_TRY(dalloc(P, &S.d_G, (size_t)nb * nb));
-    GW_TRY(dalloc(P, &S.d_Linv, (size_t)nb * nb));
-    GW_TRY(dalloc(P, &S.d_H, (size_t)nb * nb));
-    GW_TRY(dalloc(P, &S.d_Z, (size_t)nb * nb));
-    GW_TRY(dalloc(P, &S.d_theta, nb));
+    GW_TRY(sur_ensure_batch(P, 1));
     GW_TRY(dalloc(P, &S.d_A1, (size_t)N * N));
     GW_TRY(dalloc(P, &S.d_U1, (size_t)N * k));
     GW_TRY(dalloc(P, &S.d_XU, (size_t)std::max(nw, nc) * N * k));
@@ -1350,6 +1380,9 @@ gw_status gw_surrogate_enable(gw_plan P, gw_surrogate model, const gw_surrogate_
   std::vector<double> fc(nc);
   for (int i = 0; i < nc; ++i) fc[i] = P->freq[S.coarse[i]];
   GW_CUDA(cudaMemcpyAsync(S.d_jmap, jmap.data(), sizeof(int) * nw, cudaMemcpyHostToDevice, st));
+  GW_CUDA(cudaMemcpyAsync(S.d_cidx, S.coarse.data(), sizeof(int) * nc, cudaMemcpyHostToDevice, st));
+  if (!S.fine.empty())
+    GW_CUDA(cudaMemcpyAsync(S.d_fidx, S.fine.data(), sizeof(int) * S.fine.size(), cudaMemcpyHostToDevice, st));
   GW_CUDA(cudaMemcpyAsync(S.d_freq_c, fc.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, st));
   GW_CUDA(cudaMemcpyAsync(S.d_start, cfg->start, sizeof(c128) * N * nb, cudaMemcpyDeviceToDevice, st));
   GW_CUDA(cudaStreamSynchronize(st));
@@ -1375,13 +1408,61 @@ gw_status gw_surrogate_modes(gw_plan P, int32_t sys, int32_t q, float* d_out, do
   GW_CUDA(cudaMemcpyAsync(S.d_A1, P->d_E + S.coarse[0] * NN, sizeof(c128) * NN, cudaMemcpyDeviceToDevice, st));
   launch_axpby_identity<double>(N, S.d_A1, NN, 1, -1.0, st);
   launch_chol_inv_minus_I(N, P->d_E, nw, NN, P->d_work, P->d_status, st);
-  GW_TRY(modes_core(P, S.d_A1, S.d_U1));
+  GW_TRY(modes_core(P, S.d_A1, 0, 1, S.d_U1, 0));
   float* d = d_out ? d_out : reinterpret_cast<float*>(P->d_tmp);
-  mode_diag(P, P->d_E, nw, S.d_U1, d, nw, 0);
+  mode_diag(P, P->d_E, 0, nw, 1, S.d_U1, 0, d, nw);
   if (x_out || y_out) launch_sur_features(S.k, nw, S.coarse[0], S.d_jmap, d, S.nc, S.nf, x_out, y_out, st);
   if (theta_out) GW_CUDA(cudaMemcpyAsync(theta_out, S.d_theta, sizeof(double) * S.k, cudaMemcpyDeviceToDevice, st));
   GW_TRY(check_launch(P, "gw_surrogate_modes"));
   return read_status(P, "gw_surrogate_modes");
+}
+
+}  // extern "C"
+
+extern "C" {
+
+gw_status gw_surrogate_data(gw_plan P, int32_t sys, float* x_out, float* y_out, double* moments) {
+  gw_status s;
+  if (!plan_ok(P, sys, &s)) return s;
+  SurState& S = P->sur;
+  if (!S.on) return fail(GW_ERR_STATE, "gw_surrogate_data needs gw_surrogate_enable first");
+  if (!x_out || !y_out || S.nf < 1) return fail(GW_ERR_ARG, "gw_surrogate_data: x_out / y_out NULL or no fine frequencies");
+  if (moments && (P->nw > 64 || S.nc * P->nw > 1024))
+    return fail(GW_ERR_UNSUPPORTED, "gw_surrogate_data: moments need n_freq <= 64 and n_coarse * n_freq <= 1024");
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw, k = S.k;
+  const long long NN = (long long)N * N, slot = NN * nw;
+  GW_TRY(ensure_groups(P));
+  if (!S.g_Af) {
+    GW_TRY(dalloc(P, &S.g_Af, (size_t)NN * P->qb));
+    GW_TRY(dalloc(P, &S.g_Uf, (size_t)N * k * P->qb));
+    GW_TRY(dalloc(P, &S.d_df, (size_t)P->qb * k * nw));
+  }
+  P->reset_timing();
+  for (int q0 = 0; q0 < P->NK; q0 += P->qb) {
+    const int nq = std::min(P->qb, P->NK - q0);
+    GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+    for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q0 + j, P->g_chi0 + j * slot));
+    for (int j = 0; j < nq; ++j) {
+      GW_TRY(eps_core(P, q0 + j, P->g_chi0 + j * slot, P->g_E + j * slot));
+      GW_CUDA(cudaMemcpyAsync(S.g_Af + j * NN, P->g_E + j * slot + S.coarse[0] * NN, sizeof(c128) * NN,
+                              cudaMemcpyDeviceToDevice, st));
+    }
+    launch_axpby_identity<double>(N, S.g_Af, NN, nq, -1.0, st);
+    launch_chol_inv_minus_I(N, P->g_E, nq * nw, NN, P->g_work, P->d_status, st);
+    GW_TRY(modes_core(P, S.g_Af, NN, nq, S.g_Uf, (long long)N * k));
+    mode_diag(P, P->g_E, slot, nw, nq, S.g_Uf, (long long)N * k, S.d_df, nw);
+    if (moments)
+      for (int j = 0; j < nq; ++j)
+        launch_freq_moments(nw, NN, P->g_E + j * slot, S.d_cidx, S.d_fidx, S.nc, S.nf, moments, st);
+    launch_sur_features(nq * k, nw, S.coarse[0], S.d_jmap, S.d_df, S.nc, S.nf, x_out + (long long)q0 * k * S.nc,
+                        y_out + (long long)q0 * k * S.nf, st);
+    GW_TRY(check_launch(P, "gw_surrogate_data"));
+    GW_TRY(read_status(P, "gw_surrogate_data"));
+  }
+  GW_TRY(P->collect_timing());
+  P->chi0_q = P->wc_q = -1;
+  return GW_OK;
 }
 
 }  // extern "C"

@@ -168,13 +168,15 @@ bool tc_available();
 void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st);
 
 // Ritz modes and the surrogate reconstruction (k_modes.cu); small sizes nb <= 64
-void launch_small_chol_linv(int nb, const c128* G, c128* Linv, int* status, cudaStream_t st);
-void launch_small_jacobi(int nb, const c128* H, double* theta, c128* Z, cudaStream_t st);
+void launch_small_chol_linv(int nb, int batch, const c128* G, c128* Linv, int* status, cudaStream_t st);
+void launch_small_jacobi(int nb, int batch, const c128* H, double* theta, c128* Z, cudaStream_t st);
 void launch_mode_diag(int N, int k, int nc, const c128* U, const c128* T, long long sT, float* d, int ldd, int c0,
                       cudaStream_t st);
 void launch_sur_inputs(int rows, int nc, const float* d, float* x, float* sig, cudaStream_t st);
 void launch_sur_features(int rows, int nw, int j0, const int* jmap, const float* d, int nc, int nf, float* x,
                          float* y, cudaStream_t st);
+void launch_freq_moments(int nw, long long NN, const c128* X, const int* cidx, const int* fidx, int nc, int nf,
+                         double* gram, cudaStream_t st);
 void launch_sur_coef(int rows, int nf, const float* sig, const float* g, float* coef, cudaStream_t st);
 template <typename T>
 void launch_sur_assemble(int R, int nc, int nw, int k, const int* jmap, const T* Sc, const cplx<T>* P,

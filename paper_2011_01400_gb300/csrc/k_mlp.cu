@@ -677,6 +677,48 @@ gw_status gw_surrogate_fit_linear(gw_surrogate m, const float* x, const float* y
   return finish(m, "gw_surrogate_fit_linear");
 }
 
+gw_status gw_surrogate_fit_moments(gw_surrogate m, const double* moments, double ridge) {
+  if (!m || !moments || !(ridge >= 0.0)) return mfail(GW_ERR_ARG, "surrogate: bad fit_moments arguments");
+  MLP_TRY(begin(m));
+  const int I = m->I, O = m->O;
+  double* G = m->d_acc + 2;
+  double* R = G + (size_t)I * I;
+  std::vector<double> h((size_t)I * (I + O));
+  MLP_CUDA(cudaMemcpyAsync(h.data(), moments, h.size() * sizeof(double), cudaMemcpyDeviceToHost, m->st));
+  MLP_CUDA(cudaMemcpy2DAsync(G, I * sizeof(double), moments, (I + O) * sizeof(double), I * sizeof(double), I,
+                             cudaMemcpyDeviceToDevice, m->st));
+  MLP_CUDA(cudaMemcpy2DAsync(R, O * sizeof(double), moments + I, (I + O) * sizeof(double), O * sizeof(double), I,
+                             cudaMemcpyDeviceToDevice, m->st));
+  MLP_CUDA(cudaMemsetAsync(m->d_status, 0, sizeof(int), m->st));
+  MLP_CUDA(cudaStreamSynchronize(m->st));
+  double tr = 0.0;
+  for (int i = 0; i < I; ++i) tr += h[(size_t)i * (I + O) + i];
+  ++g_launch_count, k_ridge_solve<<<1, 64, 0, m->st>>>(I, O, G, R, ridge * tr / I, m->th + m->off.L, m->d_status);
+  int stt = 0;
+  MLP_CUDA(cudaMemcpyAsync(&stt, m->d_status, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+  MLP_CUDA(cudaStreamSynchronize(m->st));
+  if (stt & ST_NOT_PD) return mfail(GW_ERR_NOT_PD, "surrogate: the coarse moment matrix + ridge is not positive definite");
+  return finish(m, "gw_surrogate_fit_moments");
+}
+
+gw_status gw_surrogate_fit_scale(gw_surrogate m, const float* x, const float* y, int64_t n, double* rms) {
+  if (!m || !x || !y || n < 1) return mfail(GW_ERR_ARG, "surrogate: bad fit_scale arguments");
+  MLP_TRY(begin(m));
+  const int I = m->I, O = m->O;
+  MLP_CUDA(cudaMemsetAsync(m->d_acc, 0, sizeof(double), m->st));
+  ++g_launch_count, k_lin_resid<<<ew_grid(n * O), 256, 0, m->st>>>(n, I, O, x, y, m->th + m->off.L, m->d_acc);
+  double ss = 0.0;
+  MLP_CUDA(cudaMemcpyAsync(&ss, m->d_acc, sizeof(double), cudaMemcpyDeviceToHost, m->st));
+  MLP_CUDA(cudaStreamSynchronize(m->st));
+  const double r = std::sqrt(ss / ((double)n * O));
+  const float sc = (r > 0.0 && std::isfinite(r)) ? (float)r : 1.f;
+  MLP_CUDA(cudaMemcpyAsync(m->th + m->off.s, &sc, sizeof(float), cudaMemcpyHostToDevice, m->st));
+  MLP_CUDA(cudaStreamSynchronize(m->st));
+  m->h_s = sc;
+  if (rms) *rms = r;
+  return finish(m, "gw_surrogate_fit_scale");
+}
+
 gw_status gw_surrogate_train(gw_surrogate m, const float* x, const float* y, int64_t n, int32_t epochs, int32_t batch,
                              double lr, uint64_t seed, double* loss_hist) {
   if (!m || !x || !y || n < 1 || n > (int64_t)1 << 30 || epochs < 0 || batch < 1 || batch > 4096 || batch > n ||

@@ -6,6 +6,7 @@
 // and the reconstruction of S_nm on the fine frequencies (k_sur_assemble).
 #include "gw_internal.h"
 
+#include <algorithm>
 #include <cmath>
 
 namespace gw {
@@ -20,11 +21,14 @@ __device__ __forceinline__ c128 addc(c128 a, c128 b) { return c128{a.re + b.re, 
 __device__ __forceinline__ c128 scal(double s, c128 a) { return c128{s * a.re, s * a.im}; }
 
 // G (Hermitian [nb][nb], lower part read) = L L^H; writes Linv = L^-1 (lower, zeros above).
+// One block per problem of a batch (consecutive [nb][nb] matrices).
 // A pivot that is not positive sets ST_NOT_PD and is replaced by a tiny positive value.
 __global__ void __launch_bounds__(256) k_small_chol_linv(int nb, const c128* __restrict__ G, c128* __restrict__ Linv,
                                                          int* __restrict__ status) {
   extern __shared__ c128 L[];
   const int t = threadIdx.x;
+  G += (long long)blockIdx.x * nb * nb;
+  Linv += (long long)blockIdx.x * nb * nb;
   for (int e = t; e < nb * nb; e += blockDim.x) L[e] = G[e];
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
@@ -66,12 +70,15 @@ __global__ void __launch_bounds__(256) k_small_chol_linv(int nb, const c128* __r
 // disjoint pairs (circle ordering). Rotation of pair (p, q), c = A_pq = |c| u:
 //   tau = (A_qq - A_pp) / (2|c|), t = sign(tau) / (|tau| + sqrt(1 + tau^2)), cs = 1/sqrt(1+t^2), sn = t cs,
 //   G = [[cs, sn], [-sn conj(u), cs conj(u)]]:  A <- G^H A G,  Z <- Z G.
-// Output: theta [nb] descending, Z columns in the same order.
+// Output: theta [nb] descending, Z columns in the same order. One block per problem of a batch.
 __global__ void __launch_bounds__(256) k_small_jacobi(int nb, const c128* __restrict__ H, double* __restrict__ theta,
                                                       c128* __restrict__ Zout, int max_sweeps) {
   extern __shared__ c128 sm[];
   c128* A = sm;
   c128* Z = sm + nb * nb;
+  H += (long long)blockIdx.x * nb * nb;
+  Zout += (long long)blockIdx.x * nb * nb;
+  theta += (long long)blockIdx.x * nb;
   __shared__ int sp[32], sq[32];
   __shared__ double scs[32], ssn[32];
   __shared__ c128 su[32];
@@ -239,6 +246,41 @@ __global__ void k_sur_features(int rows, int nw, int j0, const int* __restrict__
   }
 }
 
+// frequency moments of X [nw][NN]: gram[a][b] += sum_e Re(conj(X[c_a][e]) X[j_b][e]) for the
+// coarse a < nc and b < nc + nf (b < nc: coarse index, else fine); blocks split e
+__global__ void __launch_bounds__(256) k_freq_moments(int nw, long long NN, const c128* __restrict__ X,
+                                                      const int* __restrict__ cidx, const int* __restrict__ fidx,
+                                                      int nc, int nf, long long per_block, double* __restrict__ gram) {
+  __shared__ c128 xs[32][64];
+  const long long e0 = blockIdx.x * per_block, e1 = min(NN, e0 + per_block);
+  const int npair = nc * (nc + nf);
+  double acc[4] = {0, 0, 0, 0};  // pairs tid, tid + 256, ... (npair <= 64 * 16 = 1024)
+  for (long long eb = e0; eb < e1; eb += 32) {
+    const int ne = (int)min((long long)32, e1 - eb);
+    for (int t = threadIdx.x; t < 32 * nw; t += blockDim.x) {
+      const int r = t / nw, j = t % nw;
+      xs[r][j] = (r < ne) ? X[(long long)j * NN + eb + r] : c128{0, 0};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int pidx = threadIdx.x + 256 * i;
+      if (pidx >= npair) break;
+      const int a = pidx / (nc + nf), b = pidx % (nc + nf);
+      const int ja = cidx[a], jb = b < nc ? cidx[b] : fidx[b - nc];
+      double sacc = 0.0;
+      for (int r = 0; r < ne; ++r) sacc += xs[r][ja].re * xs[r][jb].re + xs[r][ja].im * xs[r][jb].im;
+      acc[i] += sacc;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int pidx = threadIdx.x + 256 * i;
+    if (pidx < npair) atomicAdd(&gram[pidx], acc[i]);
+  }
+}
+
 // coef[l][m] = sig_l * g[l][m]
 __global__ void k_sur_coef(int rows, int nf, const float* __restrict__ sig, const float* __restrict__ g,
                            float* __restrict__ coef) {
@@ -274,24 +316,24 @@ __global__ void k_sur_assemble(int R, int nc, int nw, int k, const int* __restri
 
 }  // namespace
 
-void launch_small_chol_linv(int nb, const c128* G, c128* Linv, int* status, cudaStream_t st) {
+void launch_small_chol_linv(int nb, int batch, const c128* G, c128* Linv, int* status, cudaStream_t st) {
   const size_t sm = (size_t)nb * nb * sizeof(c128);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_small_chol_linv, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 64 * (int)sizeof(c128));
     attr = true;
   }
-  ++g_launch_count, k_small_chol_linv<<<1, 256, sm, st>>>(nb, G, Linv, status);
+  ++g_launch_count, k_small_chol_linv<<<batch, 256, sm, st>>>(nb, G, Linv, status);
 }
 
-void launch_small_jacobi(int nb, const c128* H, double* theta, c128* Z, cudaStream_t st) {
+void launch_small_jacobi(int nb, int batch, const c128* H, double* theta, c128* Z, cudaStream_t st) {
   const size_t sm = 2 * (size_t)nb * nb * sizeof(c128);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_small_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * (int)sizeof(c128));
     attr = true;
   }
-  ++g_launch_count, k_small_jacobi<<<1, 256, sm, st>>>(nb, H, theta, Z, 40);
+  ++g_launch_count, k_small_jacobi<<<batch, 256, sm, st>>>(nb, H, theta, Z, 40);
 }
 
 void launch_mode_diag(int N, int k, int nc, const c128* U, const c128* T, long long sT, float* d, int ldd, int c0,
@@ -306,6 +348,13 @@ void launch_sur_inputs(int rows, int nc, const float* d, float* x, float* sig, c
 void launch_sur_features(int rows, int nw, int j0, const int* jmap, const float* d, int nc, int nf, float* x,
                          float* y, cudaStream_t st) {
   ++g_launch_count, k_sur_features<<<(rows + 127) / 128, 128, 0, st>>>(rows, nw, j0, jmap, d, nc, nf, x, y);
+}
+
+void launch_freq_moments(int nw, long long NN, const c128* X, const int* cidx, const int* fidx, int nc, int nf,
+                         double* gram, cudaStream_t st) {
+  const long long per_block = std::max(256LL, (NN + 151) / 152);
+  const int blocks = (int)((NN + per_block - 1) / per_block);
+  ++g_launch_count, k_freq_moments<<<blocks, 256, 0, st>>>(nw, NN, X, cidx, fidx, nc, nf, per_block, gram);
 }
 
 void launch_sur_coef(int rows, int nf, const float* sig, const float* g, float* coef, cudaStream_t st) {

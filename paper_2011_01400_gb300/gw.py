@@ -25,7 +25,8 @@ EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigm
            "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_kernel_launches",
            "gw_surrogate_param_count", "gw_surrogate_create", "gw_surrogate_destroy", "gw_surrogate_get_params",
            "gw_surrogate_set_params", "gw_surrogate_forward", "gw_surrogate_loss_grad", "gw_surrogate_fit_linear",
-           "gw_surrogate_train", "gw_surrogate_enable", "gw_surrogate_modes", "gw_last_error")
+           "gw_surrogate_train", "gw_surrogate_enable", "gw_surrogate_modes", "gw_surrogate_data", "gw_surrogate_fit_moments",
+           "gw_surrogate_fit_scale", "gw_last_error")
 
 
 class GwError(RuntimeError):
@@ -107,6 +108,9 @@ def load():
     lib.gw_surrogate_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_double, u64, dpp]
     lib.gw_surrogate_enable.argtypes = [vp, vp, ctypes.POINTER(gw_surrogate_cfg)]
     lib.gw_surrogate_modes.argtypes = [vp, i32, i32, vp, vp, vp, vp]
+    lib.gw_surrogate_data.argtypes = [vp, i32, vp, vp, vp]
+    lib.gw_surrogate_fit_moments.argtypes = [vp, vp, ctypes.c_double]
+    lib.gw_surrogate_fit_scale.argtypes = [vp, vp, vp, i64, dpp]
     lib.gw_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name != "gw_last_error":
@@ -273,6 +277,20 @@ def gw_surrogate_enable(plan, model, coarse=None, n_modes=0, n_block=0, n_iter=0
 
 def gw_surrogate_modes(plan, sys, q, d_out=None, theta_out=None, x_out=None, y_out=None):
     _check(load().gw_surrogate_modes(plan, sys, q, _ptr(d_out), _ptr(theta_out), _ptr(x_out), _ptr(y_out)))
+
+
+def gw_surrogate_data(plan, sys, x_out, y_out, moments=None):
+    _check(load().gw_surrogate_data(plan, sys, _ptr(x_out), _ptr(y_out), _ptr(moments)))
+
+
+def gw_surrogate_fit_moments(model, moments, ridge):
+    _check(load().gw_surrogate_fit_moments(model, _ptr(moments), float(ridge)))
+
+
+def gw_surrogate_fit_scale(model, x, y):
+    rms = ctypes.c_double()
+    _check(load().gw_surrogate_fit_scale(model, _ptr(x), _ptr(y), x.shape[0], ctypes.byref(rms)))
+    return rms.value
 
 
 # ---------------------------------------------------------------------------------------------

@@ -187,3 +187,18 @@ def test_reconstruction_mode_diagonal_is_network_output():
         got = S.mode_diag(U, X[fine])
         assert np.allclose(got, sg[:, None] * f, rtol=0, atol=1e-12 * max(1.0, np.abs(got).max()))
         assert np.allclose(S.mode_diag(U, X[coarse]), d, atol=1e-13)
+
+
+def test_fit_moments_is_least_squares_over_matrix_elements():
+    """Fitting L from frequency moments = least squares over the real and imaginary parts of
+    every element (brute force with lstsq on the stacked elements)."""
+    rng = np.random.default_rng(13)
+    nw, N = 7, 5
+    X = rng.standard_normal((3, nw, N, N)) + 1j * rng.standard_normal((3, nw, N, N))
+    coarse, fine = [0, 3, 6], [1, 2, 4, 5]
+    m = sum(S.freq_moments(Xq, coarse, fine) for Xq in X)
+    L = S.fit_moments(m, 3, 0.0)
+    A = np.concatenate([np.concatenate([Xq[coarse].reshape(3, -1).real, Xq[coarse].reshape(3, -1).imag], 1) for Xq in X], 1).T
+    B = np.concatenate([np.concatenate([Xq[fine].reshape(4, -1).real, Xq[fine].reshape(4, -1).imag], 1) for Xq in X], 1).T
+    L_ref = np.linalg.lstsq(A, B, rcond=None)[0].T
+    assert np.allclose(L, L_ref, atol=1e-12)

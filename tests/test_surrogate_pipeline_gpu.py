@@ -98,24 +98,47 @@ def test_surrogate_g0w0_matches_oracle(prec, tol_mev):
     assert abs(gap - ref["gap"]) * HA_MEV <= tol_mev
 
 
-def gpu_mode_features(gw, s, coarse, k, nb, nit, start, prec="fp64"):
-    """(x, y) training rows of one system from the plain method on the full grid (GPU)."""
+def gpu_mode_features(gw, s, coarse, k, nb, nit, start, prec="fp64", moments=None):
+    """(x, y) training rows of one system from the plain method on the full grid (GPU); the
+    frequency moments of eps~^-1 - 1 are added into `moments` when given."""
     nc, nf = len(coarse), s.n_freq - len(coarse)
     pb = gw.Problem(s, prec)
     plan = gw.gw_plan_create(pb.prob)
-    xs, ys = [], []
+    x = torch.empty((s.n_k * k, nc), device="cuda")
+    y = torch.empty((s.n_k * k, nf), device="cuda")
+    try:
+        gw.gw_surrogate_enable(plan, None, coarse, k, nb, nit, start)
+        gw.gw_surrogate_data(plan, 0, x, y, moments)
+    finally:
+        gw.gw_plan_destroy(plan)
+    return x, y
+
+
+def test_data_pass_matches_per_q_modes():
+    from paper_2011_01400_gb300 import gw
+    s = make_system("cfg0", seed=8, n_freq=20)
+    coarse, k, nb, nit = [0, 5, 10, 15], 6, 12, 5
+    start = cdev(surrogate_start(s.n_aux, nb, seed=4))
+    mom = torch.zeros((len(coarse), s.n_freq), dtype=torch.float64, device="cuda")
+    x_all, y_all = gpu_mode_features(gw, s, coarse, k, nb, nit, start, moments=mom)
+    fine = [j for j in range(s.n_freq) if j not in coarse]
+    om, _ = O.freq_grid(s.n_freq, s.omega0)
+    mom_ref = sum(S.freq_moments(S.inverse_minus_one(O.screen(s, q, O.chi0(s, q, om), om)[0]), coarse, fine)
+                  for q in range(s.n_k))
+    assert np.abs(mom.cpu().numpy() - mom_ref).max() <= 1e-10 * np.abs(mom_ref).max()
+    pb = gw.Problem(s, "fp64")
+    plan = gw.gw_plan_create(pb.prob)
     try:
         gw.gw_surrogate_enable(plan, None, coarse, k, nb, nit, start)
         for q in range(s.n_k):
             gw.gw_chi0(plan, 0, q)
-            x = torch.empty((k, nc), device="cuda")
-            y = torch.empty((k, nf), device="cuda")
+            x = torch.empty((k, 4), device="cuda")
+            y = torch.empty((k, 16), device="cuda")
             gw.gw_surrogate_modes(plan, 0, q, None, None, x, y)
-            xs.append(x)
-            ys.append(y)
+            assert torch.allclose(x, x_all[q * k:(q + 1) * k], rtol=0, atol=1e-6)
+            assert torch.allclose(y, y_all[q * k:(q + 1) * k], rtol=0, atol=1e-6)
     finally:
         gw.gw_plan_destroy(plan)
-    return torch.cat(xs), torch.cat(ys)
 
 
 def surrogate_qp(gw, s, model, coarse, k, nb, nit, start, prec):
@@ -133,8 +156,9 @@ def surrogate_qp(gw, s, model, coarse, k, nb, nit, start, prec):
 
 
 def test_trained_surrogate_gains_over_the_coarse_method():
-    """Train on the plain method's data of 8 systems (GPU), evaluate on a ninth: with chi0 on
-    12 of 60 frequencies, the surrogate's QP energies and gap against the full 60-point FP64
+    """Train on the plain method's data of 8 systems (GPU): L from the frequency moments of
+    eps~^-1 - 1, then Adam on the MLP over the mode rows. Evaluate on a ninth system: with chi0
+    on 12 of 60 frequencies, the surrogate's QP energies and gap against the full 60-point FP64
     method, next to the plain method on a 12-point grid (the same chi0 work without the
     network) and the surrogate with its MLP switched off (linear part only)."""
     from paper_2011_01400_gb300 import gw
@@ -143,14 +167,16 @@ def test_trained_surrogate_gains_over_the_coarse_method():
     dims = (len(coarse), 256, NW - len(coarse))
     start_np = surrogate_start(96, nb, seed=9)
     start = cdev(start_np)
-    X, Y = zip(*[gpu_mode_features(gw, make_system("cfg0", seed=100 + i, n_freq=NW), coarse, k, nb, nit, start)
-                 for i in range(8)])
+    mom = torch.zeros((len(coarse), NW), dtype=torch.float64, device="cuda")
+    X, Y = zip(*[gpu_mode_features(gw, make_system("cfg0", seed=100 + i, n_freq=NW), coarse, k, nb, nit, start,
+                                   moments=mom) for i in range(8)])
     X, Y = torch.cat(X).contiguous(), torch.cat(Y).contiguous()
     s = make_system("cfg0", seed=7, n_freq=NW)
     Xv, Yv = gpu_mode_features(gw, s, coarse, k, nb, nit, start)
     model = gw.gw_surrogate_create(*dims, fdev(surrogate_init(*dims, seed=3)))
     try:
-        rms_lin = gw.gw_surrogate_fit_linear(model, X, Y, 1e-8)
+        gw.gw_surrogate_fit_moments(model, mom, 1e-10)
+        rms_lin = gw.gw_surrogate_fit_scale(model, X, Y)
         f = torch.empty_like(Yv)
         gw.gw_surrogate_forward(model, Xv, f)
         val_lin = float(torch.sqrt(torch.mean((f - Yv) ** 2)))
