@@ -172,6 +172,14 @@ gw_status gw_plan_mu(gw_plan plan, double* mu);
  * and its algorithmic flop count (8 per complex multiply-add, Hermitian lower triangle). */
 gw_status gw_plan_last_chi0_stats(gw_plan plan, double* ms, double* flops);
 
+/* Weight rows the split-precision chi0 contraction used for the last q. The frequency
+ * compression writes the Lorentzian weight matrix W [n_freq][pairs] as E V with T <= n_freq rows
+ * in V, T the smallest count for which every frequency's row keeps a relative residual
+ * |W_j - (E V)_j| / |W_j| <= 3e-8 (FP64 over all pairs); chi0(w_j) = sum_t E_jt C_t.
+ * 0 before the first split-precision chi0; compression is off on the FP64 path and for
+ * n_freq < 4 or > 64. */
+gw_status gw_plan_chi0_terms(gw_plan plan, int32_t* terms);
+
 /* Number of CUDA kernels this library has launched in the calling process so far (host-side count). */
 gw_status gw_kernel_launches(uint64_t* count);
 

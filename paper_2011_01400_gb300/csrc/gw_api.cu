@@ -192,6 +192,7 @@ struct gw_plan_s {
   float* d_delta_f = nullptr;
   c128* d_pq = nullptr;       // [ldm]
   void* d_A = nullptr;        // sigma rows [R][N]
+  void* d_Apl[2] = {};        // split precision: bf16 / tf32 pieces of the sigma rows [R][2*Kx]
   void* d_U = nullptr;        // [R][N]
   double* d_S_d = nullptr;    // [R][nw]
   float* d_S_f = nullptr;
@@ -201,6 +202,18 @@ struct gw_plan_s {
   int n_bpl = 0;
   int seg_rows = 2048;        // pair rows per FP64 promotion segment of the tensor-core chi0
   float* d_wtab = nullptr;    // [nw][ldm] Lorentzian weights
+  // frequency compression of the split-precision chi0 (k_compress.cu)
+  // largest relative residual |W_j - sum_{t<T} E_jt v_t| / |W_j| over the frequencies j that the
+  // compression may leave (computed in FP64 over all pair rows); 0 disables. 3e-8 is below the
+  // fp32 rounding of the weights themselves
+  double compress_tol = 3e-8;
+  c128 *d_wG = nullptr, *d_wU = nullptr, *d_C = nullptr;  // [NK][nw][nw], [NK][nw][nw], [nw][N][N]
+  double* d_wlam = nullptr;   // [NK][nw]
+  double *d_wn = nullptr, *d_wE = nullptr, *d_wP = nullptr, *d_werr = nullptr;  // [NK][nw], [NK][nw][nw] x2,
+                                                                               // [NK][nw][nw+1]
+  int comp_q0 = -1, comp_nq = 0, comp_nw = 0;  // q range (and grid size) whose weight spectra are ready
+  std::vector<int> comp_T;    // components kept per q of that range
+  int last_T = 0;             // components kept for the last q
   int Kx = 0;                 // n_aux rounded up to 32 (K of the Sigma contraction)
   PlaneSet d_Wpl{};           // W^c split planes [nw*N][2*Kx]
   c64* d_Vh32 = nullptr;      // FP32 copies of V^1/2 for the split-precision screen
@@ -532,6 +545,11 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
     P->d_M = a;
     P->d_A = b;
     ALLOC(P->d_S_f, (size_t)P->sig_rows * nw);
+    for (int i = 0; i < 2; ++i) {
+      uint8_t* pp;
+      ALLOC(pp, (size_t)P->sig_rows * 2 * P->Kx * (P->prec == GW_3XTF32 ? 4 : 2));
+      P->d_Apl[i] = pp;
+    }
     const size_t we = (size_t)nw * N * 2 * P->Kx * (P->prec == GW_3XTF32 ? 4 : 2);
     for (int i = 0; i < (P->prec == GW_3XTF32 ? 4 : 6); ++i) {
       uint8_t* pp;
@@ -557,6 +575,17 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
     }
     ALLOC(P->d_wtab, (size_t)nw * P->ldm);
     if (const char* e = std::getenv("GW_CHI0_SEG_ROWS")) P->seg_rows = std::max(32, std::atoi(e));
+    if (const char* e = std::getenv("GW_CHI0_COMPRESS_TOL")) P->compress_tol = std::max(0.0, std::atof(e));
+    if (nw <= 64) {
+      ALLOC(P->d_wG, (size_t)nw * nw * P->NK);
+      ALLOC(P->d_wU, (size_t)nw * nw * P->NK);
+      ALLOC(P->d_wlam, (size_t)nw * P->NK);
+      ALLOC(P->d_wn, (size_t)nw * P->NK);
+      ALLOC(P->d_wE, (size_t)nw * nw * P->NK);
+      ALLOC(P->d_wP, (size_t)nw * nw * P->NK);
+      ALLOC(P->d_werr, (size_t)nw * (nw + 1) * P->NK);
+      ALLOC(P->d_C, (size_t)nw * NN);
+    }
   }
   ALLOC(P->d_delta, P->ldm);
   ALLOC(P->d_delta_f, P->ldm);
@@ -657,6 +686,12 @@ gw_status gw_plan_mu(gw_plan P, double* mu) {
   return GW_OK;
 }
 
+gw_status gw_plan_chi0_terms(gw_plan P, int32_t* terms) {
+  if (!P || !terms) return fail(GW_ERR_ARG, "NULL argument");
+  *terms = P->last_T;
+  return GW_OK;
+}
+
 gw_status gw_plan_last_chi0_stats(gw_plan P, double* ms, double* flops) {
   if (!P) return fail(GW_ERR_ARG, "plan is NULL");
   if (ms) *ms = P->last_chi0_ms;
@@ -669,6 +704,67 @@ gw_status gw_plan_last_chi0_stats(gw_plan P, double* ms, double* flops) {
 namespace {
 
 // chi0(q) into `chi0` ([nw][N][N], FP64). Records CUDA events around the contraction launches.
+bool compress_on(const gw_plan_s* P) {
+  return !P->fp64 && P->compress_tol > 0.0 && P->d_wG && P->nw >= 4 && P->nw <= 64;
+}
+
+// Weight bases of q0 .. q0+nq-1 for the frequency compression of chi0: the Gram matrix of the
+// weight rows over all pair rows of q (FP64), normalised, its eigen-decomposition (one batched
+// Jacobi), the expansion / projection matrices, and T_q = the smallest number of components whose
+// per-frequency residual (computed directly over all pair rows) is within compress_tol for every
+// frequency. One host synchronisation per call.
+gw_status chi0_prepare(gw_plan_s* P, int q0, int nq) {
+  if (!compress_on(P)) return GW_OK;
+  cudaStream_t st = P->st;
+  const int nw = P->nw, na = P->nunocc, nb = P->nocc;
+  const long long sG = (long long)nw * nw;
+  GW_CUDA(cudaMemsetAsync(P->d_wG, 0, sizeof(c128) * sG * nq, st));
+  for (int j = 0; j < nq; ++j) {
+    for (int kk0 = 0; kk0 < P->NK; kk0 += P->chi_nkk) {
+      const int nkk = std::min(P->chi_nkk, P->NK - kk0);
+      launch_pairs(P->NK, P->NBd, P->p.nk, q0 + j, kk0, nkk, P->nocc, na, 0, nb, P->p.eps, nullptr, P->p.qhat,
+                   P->d_delta, P->d_delta_f, nullptr, st);
+      launch_wgram(nkk * na * nb, nw, P->d_delta, P->d_freq, P->d_wG + j * sG, st);
+    }
+  }
+  launch_wnorm(nw, nq, P->d_wG, P->d_wn, st);
+  launch_small_jacobi(nw, nq, P->d_wG, P->d_wlam, P->d_wU, st);
+  launch_wproj(nw, nq, P->d_wU, P->d_wn, P->d_wE, P->d_wP, st);
+  const long long sE = (long long)nw * (nw + 1);
+  GW_CUDA(cudaMemsetAsync(P->d_werr, 0, sizeof(double) * sE * nq, st));
+  for (int j = 0; j < nq; ++j) {
+    for (int kk0 = 0; kk0 < P->NK; kk0 += P->chi_nkk) {
+      const int nkk = std::min(P->chi_nkk, P->NK - kk0);
+      launch_pairs(P->NK, P->NBd, P->p.nk, q0 + j, kk0, nkk, P->nocc, na, 0, nb, P->p.eps, nullptr, P->p.qhat,
+                   P->d_delta, P->d_delta_f, nullptr, st);
+      launch_wresid(nkk * na * nb, nw, P->d_delta, P->d_freq, P->d_wE + j * sG, P->d_wP + j * sG, P->d_werr + j * sE,
+                    st);
+    }
+  }
+  std::vector<double> er((size_t)sE * nq);
+  GW_CUDA(cudaMemcpyAsync(er.data(), P->d_werr, sizeof(double) * er.size(), cudaMemcpyDeviceToHost, st));
+  GW_CUDA(cudaStreamSynchronize(st));
+  P->comp_T.assign(nq, nw);
+  for (int j = 0; j < nq; ++j) {
+    const double* e = er.data() + (size_t)j * sE;
+    for (int T = 1; T <= nw; ++T) {
+      double worst = 0.0;
+      for (int f = 0; f < nw; ++f) {
+        const double n2 = e[f * (nw + 1)];
+        if (n2 > 0.0) worst = std::max(worst, std::sqrt(std::max(e[f * (nw + 1) + T], 0.0) / n2));
+      }
+      if (worst <= P->compress_tol) {
+        P->comp_T[j] = T;
+        break;
+      }
+    }
+  }
+  P->comp_q0 = q0;
+  P->comp_nq = nq;
+  P->comp_nw = nw;
+  return check_launch(P, "chi0 weight spectra");
+}
+
 gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
   cudaStream_t st = P->st;
   const int N = P->N, nw = P->nw;
@@ -684,6 +780,17 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
   }
   const double scale = -P->p.spin / P->NK;
   const int na = P->nunocc, nb = P->nocc;
+  // frequency compression (split precision): chi0(w_j) = sum_t U_jt C_t over T <= nw weight rows
+  const bool comp = compress_on(P);
+  int T = nw;
+  const double* Uw = nullptr;
+  if (comp) {
+    if (q < P->comp_q0 || q >= P->comp_q0 + P->comp_nq || P->comp_nw != nw) GW_TRY(chi0_prepare(P, q, 1));
+    T = P->comp_T[q - P->comp_q0];
+    Uw = P->d_wE + (long long)(q - P->comp_q0) * nw * nw;
+    P->last_T = T;
+    GW_CUDA(cudaMemsetAsync(P->d_C, 0, sizeof(c128) * NN * T, st));
+  }
   for (int kk0 = 0; kk0 < P->NK; kk0 += P->chi_nkk) {
     const int nkk = std::min(P->chi_nkk, P->NK - kk0);
     const int K = nkk * na * nb;
@@ -726,13 +833,18 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
       for (int i = 0; i < 6; ++i) a.bpl[i] = P->d_Pb[i];
       a.delta = P->d_delta_f;
       a.freq = P->d_freq;
-      a.nw = nw;
+      a.nw = comp ? T : nw;
       a.scale = scale;
-      a.chi0 = chi0;
+      a.chi0 = comp ? P->d_C : chi0;
       a.tf32 = tf32;
       a.status = P->d_status;
       a.seg_rows = P->seg_rows;
       a.wtab = P->d_wtab;
+      if (comp) {
+        launch_wtab_compressed(K, (int)P->ldm, nw, T, P->d_delta, P->d_freq,
+                               P->d_wP + (long long)(q - P->comp_q0) * nw * nw, P->d_wtab, st);
+        a.wtab_ready = 1;
+      }
       std::string err;
       GW_CUDA(cudaEventRecord(e0, st));
       gw_status ts = tc_chi0_run(a, P->tcws, st, err);
@@ -751,6 +863,7 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
     }
     GW_TRY(check_launch(P, "chi0"));
   }
+  if (comp) launch_expand(nw, T, (long long)NN, Uw, P->d_C, chi0, st);
   if (!P->fp64) tc_herm_fill(N, nw, chi0, st);
   P->chi0_flops_acc += 8.0 * (double)P->NK * na * nb * ((double)N * (N + 1) / 2) * nw;
   return GW_OK;
@@ -849,6 +962,8 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig) {
       a.raw = reinterpret_cast<const float*>(A);
       for (int i = 0; i < 6; ++i) a.bpl[i] = P->d_Wpl.b[i];
       a.S = P->d_S_f;
+      a.apl[0] = P->d_Apl[0];
+      a.apl[1] = P->d_Apl[1];
       a.tf32 = tf32;
       a.status = P->d_status;
       std::string err;
@@ -942,6 +1057,7 @@ gw_status gw_g0w0(gw_plan P, int32_t sys, gw_complex* sigma_acc) {
   for (int q0 = 0; q0 < P->NK; q0 += P->qb) {
     const int nq = std::min(P->qb, P->NK - q0);
     GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+    GW_TRY(chi0_prepare(P, q0, nq));
     for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q0 + j, P->g_chi0 + j * slot));
     for (int j = 0; j < nq; ++j) GW_TRY(eps_core(P, q0 + j, P->g_chi0 + j * slot, P->g_E + j * slot));
     launch_chol_inv_minus_I(N, P->g_E, nq * nw, NN, P->g_work, P->d_status, st);
@@ -1244,6 +1360,8 @@ gw_status sigma_core_sur(gw_plan_s* P, int q, const c128* Wc_c, const c128* U, c
       a.raw = reinterpret_cast<const float*>(A);
       for (int i = 0; i < 6; ++i) a.bpl[i] = P->d_Wpl.b[i];
       a.S = S.d_Sc;
+      a.apl[0] = P->d_Apl[0];
+      a.apl[1] = P->d_Apl[1];
       a.tf32 = tf32;
       a.status = P->d_status;
       std::string err;
@@ -1291,6 +1409,7 @@ gw_status g0w0_sur(gw_plan_s* P, c128* sig) {
     GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
     {
       FreqView fv(P, nc, S.d_freq_c);
+      GW_TRY(chi0_prepare(P, q0, nq));
       for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q0 + j, S.g_chi0 + j * slot));
       for (int j = 0; j < nq; ++j) {
         GW_TRY(eps_core(P, q0 + j, S.g_chi0 + j * slot, S.g_E + j * slot));
@@ -1442,6 +1561,7 @@ gw_status gw_surrogate_data(gw_plan P, int32_t sys, float* x_out, float* y_out, 
   for (int q0 = 0; q0 < P->NK; q0 += P->qb) {
     const int nq = std::min(P->qb, P->NK - q0);
     GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+    GW_TRY(chi0_prepare(P, q0, nq));
     for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q0 + j, P->g_chi0 + j * slot));
     for (int j = 0; j < nq; ++j) {
       GW_TRY(eps_core(P, q0 + j, P->g_chi0 + j * slot, P->g_E + j * slot));

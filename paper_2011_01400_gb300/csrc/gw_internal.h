@@ -137,6 +137,7 @@ struct TcChi0Args {
   int* status;
   int seg_rows;     // pair rows per FP64 promotion segment
   float* wtab;      // workspace [nw][Kpad] for the Lorentzian weights
+  int wtab_ready;   // 1: wtab already holds the nw weight rows (frequency compression), 0: fill it
 };
 struct PlaneSet {
   void* b[6];       // B1 pieces then B2 pieces
@@ -157,6 +158,8 @@ struct TcSigmaArgs {
   int nw;
   const float* raw; // [R][2*Kpad] fp32 (re, im) of a_r (zero beyond n_aux)
   const void* bpl[6];  // W^c planes [nw*N][2*Kpad] (B1 pieces then B2 pieces)
+  void* apl[2];     // A pieces [R][2*Kpad] (bf16 or tf32), written by tc_sigma_run from raw before the
+                    // launch; NULL: the kernel splits the rows itself
   float* S;         // [R][nw] accumulated (zeroed by the caller)
   int tf32;
   int* status;
@@ -181,6 +184,16 @@ void launch_sur_coef(int rows, int nf, const float* sig, const float* g, float* 
 template <typename T>
 void launch_sur_assemble(int R, int nc, int nw, int k, const int* jmap, const T* Sc, const cplx<T>* P,
                          const float* coef, int nf, const float* L, T* S, cudaStream_t st);
+
+// frequency compression of chi0 (k_compress.cu)
+void launch_wgram(int K, int nw, const double* delta, const double* freq, c128* G, cudaStream_t st);
+void launch_wnorm(int nw, int batch, c128* G, double* nrm, cudaStream_t st);
+void launch_wproj(int nw, int batch, const c128* Uh, const double* nrm, double* E, double* Pm, cudaStream_t st);
+void launch_wresid(int K, int nw, const double* delta, const double* freq, const double* E, const double* Pm,
+                   double* err, cudaStream_t st);
+void launch_wtab_compressed(int K, int Kpad, int nw, int T, const double* delta, const double* freq, const double* Pm,
+                            float* wtab, cudaStream_t st);
+void launch_expand(int nw, int T, long long NN, const double* E, const c128* C, c128* chi0, cudaStream_t st);
 
 // text returned by gw_last_error() on this thread
 void gw_set_last_error(const std::string& msg);

@@ -217,6 +217,7 @@ struct TcParams {
 struct Maps {
   CUtensorMap b[6];   // B1 pieces then B2 pieces
   CUtensorMap raw;    // A-side fp32 plane, 32 floats x 128 rows per box
+  CUtensorMap a[3];   // PRE: A-side pieces, split before the launch (128 B x 128 rows per box)
 };
 
 template <int MODE>
@@ -253,7 +254,7 @@ __device__ __forceinline__ bool is_seg_end(const TcParams& p, int i, int i0, int
   return (i % F) == F - 1 || i == nst - 1;
 }
 
-template <bool TF32, int NPC, int MODE>
+template <bool TF32, int NPC, int MODE, bool PRE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps maps, TcParams p) {
   using C = Cfg<TF32, NPC>;
   constexpr int NP = C::NP, STAGES = C::STAGES, STAGE = C::STAGE, RS = C::RS, RPS = C::RPS, RING = C::RING;
@@ -278,7 +279,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_b[s], 1);
-      mbar_init(&full_a[s], 128);
+      mbar_init(&full_a[s], PRE ? 1 : 128);
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -325,6 +326,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
             tma_load_2d(st + pc * TILE, &maps.b[pc], &full_b[s], x, yrow);              // B1 rows 0..63
             tma_load_2d(st + pc * TILE + HALF, &maps.b[NP + pc], &full_b[s], x, yrow);  // B2 rows 64..127
           }
+        }
+      }
+    }
+  } else if (warp == 14 && PRE) {
+    // ---------------- TMA producer: A pieces (split before the launch) into the stages ----------------
+    if (lane == 0) {
+      uint32_t gs = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+        int m0, n0, w;
+        decode_item<MODE>(p, item, m0, n0, w);
+        for (int i = first_stage<MODE, RS>(p, n0); i < nst; ++i, ++gs) {
+          const int s = gs % STAGES;
+          if (!mbar_wait(&empty[s], ((gs / STAGES) & 1) ^ 1, p.status)) { ok = false; break; }
+          uint8_t* at = smem + s * STAGE + NP * TILE;
+          mbar_arrive_expect_tx(&full_a[s], NP * TILE);
+          const int x = i * (ROWB / (TF32 ? 4 : 2));
+#pragma unroll
+          for (int pc = 0; pc < NP; ++pc) tma_load_2d(at + pc * TILE, &maps.a[pc], &full_a[s], x, m0);
         }
       }
     }
@@ -401,7 +421,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
       mma_commit(done);
       mbar_wait(done, 0, p.status);
     }
-  } else if (warp >= 2 && warp <= 5) {
+  } else if (warp >= 2 && warp <= 5 && !PRE) {
     // ---------------- transform: weighted, split A operand ----------------
     const int row = threadIdx.x - 64;          // 0..127
     uint32_t gs = 0, gr = 0;
@@ -612,6 +632,24 @@ __global__ void k_herm_fill(int N, int nw, c128* chi0) {
   }
 }
 
+// A pieces of an fp32 (re, im) plane [rows][ldk] for the pre-split path, two pieces:
+// BF16: h = bf16(y), l = bf16(y - h);  TF32: h = tf32(y), l = y - h (read as TF32 by the MMA).
+__global__ void k_a_planes(long long n, const float* __restrict__ raw, void* p0, void* p1, int tf32) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float2 y = reinterpret_cast<const float2*>(raw)[e];
+    if (tf32) {
+      const float hr = tf32_rn(y.x), hi = tf32_rn(y.y);
+      reinterpret_cast<float2*>(p0)[e] = make_float2(hr, hi);
+      reinterpret_cast<float2*>(p1)[e] = make_float2(y.x - hr, y.y - hi);
+    } else {
+      const __nv_bfloat162 hh = __floats2bfloat162_rn(y.x, y.y);
+      const float2 hf = __bfloat1622float2(hh);
+      reinterpret_cast<__nv_bfloat162*>(p0)[e] = hh;
+      reinterpret_cast<__nv_bfloat162*>(p1)[e] = __floats2bfloat162_rn(y.x - hf.x, y.y - hf.y);
+    }
+  }
+}
+
 // B planes of W^c for the Sigma contraction: row (j, nu), K index 2 mu + {0, 1}:
 // B1 = split(Re W_{nu mu}, Im W_{nu mu}), B2 = split(-Im, Re); mu >= N is zero padding.
 __global__ void k_w_planes(int N, int nw, int Kpad, const c128* __restrict__ Wc, PlaneSet P, int tf32, int np) {
@@ -707,12 +745,12 @@ int num_sms() {
   return n;
 }
 
-template <bool TF32, int NPC, int MODE>
+template <bool TF32, int NPC, int MODE, bool PRE = false>
 gw_status launch_tc(const Maps& maps, const TcParams& p, cudaStream_t st, std::string& err) {
   const int smem = Cfg<TF32, NPC>::SMEM;
-  cudaFuncSetAttribute(k_tc<TF32, NPC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_tc<TF32, NPC, MODE, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int grid = std::min(p.n_items, num_sms());
-  ++::gw::g_launch_count, k_tc<TF32, NPC, MODE><<<grid, NTHREADS, smem, st>>>(maps, p);
+  ++::gw::g_launch_count, k_tc<TF32, NPC, MODE, PRE><<<grid, NTHREADS, smem, st>>>(maps, p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("k_tc launch: ") + cudaGetErrorString(e);
@@ -786,8 +824,9 @@ gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std
     err = std::string("tc_chi0 tile table: ") + cudaGetErrorString(e);
     return GW_ERR_CUDA;
   }
-  ++::gw::g_launch_count, k_weights<<<std::min<long long>(((long long)a.nw * a.Kpad + 255) / 256, 152 * 32), 256, 0, st>>>(
-      a.Kpad, a.nw, a.delta, a.freq, a.wtab);
+  if (!a.wtab_ready)
+    ++::gw::g_launch_count, k_weights<<<std::min<long long>(((long long)a.nw * a.Kpad + 255) / 256, 152 * 32), 256, 0, st>>>(
+        a.Kpad, a.nw, a.delta, a.freq, a.wtab);
   TcParams p{};
   p.Mrows = a.N;
   p.Ncols = a.N;
@@ -830,6 +869,14 @@ gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, s
   for (int i = 0; i < 2 * NP; ++i)
     if (!make_map(&maps.b[i], a.bpl[i], tf32, ldk, (long long)a.nw * a.N, BN, err)) return GW_ERR_CUDA;
   if (!make_map(&maps.raw, a.raw, 1, ldk, a.R, BM, err)) return GW_ERR_CUDA;
+  const bool pre = a.apl[0] != nullptr && a.apl[1] != nullptr;
+  if (pre) {
+    const long long n = (long long)a.R * a.Kpad;   // complex elements
+    ++::gw::g_launch_count, k_a_planes<<<std::min<long long>((n + 255) / 256, 152 * 64), 256, 0, st>>>(
+        n, a.raw, a.apl[0], a.apl[1], tf32 ? 1 : 0);
+    for (int i = 0; i < NP; ++i)
+      if (!make_map(&maps.a[i], a.apl[i], tf32, ldk, a.R, BM, err)) return GW_ERR_CUDA;
+  }
   TcParams p{};
   p.Mrows = a.R;
   p.Ncols = a.N;
@@ -848,6 +895,7 @@ gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, s
   p.S = a.S;
   p.tri = 1;
   p.status = a.status;
+  if (pre) return tf32 ? launch_tc<true, 2, 1, true>(maps, p, st, err) : launch_tc<false, 2, 1, true>(maps, p, st, err);
   return tf32 ? launch_tc<true, 2, 1>(maps, p, st, err) : launch_tc<false, 2, 1>(maps, p, st, err);
 }
 
