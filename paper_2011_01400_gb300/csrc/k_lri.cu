@@ -133,6 +133,112 @@ __device__ __forceinline__ void mgen_body(const cplx<T>* __restrict__ T1, const 
   }
 }
 
+// Shared-memory form for fp32 (split-precision path). For one k' and a tile of MGT ABFs of one
+// atom A (j, i run over the n_b(A) basis functions of A):
+//   M^mu_{ab} = sum_j cK_{jb} conj(T1q^mu_{ja}) + sum_i conj(cQ_{ia}) T1k^mu_{ib}
+//   cK = c(k')[A][b-range], cQ = c(k'+q)[A][a-range], T1q^mu = T1^mu(k'+q)[.][a-range], T1k^mu = T1^mu(k')[.][b-range]
+// i.e. a complex product of K = 2 n_b(A) per ABF. The block stages cK, cQ and the T1 slices of its
+// ABFs in shared memory (fp32) once; threads run over (mu, a, b) outputs with the K loop in
+// shared memory. Tiles never straddle atoms (tile t -> atom by the cumulative tile counts).
+constexpr int MGT = 4;
+
+__device__ __forceinline__ bool mgen_tile(const LriGeom& g, int t, int& A, int& mu0, int& cnt) {
+  for (A = 0; A < g.n_atoms; ++A) {
+    const int nt = (g.atom_nx[A] + MGT - 1) / MGT;
+    if (t < nt) {
+      mu0 = g.atom_x0[A] + t * MGT;
+      cnt = min(MGT, g.atom_x0[A] + g.atom_nx[A] - mu0);
+      return true;
+    }
+    t -= nt;
+  }
+  return false;
+}
+
+template <typename Store>
+__device__ __forceinline__ void mgen_smem_body(const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0,
+                                               int mode, int a0, int na, int b0, int nb, Store store) {
+  extern __shared__ float2 sm2[];
+  const LriGeom& g = c_geom;
+  const int kk = blockIdx.x;
+  int A, mu0, cnt;
+  if (!mgen_tile(g, blockIdx.y, A, mu0, cnt)) return;
+  int ktgt = kk0 + kk;
+  int k3 = ktgt % g.nk[2], k2 = (ktgt / g.nk[2]) % g.nk[1], k1 = ktgt / (g.nk[1] * g.nk[2]);
+  int q3 = q % g.nk[2], q2 = (q / g.nk[2]) % g.nk[1], q1 = q / (g.nk[1] * g.nk[2]);
+  int kp;
+  if (mode == MAP_K_IS_KK) {
+    kp = ktgt;
+  } else {
+    kp = (((k1 - q1 + g.nk[0]) % g.nk[0]) * g.nk[1] + ((k2 - q2 + g.nk[1]) % g.nk[1])) * g.nk[2] +
+         ((k3 - q3 + g.nk[2]) % g.nk[2]);
+  }
+  const int p3 = kp % g.nk[2], p2 = (kp / g.nk[2]) % g.nk[1], p1 = kp / (g.nk[1] * g.nk[2]);
+  const int kpq = (((p1 + q1) % g.nk[0]) * g.nk[1] + ((p2 + q2) % g.nk[1])) * g.nk[2] + ((p3 + q3) % g.nk[2]);
+  const int nbA = g.atom_nb[A], b0A = g.atom_b0[A];
+  // shared layout (float2): cK [nbA][nb], cQ [nbA][na], T1q [MGT][nbA][na], T1k [MGT][nbA][nb]
+  float2* cK = sm2;
+  float2* cQ = cK + nbA * nb;
+  float2* tq = cQ + nbA * na;
+  float2* tk = tq + MGT * nbA * na;
+  const c128* ck = evec + (long long)kp * g.NB * g.NBd;
+  const c128* ckq = evec + (long long)kpq * g.NB * g.NBd;
+  for (int e = threadIdx.x; e < nbA * nb; e += blockDim.x) {
+    const c128 v = ck[(long long)(b0A + e / nb) * g.NBd + b0 + e % nb];
+    cK[e] = make_float2((float)v.re, (float)v.im);
+  }
+  for (int e = threadIdx.x; e < nbA * na; e += blockDim.x) {
+    const c128 v = ckq[(long long)(b0A + e / na) * g.NBd + a0 + e % na];
+    cQ[e] = make_float2((float)v.re, (float)v.im);
+  }
+  for (int e = threadIdx.x; e < cnt * nbA * na; e += blockDim.x) {
+    const int m = e / (nbA * na), rest = e % (nbA * na), j = rest / na, a = rest % na;
+    const c64 v = T1[g.t_off[A] + (((long long)kpq * g.atom_nx[A] + (mu0 - g.atom_x0[A] + m)) * nbA + j) * g.NBd + a0 + a];
+    tq[e] = make_float2(v.re, v.im);
+  }
+  for (int e = threadIdx.x; e < cnt * nbA * nb; e += blockDim.x) {
+    const int m = e / (nbA * nb), rest = e % (nbA * nb), j = rest / nb, b = rest % nb;
+    const c64 v = T1[g.t_off[A] + (((long long)kp * g.atom_nx[A] + (mu0 - g.atom_x0[A] + m)) * nbA + j) * g.NBd + b0 + b];
+    tk[e] = make_float2(v.re, v.im);
+  }
+  __syncthreads();
+  const int npair = na * nb;
+  for (int idx = threadIdx.x; idx < cnt * npair; idx += blockDim.x) {
+    const int m = idx / npair, pr = idx % npair, a = pr / nb, b = pr % nb;
+    const float2* tqm = tq + m * nbA * na;
+    const float2* tkm = tk + m * nbA * nb;
+    float sr = 0.f, si = 0.f;
+    for (int j = 0; j < nbA; ++j) {
+      const float2 c = cK[j * nb + b], t = tqm[j * na + a];     // c conj(t)
+      sr = fmaf(c.x, t.x, fmaf(c.y, t.y, sr));
+      si = fmaf(c.y, t.x, fmaf(-c.x, t.y, si));
+      const float2 d = cQ[j * na + a], u = tkm[j * nb + b];     // conj(d) u
+      sr = fmaf(d.x, u.x, fmaf(d.y, u.y, sr));
+      si = fmaf(d.x, u.y, fmaf(-d.y, u.x, si));
+    }
+    store(((long long)kk * na + a) * nb + b, mu0 + m, sr, si);
+  }
+}
+
+int mgen_tiles(const LriGeom& g) {
+  int t = 0;
+  for (int A = 0; A < g.n_atoms; ++A) t += (g.atom_nx[A] + MGT - 1) / MGT;
+  return t;
+}
+
+size_t mgen_smem(const LriGeom& g, int na, int nb) {
+  int nbA = 0;
+  for (int A = 0; A < g.n_atoms; ++A) nbA = std::max(nbA, g.atom_nb[A]);
+  return sizeof(float2) * (size_t)nbA * (na + nb) * (1 + MGT);
+}
+
+__global__ void k_mgen_smem(const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int mode, int a0,
+                            int na, int b0, int nb, c64* __restrict__ out, long long s_r, long long s_mu) {
+  mgen_smem_body(T1, evec, q, kk0, mode, a0, na, b0, nb, [&](long long r, int mu, float re, float im) {
+    out[r * s_r + (long long)mu * s_mu] = c64{re, im};
+  });
+}
+
 template <typename T>
 __global__ void k_mgen(const cplx<T>* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int mode,
                        int a0, int na, int b0, int nb, cplx<T>* __restrict__ out, long long s_r, long long s_mu) {
@@ -151,8 +257,27 @@ void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* /*T2*/, con
 }
 template void launch_mgen<double>(const LriGeom&, const c128*, const c128*, const c128*, int, int, int, MapMode, int,
                                   int, int, int, c128*, long long, long long, cudaStream_t);
-template void launch_mgen<float>(const LriGeom&, const c64*, const c64*, const c128*, int, int, int, MapMode, int,
-                                 int, int, int, c64*, long long, long long, cudaStream_t);
+
+// fp32: the shared-memory kernel when its staging fits, else the plain one
+template <>
+void launch_mgen<float>(const LriGeom& g, const c64* T1, const c64* T2, const c128* evec, int q, int kk0, int nkk,
+                        MapMode mode, int a0, int na, int b0, int nb, c64* out, long long s_r, long long s_mu,
+                        cudaStream_t st) {
+  const size_t sm = mgen_smem(g, na, nb);
+  if (sm > 200 * 1024) {
+    cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
+    dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
+    ++::gw::g_launch_count, k_mgen<float><<<grid, 256, 0, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r,
+                                                                s_mu);
+    return;
+  }
+  (void)T2;
+  cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
+  cudaFuncSetAttribute(k_mgen_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  dim3 grid(nkk, mgen_tiles(g));
+  ++::gw::g_launch_count, k_mgen_smem<<<grid, 256, sm, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r,
+                                                            s_mu);
+}
 
 // Operand planes for the tensor-core chi0 (row mu, K index kofs + 2r + {0, 1}):
 //   raw:  fp32 (re, im) of M^mu_r -- read by the transform warps that build the weighted A side;
@@ -173,9 +298,10 @@ struct PlanePtrs {
   void* b[6];      // B1 pieces then B2 pieces
 };
 
+template <bool SMEM>
 __global__ void k_mgen_planes(const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int a0,
                               int na, int b0, int nb, PlanePtrs P, long long ldk, long long kofs, int tf32) {
-  mgen_body<float>(T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, [&](long long r, int mu, float re, float im) {
+  auto st = [&](long long r, int mu, float re, float im) {
     const long long e = (long long)mu * ldk + kofs + 2 * r;
     *reinterpret_cast<float2*>(P.raw + e) = make_float2(re, im);
     const float v1[2] = {re, im}, v2[2] = {-im, re};
@@ -201,7 +327,11 @@ __global__ void k_mgen_planes(const c64* __restrict__ T1, const c128* __restrict
         *reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(P.b[3 * half + 2]) + e) = l;
       }
     }
-  });
+  };
+  if constexpr (SMEM)
+    mgen_smem_body(T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
+  else
+    mgen_body<float>(T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
 }
 
 void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
@@ -211,8 +341,17 @@ void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q
   PlanePtrs P{};
   P.raw = raw;
   for (int i = 0; i < (tf32 ? 4 : 6); ++i) P.b[i] = bplanes[i];
-  dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
-  ++::gw::g_launch_count, k_mgen_planes<<<grid, 256, 0, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs, tf32);
+  const size_t sm = mgen_smem(g, na, nb);
+  if (sm <= 200 * 1024) {
+    cudaFuncSetAttribute(k_mgen_planes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    dim3 grid(nkk, mgen_tiles(g));
+    ++::gw::g_launch_count, k_mgen_planes<true><<<grid, 256, sm, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
+                                                                       tf32);
+  } else {
+    dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
+    ++::gw::g_launch_count, k_mgen_planes<false><<<grid, 256, 0, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
+                                                                        tf32);
+  }
 }
 
 }  // namespace gw
