@@ -23,6 +23,8 @@
 // biases a long sum by ~3e-8 relative per accumulation. So:
 //   * hh goes to accumulator D1, which is drained after every stage (4 MMAs per output)
 //     into FP32 running sums held in registers by the epilogue warps (round to nearest);
+//     MODE 1 sums only K = n_aux (at most 52 MMAs per item), so there D1 is drained once per
+//     segment like D2 (the truncation bias stays ~1e-6 relative of S, far inside the budget);
 //   * the correction products (2^-8 smaller) go to D2, drained once per segment;
 //   * after each segment the running sums are added in FP64 into the output (MODE 0), or
 //     dotted with a and added to S (MODE 1, one segment per work item).
@@ -378,10 +380,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
         const int i0 = first_stage<MODE, RS>(p, n0);
         for (int i = i0; i < nst; ++i, ++gs) {
           const int s = gs % STAGES;
-          const int b = gs & 1;
           const int b2 = gseg & 1;
+          // MODE 0 drains D1 after every stage; MODE 1 (K <= n_aux) once per segment, like D2
+          const int b = (MODE == 0) ? (gs & 1) : b2;
           const bool seg_first = is_seg_first<MODE, RS>(p, i, i0, F);
-          if (gs >= 2 && !mbar_wait(&t1empty[b], ((gs >> 1) - 1) & 1, p.status)) { ok = false; break; }
+          if constexpr (MODE == 0) {
+            if (gs >= 2 && !mbar_wait(&t1empty[b], ((gs >> 1) - 1) & 1, p.status)) { ok = false; break; }
+          } else {
+            if (seg_first && gseg >= 2 && !mbar_wait(&t1empty[b], ((gseg >> 1) - 1) & 1, p.status)) {
+              ok = false;
+              break;
+            }
+          }
           if (seg_first && gseg >= 2 && !mbar_wait(&t2empty[b2], ((gseg >> 1) - 1) & 1, p.status)) {
             ok = false;
             break;
@@ -396,7 +406,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             const uint32_t ko = kk * 32;
-            const uint32_t acc1 = kk == 0 ? 0u : 1u;
+            const uint32_t acc1 = (MODE == 0) ? (kk == 0 ? 0u : 1u) : ((seg_first && kk == 0) ? 0u : 1u);
             const uint32_t acc2 = (seg_first && kk == 0) ? 0u : 1u;
             const uint64_t A0 = sdesc(abase + ko), B0 = sdesc(bbase + ko);
             const uint64_t A1 = sdesc(abase + TILE + ko), B1 = sdesc(bbase + TILE + ko);
@@ -411,8 +421,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
             }
           }
           mma_commit(&empty[s]);
-          mma_commit(&t1full[b]);
+          if constexpr (MODE == 0) mma_commit(&t1full[b]);
           if (is_seg_end<MODE, RS>(p, i, i0, F, nst)) {
+            if constexpr (MODE == 1) mma_commit(&t1full[b]);
             mma_commit(&t2full[b2]);
             ++gseg;
           }
@@ -525,26 +536,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
 #pragma unroll
       for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
       for (int i = first_stage<MODE, RS>(p, n0); i < nst; ++i, ++gs) {
-        const int b = gs & 1;
-        // every lane polls the barrier; reconverge before the warp-wide (.sync.aligned) TMEM loads
-        ok = __all_sync(0xffffffffu, mbar_wait(&t1full[b], (gs >> 1) & 1, p.status));
-        if (!ok) break;
-        tc_fence_after();
-        {
-          uint32_t vr[32], vi[32];
-          const uint32_t t = tmem + lane_off + D1_COL + b * DBUF + half * 32;
-          tmem_ld32_nowait(t, vr);
-          tmem_ld32_nowait(t + BN, vi);
-          tmem_wait_ld();
+        const bool seg_end = is_seg_end<MODE, RS>(p, i, first_stage<MODE, RS>(p, n0), F, nst);
+        if (MODE == 0 || seg_end) {
+          const int b = (MODE == 0) ? (gs & 1) : (gseg & 1);
+          const uint32_t ph = (MODE == 0) ? ((gs >> 1) & 1) : ((gseg >> 1) & 1);
+          // every lane polls the barrier; reconverge before the warp-wide (.sync.aligned) TMEM loads
+          ok = __all_sync(0xffffffffu, mbar_wait(&t1full[b], ph, p.status));
+          if (!ok) break;
+          tc_fence_after();
+          {
+            uint32_t vr[32], vi[32];
+            const uint32_t t = tmem + lane_off + D1_COL + b * DBUF + half * 32;
+            tmem_ld32_nowait(t, vr);
+            tmem_ld32_nowait(t + BN, vi);
+            tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            sr[j] += __uint_as_float(vr[j]);
-            si[j] += __uint_as_float(vi[j]);
+            for (int j = 0; j < 32; ++j) {
+              sr[j] += __uint_as_float(vr[j]);
+              si[j] += __uint_as_float(vi[j]);
+            }
           }
+          tc_fence_before();
+          mbar_arrive(&t1empty[b]);
         }
-        tc_fence_before();
-        mbar_arrive(&t1empty[b]);
-        if (is_seg_end<MODE, RS>(p, i, first_stage<MODE, RS>(p, n0), F, nst)) {
+        if (seg_end) {
           const int b2 = gseg & 1;
           ok = __all_sync(0xffffffffu, mbar_wait(&t2full[b2], (gseg >> 1) & 1, p.status));
           if (!ok) break;
