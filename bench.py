@@ -398,6 +398,12 @@ def run_device(args, system, world, rank):
     fl = algorithmic_flops(s)
     chi_avg_ms = sum(x[0] for x in chi_ms) / len(chi_ms)       # chi0 launches of one step (all q)
     chi_flops = chi_ms[0][1]
+    plan_t = gw.gw_plan_create(pb.prob)     # weight rows of the compressed chi0 (same for every q here)
+    try:
+        gw.gw_chi0(plan_t, 0, 1 % s.n_k)
+        T_rows = gw.gw_plan_chi0_terms(plan_t) or s.n_freq
+    finally:
+        gw.gw_plan_destroy(plan_t)
     peak_bf16, peak_hbm, peak_kind = load_peaks()
     tf32 = args.prec == "3xtf32"
     peak = peak_bf16 * (0.5 if tf32 else 1.0) if args.prec != "fp64" else 1.25
@@ -420,8 +426,12 @@ def run_device(args, system, world, rank):
         roofline=dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                       traffic=None, kernel="k_tc<chi0> (tcgen05 weighted Hermitian update)",
                       peak_note=f"{'TF32' if tf32 else 'BF16'} dense {peak_kind}; achieved counts algorithmic "
-                                f"flops (8 per complex MAC, lower triangle); tensor-issued = x{products}",
-                      tensor_issued_frac=achieved * products / peak),
+                                f"flops (8 per complex MAC, lower triangle, all {s.n_freq} frequencies); the "
+                                f"kernel runs {T_rows} compressed weight rows instead of {s.n_freq} frequencies and "
+                                f"x{products} split products: tensor-issued = achieved x {products} x "
+                                f"{T_rows}/{s.n_freq}",
+                      chi0_weight_rows=T_rows,
+                      tensor_issued_frac=achieved * products * T_rows / s.n_freq / peak),
         e2e=dict(value=ms_e2e / 1e3 / world, unit="s", h2d_bytes_per_step=pb.nbytes(),
                  d2h_bytes_per_step=s.n_k * (s.sigma_hi - s.sigma_lo) * 8 + 8),
         gpu_launches=launches,

@@ -137,9 +137,9 @@ __device__ __forceinline__ void mgen_body(const cplx<T>* __restrict__ T1, const 
 // atom A (j, i run over the n_b(A) basis functions of A):
 //   M^mu_{ab} = sum_j cK_{jb} conj(T1q^mu_{ja}) + sum_i conj(cQ_{ia}) T1k^mu_{ib}
 //   cK = c(k')[A][b-range], cQ = c(k'+q)[A][a-range], T1q^mu = T1^mu(k'+q)[.][a-range], T1k^mu = T1^mu(k')[.][b-range]
-// i.e. a complex product of K = 2 n_b(A) per ABF. The block stages cK, cQ and the T1 slices of its
-// ABFs in shared memory (fp32) once; threads run over (mu, a, b) outputs with the K loop in
-// shared memory. Tiles never straddle atoms (tile t -> atom by the cumulative tile counts).
+// i.e. a complex product of K = 2 n_b(A) per ABF. The block (512 threads: one block of ~130 KB
+// fits an SM, so the width buys the latency hiding) stages cK, cQ and the T1 slices of its ABFs
+// in shared memory (fp32) once; threads run over (mu, a, b) outputs with the K loop in shared memory. Tiles never straddle atoms (tile t -> atom by the cumulative tile counts).
 constexpr int MGT = 4;
 
 __device__ __forceinline__ bool mgen_tile(const LriGeom& g, int t, int& A, int& mu0, int& cnt) {
@@ -275,7 +275,7 @@ void launch_mgen<float>(const LriGeom& g, const c64* T1, const c64* T2, const c1
   cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
   cudaFuncSetAttribute(k_mgen_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   dim3 grid(nkk, mgen_tiles(g));
-  ++::gw::g_launch_count, k_mgen_smem<<<grid, 256, sm, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r,
+  ++::gw::g_launch_count, k_mgen_smem<<<grid, 512, sm, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r,
                                                             s_mu);
 }
 
@@ -345,7 +345,7 @@ void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q
   if (sm <= 200 * 1024) {
     cudaFuncSetAttribute(k_mgen_planes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     dim3 grid(nkk, mgen_tiles(g));
-    ++::gw::g_launch_count, k_mgen_planes<true><<<grid, 256, sm, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
+    ++::gw::g_launch_count, k_mgen_planes<true><<<grid, 512, sm, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
                                                                        tf32);
   } else {
     dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
