@@ -90,9 +90,17 @@ typedef struct {
  * library's own workspace, and on `stream` precomputes the half-transformed
  * LRI coefficients (Eqs. expan_coeff_FT1/2 contracted with c(k)), V(q)^{1/2}
  * for every q and the Coulomb eigenvector lambda = 1 at q = 0.
- * `n_sys` must be 1. `stream` is a cudaStream_t (NULL = legacy default).
+ * `stream` is a cudaStream_t (NULL = legacy default).
+ * n_sys > 1 (batch of independent systems, sizes free per system): `prob` points to an array of
+ * n_sys problems; the plan holds one plan per system, each on a stream of its own created by the
+ * library (all of them resident at once). The per-system calls (gw_chi0, gw_screen, gw_sigma,
+ * gw_g0w0, gw_qp, gw_qp_static, gw_surrogate_modes, gw_surrogate_data) take `sys` in [0, n_sys);
+ * on a batch plan each such call starts after the work queued on `stream` and returns after its
+ * own work. gw_plan_freq / gw_plan_mu / gw_plan_chi0_terms / gw_plan_last_chi0_stats report
+ * system 0; gw_surrogate_enable is not available on a batch plan. n_sys in [1, 4096].
  * On success *out owns the workspace until gw_plan_destroy.
- * Errors: GW_ERR_ARG (bad sizes/pointers), GW_ERR_NOMEM, GW_ERR_CUDA. */
+ * Errors: GW_ERR_ARG (bad sizes/pointers; for a batch the message names the system),
+ * GW_ERR_NOMEM, GW_ERR_CUDA. */
 gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw_plan* out);
 
 /* Release the plan and its workspace (waits for the plan's stream). NULL is a no-op. */
@@ -129,6 +137,18 @@ gw_status gw_sigma(gw_plan plan, int32_t sys, int32_t q, gw_complex* sigma_acc);
  * the group buffers (about 8 GB at most) are allocated on the first call and kept by the plan.
  * Results equal those of the per-q calls. Errors: as gw_chi0 / gw_screen / gw_sigma. */
 gw_status gw_g0w0(gw_plan plan, int32_t sys, gw_complex* sigma_acc);
+
+/* gw_g0w0 for every system of a batch plan: the systems' q loops run concurrently, each on its
+ * own stream, driven by n_threads host threads (0: min(n_sys, 8)), so that small systems
+ * together fill the GPU. sigma_accs: host array of n_sys device accumulators
+ * ([N_k][n_sigma][n_freq] of each system, zeroed by the caller; an entry may be NULL for the
+ * plan's own accumulator), or NULL for all own accumulators. Returns after all systems are done.
+ * On a single-system plan it is gw_g0w0(plan, 0, sigma_accs[0]).
+ * Errors: the first failing system's status, its message prefixed with "system i". */
+gw_status gw_g0w0_batch(gw_plan plan, gw_complex* const* sigma_accs, int32_t n_threads);
+
+/* Number of systems of a plan (host scalar). */
+gw_status gw_plan_n_sys(gw_plan plan, int32_t* n_sys);
 
 /* Quasiparticle energies: Sigma_c(i w) continued with the two-pole model
  * (p1 z + p0)/(z^2 + q1 z + q0) fitted by linear least squares on all n_freq points,

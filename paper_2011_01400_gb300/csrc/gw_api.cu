@@ -11,7 +11,7 @@
 #include <vector>
 
 namespace gw {
-unsigned long long g_launch_count = 0;
+std::atomic<unsigned long long> g_launch_count{0};
 }
 
 using namespace gw;
@@ -222,7 +222,12 @@ struct gw_plan_s {
   // q-group buffers of gw_g0w0
   c128 *g_chi0 = nullptr, *g_E = nullptr, *g_work = nullptr;
   int qb = 0;
+  double group_budget = 8.0e9;  // bytes for the q-group buffers of gw_g0w0
   SurState sur;
+  // batch plan (n_sys > 1): one plan per system, each on its own stream; the batch plan itself
+  // holds no device memory
+  std::vector<gw_plan_s*> subs;
+  std::vector<cudaStream_t> sub_streams;
   // timing of the chi0 contraction launches of the last call (CUDA events on the plan's stream)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   double last_chi0_ms = 0.0, last_chi0_flops = 0.0, chi0_flops_acc = 0.0;
@@ -353,7 +358,7 @@ gw_status newton_schulz(gw_plan_s* P, const c128* V, c128* out, int batch, int i
 
 gw_status validate(const gw_problem* p, int n_sys) {
   if (!p) return fail(GW_ERR_ARG, "problem is NULL");
-  if (n_sys != 1) return fail(GW_ERR_UNSUPPORTED, "n_sys must be 1 in this build");
+  if (n_sys != 1) return fail(GW_ERR_ARG, "validate: one problem at a time");
   for (int d = 0; d < 3; ++d)
     if (p->nk[d] < 1 || p->nk[d] > 64) return fail(GW_ERR_ARG, "nk out of range [1, 64]");
   if (p->n_atoms < 1 || p->n_atoms > 64) return fail(GW_ERR_ARG, "n_atoms out of range [1, 64]");
@@ -380,6 +385,29 @@ gw_status validate(const gw_problem* p, int n_sys) {
     if (i && p->aux_atom[i] < p->aux_atom[i - 1]) return fail(GW_ERR_ARG, "aux_atom must be non-decreasing");
   }
   return GW_OK;
+}
+
+// A batch plan routes a per-system call to the plan of system `sys`: the call starts after the
+// work queued on the caller's stream and returns after its own work on the system's stream.
+struct Route {
+  gw_plan_s* P = nullptr;
+  ~Route() {
+    if (P) cudaStreamSynchronize(P->st);
+  }
+};
+
+bool route(gw_plan& P, int32_t& sys, Route& r, gw_status* s) {
+  if (P && !P->subs.empty()) {
+    if (sys < 0 || sys >= (int)P->subs.size()) {
+      *s = fail(GW_ERR_ARG, "sys out of range");
+      return false;
+    }
+    cudaStreamSynchronize(P->st);
+    P = P->subs[sys];
+    sys = 0;
+    r.P = P;
+  }
+  return true;
 }
 
 bool plan_ok(gw_plan P, int32_t sys, gw_status* s) {
@@ -413,6 +441,34 @@ gw_status gw_kernel_launches(uint64_t* count) {
 gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw_plan* out) {
   if (!out) return fail(GW_ERR_ARG, "out is NULL");
   *out = nullptr;
+  if (n_sys < 1 || n_sys > 4096) return fail(GW_ERR_ARG, "n_sys out of range [1, 4096]");
+  if (n_sys > 1) {
+    if (!prob) return fail(GW_ERR_ARG, "problem array is NULL");
+    gw_plan_s* B = new (std::nothrow) gw_plan_s();
+    if (!B) return fail(GW_ERR_NOMEM, "host allocation failed");
+    B->st = static_cast<cudaStream_t>(stream);
+    GW_CUDA(cudaStreamSynchronize(B->st));   // inputs the caller queued on its stream
+    for (int i = 0; i < n_sys; ++i) {
+      cudaStream_t si = nullptr;
+      gw_plan_s* sub = nullptr;
+      gw_status st = GW_OK;
+      if (cudaStreamCreateWithFlags(&si, cudaStreamNonBlocking) != cudaSuccess) {
+        st = fail(GW_ERR_CUDA, "stream creation failed");
+      } else {
+        B->sub_streams.push_back(si);
+        st = gw_plan_create(prob + i, 1, si, &sub);
+      }
+      if (st != GW_OK) {
+        const std::string msg = "system " + std::to_string(i) + ": " + g_last_error;
+        gw_plan_destroy(B);
+        return fail(st, msg);
+      }
+      sub->group_budget = 2.0e9;
+      B->subs.push_back(sub);
+    }
+    *out = B;
+    return GW_OK;
+  }
   GW_TRY(validate(prob, n_sys));
   gw_plan_s* P = new (std::nothrow) gw_plan_s();
   if (!P) return fail(GW_ERR_NOMEM, "host allocation failed");
@@ -660,6 +716,12 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
 
 gw_status gw_plan_destroy(gw_plan P) {
   if (!P) return GW_OK;
+  if (!P->subs.empty() || !P->sub_streams.empty()) {
+    for (gw_plan_s* sub : P->subs) gw_plan_destroy(sub);
+    for (cudaStream_t si : P->sub_streams) cudaStreamDestroy(si);
+    delete P;
+    return GW_OK;
+  }
   if (P->st) cudaStreamSynchronize(P->st);
   else cudaDeviceSynchronize();
   for (void* a : P->allocs) cudaFree(a);
@@ -674,6 +736,7 @@ gw_status gw_plan_destroy(gw_plan P) {
 }
 
 gw_status gw_plan_freq(gw_plan P, double* freq, double* weight) {
+  if (P && !P->subs.empty()) P = P->subs[0];  // batch plan: system 0
   if (!P) return fail(GW_ERR_ARG, "plan is NULL");
   if (freq) std::copy(P->freq.begin(), P->freq.end(), freq);
   if (weight) std::copy(P->fweight.begin(), P->fweight.end(), weight);
@@ -681,18 +744,21 @@ gw_status gw_plan_freq(gw_plan P, double* freq, double* weight) {
 }
 
 gw_status gw_plan_mu(gw_plan P, double* mu) {
+  if (P && !P->subs.empty()) P = P->subs[0];  // batch plan: system 0
   if (!P || !mu) return fail(GW_ERR_ARG, "NULL argument");
   *mu = P->mu;
   return GW_OK;
 }
 
 gw_status gw_plan_chi0_terms(gw_plan P, int32_t* terms) {
+  if (P && !P->subs.empty()) P = P->subs[0];  // batch plan: system 0
   if (!P || !terms) return fail(GW_ERR_ARG, "NULL argument");
   *terms = P->last_T;
   return GW_OK;
 }
 
 gw_status gw_plan_last_chi0_stats(gw_plan P, double* ms, double* flops) {
+  if (P && !P->subs.empty()) P = P->subs[0];  // batch plan: system 0
   if (!P) return fail(GW_ERR_ARG, "plan is NULL");
   if (ms) *ms = P->last_chi0_ms;
   if (flops) *flops = P->last_chi0_flops;
@@ -987,7 +1053,7 @@ gw_status ensure_groups(gw_plan_s* P) {
   if (P->g_chi0) return GW_OK;
   const long long slot = (long long)P->N * P->N * P->nw;
   const double per_q = 3.0 * sizeof(c128) * (double)slot;
-  P->qb = (int)std::max(1.0, std::min((double)P->NK, std::floor(8.0e9 / per_q)));
+  P->qb = (int)std::max(1.0, std::min((double)P->NK, std::floor(P->group_budget / per_q)));
   GW_TRY(dalloc(P, &P->g_chi0, (size_t)slot * P->qb));
   GW_TRY(dalloc(P, &P->g_E, (size_t)slot * P->qb));
   GW_TRY(dalloc(P, &P->g_work, (size_t)slot * P->qb));
@@ -1000,6 +1066,8 @@ extern "C" {
 
 gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
   gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
   if (!plan_ok(P, sys, &s)) return s;
   if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
   cudaStream_t st = P->st;
@@ -1017,6 +1085,8 @@ gw_status gw_chi0(gw_plan P, int32_t sys, int32_t q, gw_complex* chi0_out) {
 
 gw_status gw_screen(gw_plan P, int32_t sys, int32_t q, gw_complex* wc_out) {
   gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
   if (!plan_ok(P, sys, &s)) return s;
   if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
   if (P->chi0_q != q) return fail(GW_ERR_STATE, "gw_screen needs gw_chi0 for the same q first");
@@ -1034,6 +1104,8 @@ gw_status gw_screen(gw_plan P, int32_t sys, int32_t q, gw_complex* wc_out) {
 
 gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
   gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
   if (!plan_ok(P, sys, &s)) return s;
   if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
   if (P->wc_q != q) return fail(GW_ERR_STATE, "gw_sigma needs gw_screen for the same q first");
@@ -1044,6 +1116,8 @@ gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
 
 gw_status gw_g0w0(gw_plan P, int32_t sys, gw_complex* sigma_acc) {
   gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
   if (!plan_ok(P, sys, &s)) return s;
   if (P->sur.on && P->sur.model)
     return g0w0_sur(P, sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma);
@@ -1074,6 +1148,8 @@ gw_status gw_g0w0(gw_plan P, int32_t sys, gw_complex* sigma_acc) {
 gw_status gw_qp(gw_plan P, int32_t sys, const gw_complex* sigma, const double* dxv, double* e_qp, double* gap,
                 int32_t* n_conv) {
   gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
   if (!plan_ok(P, sys, &s)) return s;
   if (!e_qp || !gap) return fail(GW_ERR_ARG, "e_qp and gap must not be NULL");
   cudaStream_t st = P->st;
@@ -1177,6 +1253,8 @@ extern "C" {
 gw_status gw_qp_static(gw_plan P, int32_t sys, const gw_complex* sigma, const double* dxv, double* e_qp,
                        double* gap, int32_t* n_conv) {
   gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
   if (!plan_ok(P, sys, &s)) return s;
   if (!e_qp || !gap) return fail(GW_ERR_ARG, "e_qp and gap must not be NULL");
   const int n = P->NK * P->nsig;
@@ -1440,6 +1518,7 @@ extern "C" {
 
 gw_status gw_surrogate_enable(gw_plan P, gw_surrogate model, const gw_surrogate_cfg* cfg) {
   gw_status s;
+  if (P && !P->subs.empty()) return fail(GW_ERR_UNSUPPORTED, "gw_surrogate_enable: not on a batch plan");
   if (!plan_ok(P, 0, &s)) return s;
   SurState& S = P->sur;
   if (!cfg) {
@@ -1513,6 +1592,8 @@ gw_status gw_surrogate_enable(gw_plan P, gw_surrogate model, const gw_surrogate_
 gw_status gw_surrogate_modes(gw_plan P, int32_t sys, int32_t q, float* d_out, double* theta_out, float* x_out,
                              float* y_out) {
   gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
   if (!plan_ok(P, sys, &s)) return s;
   SurState& S = P->sur;
   if (!S.on) return fail(GW_ERR_STATE, "gw_surrogate_modes needs gw_surrogate_enable first");
@@ -1542,6 +1623,8 @@ extern "C" {
 
 gw_status gw_surrogate_data(gw_plan P, int32_t sys, float* x_out, float* y_out, double* moments) {
   gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
   if (!plan_ok(P, sys, &s)) return s;
   SurState& S = P->sur;
   if (!S.on) return fail(GW_ERR_STATE, "gw_surrogate_data needs gw_surrogate_enable first");
@@ -1582,6 +1665,55 @@ gw_status gw_surrogate_data(gw_plan P, int32_t sys, float* x_out, float* y_out, 
   }
   GW_TRY(P->collect_timing());
   P->chi0_q = P->wc_q = -1;
+  return GW_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Batch of independent systems (gw_plan_create with n_sys > 1): every system's whole q loop
+// (gw_g0w0) on its own stream, driven by a pool of host threads, so that the kernels of
+// different systems run concurrently and fill the GPU when single systems are small.
+// ---------------------------------------------------------------------------------------------
+#include <atomic>
+#include <thread>
+
+extern "C" {
+
+gw_status gw_g0w0_batch(gw_plan P, gw_complex* const* sigma_accs, int32_t n_threads) {
+  if (!P) return fail(GW_ERR_ARG, "plan is NULL");
+  if (P->subs.empty()) return gw_g0w0(P, 0, sigma_accs ? sigma_accs[0] : nullptr);
+  const int n = (int)P->subs.size();
+  if (n_threads < 0) return fail(GW_ERR_ARG, "n_threads must be >= 0");
+  const int nt = std::max(1, std::min(n, n_threads > 0 ? (int)n_threads : 8));
+  GW_CUDA(cudaStreamSynchronize(P->st));
+  int dev = 0;
+  GW_CUDA(cudaGetDevice(&dev));
+  std::vector<gw_status> st(n, GW_OK);
+  std::vector<std::string> msg(n);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) break;
+      st[i] = gw_g0w0(P->subs[i], 0, sigma_accs ? sigma_accs[i] : nullptr);
+      if (st[i] != GW_OK) msg[i] = gw_last_error();
+      cudaStreamSynchronize(P->subs[i]->st);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto& th : pool) th.join();
+  for (int i = 0; i < n; ++i)
+    if (st[i] != GW_OK) return fail(st[i], "system " + std::to_string(i) + ": " + msg[i]);
+  return GW_OK;
+}
+
+gw_status gw_plan_n_sys(gw_plan P, int32_t* n_sys) {
+  if (!P || !n_sys) return fail(GW_ERR_ARG, "NULL argument");
+  *n_sys = P->subs.empty() ? 1 : (int32_t)P->subs.size();
   return GW_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 #include <string>
@@ -12,7 +13,7 @@
 namespace gw {
 
 // number of kernels this library has launched (process-wide, host side)
-extern unsigned long long g_launch_count;
+extern std::atomic<unsigned long long> g_launch_count;
 
 // complex helpers (device and host)
 template <typename T> struct cplx { T re, im; };

@@ -16,12 +16,9 @@
 
 namespace gw {
 
-__constant__ LriGeom c_geom;
-
 template <typename T>
-__global__ void k_lri_halfT(const double* __restrict__ ctil, const c128* __restrict__ evec, cplx<T>* __restrict__ T1,
-                            int A) {
-  const LriGeom& g = c_geom;
+__global__ void k_lri_halfT(const __grid_constant__ LriGeom g, const double* __restrict__ ctil,
+                            const c128* __restrict__ evec, cplx<T>* __restrict__ T1, int A) {
   const int nb_A = g.atom_nb[A], nx_A = g.atom_nx[A];
   const long long total = (long long)g.NK * nx_A * nb_A * g.NBd;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -58,11 +55,10 @@ __global__ void k_lri_halfT(const double* __restrict__ ctil, const c128* __restr
 template <typename T>
 void launch_lri_halfT(const LriGeom& g, const double* ctil, const c128* evec, cplx<T>* T1, cplx<T>* /*T2*/,
                       cudaStream_t st) {
-  cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
   for (int A = 0; A < g.n_atoms; ++A) {
     long long total = (long long)g.NK * g.atom_nx[A] * g.atom_nb[A] * g.NBd;
     int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
-    ++::gw::g_launch_count, k_lri_halfT<T><<<blocks, 256, 0, st>>>(ctil, evec, T1, A);
+    ++::gw::g_launch_count, k_lri_halfT<T><<<blocks, 256, 0, st>>>(g, ctil, evec, T1, A);
   }
 }
 template void launch_lri_halfT<double>(const LriGeom&, const double*, const c128*, c128*, c128*, cudaStream_t);
@@ -80,9 +76,9 @@ __device__ __forceinline__ int aux_atom_of(const LriGeom& g, int mu) {
 }
 
 template <typename T, typename Store>
-__device__ __forceinline__ void mgen_body(const cplx<T>* __restrict__ T1, const c128* __restrict__ evec, int q,
-                                          int kk0, int mode, int a0, int na, int b0, int nb, Store store) {
-  const LriGeom& g = c_geom;
+__device__ __forceinline__ void mgen_body(const LriGeom& g, const cplx<T>* __restrict__ T1,
+                                          const c128* __restrict__ evec, int q, int kk0, int mode, int a0, int na,
+                                          int b0, int nb, Store store) {
   const int kk = blockIdx.x;
   int ktgt = kk0 + kk;
   int k3 = ktgt % g.nk[2], k2 = (ktgt / g.nk[2]) % g.nk[1], k1 = ktgt / (g.nk[1] * g.nk[2]);
@@ -156,10 +152,10 @@ __device__ __forceinline__ bool mgen_tile(const LriGeom& g, int t, int& A, int& 
 }
 
 template <typename Store>
-__device__ __forceinline__ void mgen_smem_body(const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0,
-                                               int mode, int a0, int na, int b0, int nb, Store store) {
+__device__ __forceinline__ void mgen_smem_body(const LriGeom& g, const c64* __restrict__ T1,
+                                               const c128* __restrict__ evec, int q, int kk0, int mode, int a0, int na,
+                                               int b0, int nb, Store store) {
   extern __shared__ float2 sm2[];
-  const LriGeom& g = c_geom;
   const int kk = blockIdx.x;
   int A, mu0, cnt;
   if (!mgen_tile(g, blockIdx.y, A, mu0, cnt)) return;
@@ -232,17 +228,17 @@ size_t mgen_smem(const LriGeom& g, int na, int nb) {
   return sizeof(float2) * (size_t)nbA * (na + nb) * (1 + MGT);
 }
 
-__global__ void k_mgen_smem(const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int mode, int a0,
+__global__ void k_mgen_smem(const __grid_constant__ LriGeom g, const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int mode, int a0,
                             int na, int b0, int nb, c64* __restrict__ out, long long s_r, long long s_mu) {
-  mgen_smem_body(T1, evec, q, kk0, mode, a0, na, b0, nb, [&](long long r, int mu, float re, float im) {
+  mgen_smem_body(g, T1, evec, q, kk0, mode, a0, na, b0, nb, [&](long long r, int mu, float re, float im) {
     out[r * s_r + (long long)mu * s_mu] = c64{re, im};
   });
 }
 
 template <typename T>
-__global__ void k_mgen(const cplx<T>* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int mode,
+__global__ void k_mgen(const __grid_constant__ LriGeom g, const cplx<T>* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int mode,
                        int a0, int na, int b0, int nb, cplx<T>* __restrict__ out, long long s_r, long long s_mu) {
-  mgen_body<T>(T1, evec, q, kk0, mode, a0, na, b0, nb, [&](long long r, int mu, T re, T im) {
+  mgen_body<T>(g, T1, evec, q, kk0, mode, a0, na, b0, nb, [&](long long r, int mu, T re, T im) {
     out[r * s_r + (long long)mu * s_mu] = cplx<T>{re, im};
   });
 }
@@ -251,9 +247,8 @@ template <typename T>
 void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* /*T2*/, const c128* evec, int q, int kk0,
                  int nkk, MapMode mode, int a0, int na, int b0, int nb, cplx<T>* out, long long s_r, long long s_mu,
                  cudaStream_t st) {
-  cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
   dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
-  ++::gw::g_launch_count, k_mgen<T><<<grid, 256, 0, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r, s_mu);
+  ++::gw::g_launch_count, k_mgen<T><<<grid, 256, 0, st>>>(g, T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r, s_mu);
 }
 template void launch_mgen<double>(const LriGeom&, const c128*, const c128*, const c128*, int, int, int, MapMode, int,
                                   int, int, int, c128*, long long, long long, cudaStream_t);
@@ -265,17 +260,15 @@ void launch_mgen<float>(const LriGeom& g, const c64* T1, const c64* T2, const c1
                         cudaStream_t st) {
   const size_t sm = mgen_smem(g, na, nb);
   if (sm > 200 * 1024) {
-    cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
     dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
-    ++::gw::g_launch_count, k_mgen<float><<<grid, 256, 0, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r,
+    ++::gw::g_launch_count, k_mgen<float><<<grid, 256, 0, st>>>(g, T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r,
                                                                 s_mu);
     return;
   }
   (void)T2;
-  cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
   cudaFuncSetAttribute(k_mgen_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   dim3 grid(nkk, mgen_tiles(g));
-  ++::gw::g_launch_count, k_mgen_smem<<<grid, 512, sm, st>>>(T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r,
+  ++::gw::g_launch_count, k_mgen_smem<<<grid, 512, sm, st>>>(g, T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r,
                                                             s_mu);
 }
 
@@ -299,7 +292,7 @@ struct PlanePtrs {
 };
 
 template <bool SMEM>
-__global__ void k_mgen_planes(const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int a0,
+__global__ void k_mgen_planes(const __grid_constant__ LriGeom g, const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int a0,
                               int na, int b0, int nb, PlanePtrs P, long long ldk, long long kofs, int tf32) {
   auto st = [&](long long r, int mu, float re, float im) {
     const long long e = (long long)mu * ldk + kofs + 2 * r;
@@ -329,15 +322,14 @@ __global__ void k_mgen_planes(const c64* __restrict__ T1, const c128* __restrict
     }
   };
   if constexpr (SMEM)
-    mgen_smem_body(T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
+    mgen_smem_body(g, T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
   else
-    mgen_body<float>(T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
+    mgen_body<float>(g, T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
 }
 
 void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
                         int b0, int nb, float* raw, void* const* bplanes, long long ldk, long long kofs, int tf32,
                         cudaStream_t st) {
-  cudaMemcpyToSymbolAsync(c_geom, &g, sizeof(LriGeom), 0, cudaMemcpyHostToDevice, st);
   PlanePtrs P{};
   P.raw = raw;
   for (int i = 0; i < (tf32 ? 4 : 6); ++i) P.b[i] = bplanes[i];
@@ -345,11 +337,11 @@ void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q
   if (sm <= 200 * 1024) {
     cudaFuncSetAttribute(k_mgen_planes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     dim3 grid(nkk, mgen_tiles(g));
-    ++::gw::g_launch_count, k_mgen_planes<true><<<grid, 512, sm, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
+    ++::gw::g_launch_count, k_mgen_planes<true><<<grid, 512, sm, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
                                                                        tf32);
   } else {
     dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
-    ++::gw::g_launch_count, k_mgen_planes<false><<<grid, 256, 0, st>>>(T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
+    ++::gw::g_launch_count, k_mgen_planes<false><<<grid, 256, 0, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
                                                                         tf32);
   }
 }

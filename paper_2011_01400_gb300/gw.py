@@ -21,7 +21,8 @@ GW_FP64, GW_3XTF32, GW_3XBF16 = 0, 1, 2
 PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16}
 
 # every symbol include/gw.h declares
-EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_g0w0", "gw_qp",
+EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_g0w0", "gw_g0w0_batch",
+           "gw_plan_n_sys", "gw_qp",
            "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_plan_chi0_terms", "gw_kernel_launches",
            "gw_surrogate_param_count", "gw_surrogate_create", "gw_surrogate_destroy", "gw_surrogate_get_params",
            "gw_surrogate_set_params", "gw_surrogate_forward", "gw_surrogate_loss_grad", "gw_surrogate_fit_linear",
@@ -89,6 +90,8 @@ def load():
     lib.gw_screen.argtypes = [vp, i32, i32, vp]
     lib.gw_sigma.argtypes = [vp, i32, i32, vp]
     lib.gw_g0w0.argtypes = [vp, i32, vp]
+    lib.gw_g0w0_batch.argtypes = [vp, ctypes.POINTER(vp), i32]
+    lib.gw_plan_n_sys.argtypes = [vp, ctypes.POINTER(i32)]
     lib.gw_qp.argtypes = [vp, i32, vp, vp, dp, dp, ctypes.POINTER(i32)]
     lib.gw_qp_static.argtypes = [vp, i32, vp, vp, dp, dp, ctypes.POINTER(i32)]
     lib.gw_plan_freq.argtypes = [vp, dp, dp]
@@ -135,11 +138,30 @@ def _ptr(t):
 
 
 def gw_plan_create(prob, n_sys=1, stream=None):
+    """prob: a gw_problem, or a list of them (a batch plan with n_sys = len(list))."""
     import torch
     h = ctypes.c_void_p()
     s = torch.cuda.current_stream().cuda_stream if stream is None else stream
-    _check(load().gw_plan_create(ctypes.byref(prob), n_sys, ctypes.c_void_p(s), ctypes.byref(h)))
+    if isinstance(prob, (list, tuple)):
+        arr = (gw_problem * len(prob))(*prob)
+        _check(load().gw_plan_create(arr, len(prob), ctypes.c_void_p(s), ctypes.byref(h)))
+    else:
+        _check(load().gw_plan_create(ctypes.byref(prob), n_sys, ctypes.c_void_p(s), ctypes.byref(h)))
     return h
+
+
+def gw_g0w0_batch(plan, sigma_accs=None, n_threads=0):
+    """sigma_accs: list of device tensors (or None entries) per system, or None."""
+    arr = None
+    if sigma_accs is not None:
+        arr = (ctypes.c_void_p * len(sigma_accs))(*[None if t is None else t.data_ptr() for t in sigma_accs])
+    _check(load().gw_g0w0_batch(plan, arr, int(n_threads)))
+
+
+def gw_plan_n_sys(plan):
+    n = ctypes.c_int32()
+    _check(load().gw_plan_n_sys(plan, ctypes.byref(n)))
+    return n.value
 
 
 def gw_plan_destroy(plan):
