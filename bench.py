@@ -323,6 +323,72 @@ def surrogate_bench(args, gw, torch):
                 judge="the plain method on the full 60-point grid, same precision, same system")
 
 
+def batch_systems(n, seed0=30000):
+    """Seeded systems of uneven size for the batch measurement: 2 atoms, bands 20-80 (n_occ 4-8),
+    ABFs 60-200 per atom, k mesh 2x2x2 / 3x3x3 / 4x4x4, 16-32 frequencies, Sigma_c for the
+    4 bands at the gap."""
+    import numpy as np
+    from paper_2011_01400_gb300.synth import make_system
+    out = []
+    for i in range(n):
+        r = np.random.default_rng(seed0 + i)
+        nb = int(r.integers(10, 41)) * 2
+        nocc = int(r.integers(4, 9))
+        nx = int(r.integers(60, 201))
+        nkm = [(2, 2, 2), (3, 3, 3), (4, 4, 4)][int(r.integers(0, 3))]
+        nw = int(r.integers(16, 33))
+        cfg = dict(nk=nkm, n_atoms=2, nb_per_atom=nb // 2, naux_per_atom=nx, n_bands=nb, n_occ=nocc,
+                   n_freq=nw, sigma=(nocc - 2, nocc + 2), omega_cell=270.25)
+        out.append(make_system(cfg, seed=seed0 + i))
+    return out
+
+
+def batch_bench(args, gw, torch):
+    """Many independent systems of uneven size in one batch plan: gw_g0w0_batch with the q loops
+    of the systems running concurrently, against the same systems one after another, and the
+    split-precision QP gaps against the FP64 GPU path on the 4 smallest systems."""
+    ss = batch_systems(args.batch)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def run(prec, systems, threads):
+        pbs = [gw.Problem(s, prec) for s in systems]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan = gw.gw_plan_create([pb.prob for pb in pbs])
+        torch.cuda.synchronize()
+        t_plan = time.perf_counter() - t0
+        try:
+            gw.gw_g0w0_batch(plan, None, threads)   # warm-up (group buffers)
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            gw.gw_g0w0_batch(plan, None, threads)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            t = ev[0].elapsed_time(ev[1]) / 1e3
+            gaps = [gw.gw_qp(plan, i, s.n_k, s.sigma_hi - s.sigma_lo)[1] for i, s in enumerate(systems)]
+        finally:
+            gw.gw_plan_destroy(plan)
+        return t, t_plan, gaps
+
+    t_conc, t_plan, gaps = run(args.prec, ss, 8)
+    t_seq, _, _ = run(args.prec, ss, 1)
+    sub = sorted(ss, key=lambda x: algorithmic_flops(x)["total"])[:4]   # the FP64 path is slow: smallest 4
+    _, _, gaps64 = run("fp64", sub, 8)
+    _, _, gaps_sub = run(args.prec, sub, 8)
+    fl = sum(algorithmic_flops(s)["total"] for s in ss)
+    ha = 27211.386
+    dg = [abs(a - b) * ha for a, b in zip(gaps_sub, gaps64) if a == a and b == b]
+    return dict(workload=f"{len(ss)} seeded systems: 2 atoms, 20-80 bands (4-8 occupied), 120-400 ABF, "
+                         f"k mesh 2^3/3^3/4^3, 16-32 frequencies",
+                precision=args.prec, systems=len(ss), plan_create_s=t_plan,
+                concurrent_s=t_conc, sequential_s=t_seq, concurrency_speedup=t_seq / t_conc,
+                aggregate_useful_tflops=fl / t_conc / 1e12, threads=8,
+                max_abs_dgap_vs_fp64_meV=max(dg) if dg else None, fp64_checked_systems=len(sub),
+                note="q loops of the systems run concurrently on their own streams (host thread pool); "
+                     "the time covers the whole G0W0 pass of every system, plans built beforehand")
+
+
 def run_device(args, system, world, rank):
     import torch
     import torch.distributed as dist
@@ -441,6 +507,8 @@ def run_device(args, system, world, rank):
     )
     if args.surrogate:
         line["surrogate"] = surrogate_bench(args, gw, torch)
+    if args.batch:
+        line["batch"] = batch_bench(args, gw, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(s)
     print(json.dumps(line), flush=True)
@@ -464,6 +532,8 @@ def main():
                     help="also train the frequency surrogate and time it against the full 60-point grid")
     ap.add_argument("--sur-systems", type=int, default=64, help="training systems of the surrogate")
     ap.add_argument("--sur-epochs", type=int, default=40, help="training epochs of the surrogate")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="also run a batch of this many seeded systems of uneven size (e.g. 64)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
