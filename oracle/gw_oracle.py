@@ -313,6 +313,29 @@ def sigma_q(sys, iq, Wc_q, omegas, gweights, mu):
     return -out / (2.0 * np.pi * sys.n_k)
 
 
+def sigma_x(sys):
+    """Exchange self-energy, the bare-Coulomb part of Eq. (GW_selfe_element) (W = V + W^c):
+    the frequency integral of V G over the occupied bands gives
+
+      Sigma_x_n(k) = -(1/N_q) sum_q sum_{m occ} sum_{mu nu} C^mu_{nm}(k, k-q) V_{mu nu}(q) C^nu_{mn}(k-q, k)
+
+    with C^nu_{mn}(k-q, k) = conj(C^nu_{nm}(k, k-q)); V(q=0) is the (truncated) Coulomb matrix
+    as given. reading: w_q = 1/N_q as for Sigma_c. Returns [N_k, n_sigma] real (Ha).
+    """
+    nsig = sys.sigma_hi - sys.sigma_lo
+    out = np.zeros((sys.n_k, nsig))
+    sig_b = np.arange(sys.sigma_lo, sys.sigma_hi)
+    occ = np.arange(sys.n_occ)
+    for iq in range(sys.n_k):
+        for ik in range(sys.n_k):
+            ikmq = k_minus(sys.nk, ik, iq)
+            M = mo_triple(sys, ikmq, iq, sig_b, occ)          # [mu, n, m]: n at k, m occupied at k-q
+            Mf = M.reshape(sys.n_aux, -1)
+            S = np.sum(Mf * (sys.V[iq] @ np.conj(Mf)), axis=0).real.reshape(nsig, -1)
+            out[ik] -= S.sum(axis=1)
+    return out / sys.n_k
+
+
 # ----------------------------------------------------------------------------
 # step (e): analytic continuation and quasiparticle equation
 # ----------------------------------------------------------------------------

@@ -256,3 +256,42 @@ def test_qp_stable_under_small_sigma_noise():
     assert conv.all() and r["converged"].all()
     assert np.abs(E - r["e_qp"]).max() * HA_MEV < 0.1
     assert abs(gap - r["gap"]) * HA_MEV < 0.1
+
+
+def test_sigma_x_closed_form_delta_lri_identity_coulomb(monkeypatch):
+    """C~^mu_ij = t delta_ij for every ABF and V(q) = 1: C^mu_{nm}(k, k-q) = t <psi_nk|psi_m,k-q>,
+    so Sigma_x_n(k) = -(N_aux |t|^2 / N_q) sum_q sum_{m occ} |<psi_nk|psi_m,k-q>|^2 (overlaps from c)."""
+    s = make_system("tiny", seed=6, trs=False)
+    t = 0.6 + 0.3j
+    monkeypatch.setattr(O, "ao_triple",
+                        lambda sys, ik, iq: np.broadcast_to(t * np.eye(sys.n_basis), (sys.n_aux, sys.n_basis, sys.n_basis)))
+    s.V = np.broadcast_to(np.eye(s.n_aux, dtype=complex), (s.n_k, s.n_aux, s.n_aux)).copy()
+    got = O.sigma_x(s)
+    want = np.zeros_like(got)
+    for ik in range(s.n_k):
+        for iq in range(s.n_k):
+            ikmq = O.k_minus(s.nk, ik, iq)
+            ov = np.conj(s.evec[ik][:, s.sigma_lo:s.sigma_hi]).T @ s.evec[ikmq][:, :s.n_occ]
+            want[ik] -= s.n_aux * abs(t) ** 2 * np.sum(np.abs(ov) ** 2, axis=1)
+    want /= s.n_k
+    assert np.allclose(got, want, rtol=1e-12, atol=0)
+
+
+def test_sigma_x_negative_and_matches_loops():
+    """Sigma_x <= 0 (V positive definite) and equals an explicit-loop evaluation on the brute-force
+    LRI coefficients (real-space sum per cell, no half transforms)."""
+    from oracle import brute as B
+    s = make_system("tiny", seed=7)
+    got = O.sigma_x(s)
+    assert (got < 0).all()
+    ref = np.zeros_like(got)
+    for ik in range(s.n_k):
+        for iq in range(s.n_k):
+            ikmq = O.k_minus(s.nk, ik, iq)
+            M = B.mo_triple_brute(s, ikmq, iq)                 # [mu, a (k-q+q = k), b (k-q)]
+            for n in range(s.sigma_lo, s.sigma_hi):
+                for m in range(s.n_occ):
+                    a = M[:, n, m]
+                    ref[ik, n - s.sigma_lo] -= (a @ s.V[iq] @ np.conj(a)).real
+    ref /= s.n_k
+    assert np.allclose(got, ref, rtol=1e-10, atol=0)
