@@ -130,6 +130,15 @@ gw_status gw_screen(gw_plan plan, int32_t sys, int32_t q, gw_complex* wc_out);
  *            or NULL to accumulate into the plan's own buffer (zeroed at plan creation). */
 gw_status gw_sigma(gw_plan plan, int32_t sys, int32_t q, gw_complex* sigma_acc);
 
+/* Exchange self-energy, the bare-Coulomb part of Eq. (GW_selfe_element) (W = V + W^c): the
+ * frequency integral of V G leaves the occupied bands,
+ *   Sigma_x_n(k) = -(1/N_q) sum_q sum_{m occ} sum_{mu nu} C^mu_{nm}(k,k-q) V_{mu nu}(q) C^nu_{mn}(k-q,k),
+ * n in [sigma_lo, sigma_hi), V(0) the (truncated) Coulomb matrix as given.
+ * sigx: device [N_k][n_sigma] FP64 output (overwritten). The products run in FP64 on the FP64
+ * path and in FP32 on the split paths. For the QP equation, pass dxv = Sigma_x - v_xc to gw_qp.
+ * Errors: GW_ERR_ARG, GW_ERR_NOMEM, GW_ERR_CUDA. */
+gw_status gw_sigma_x(gw_plan plan, int32_t sys, double* sigx);
+
 /* The whole q loop of the G0W0 pass in one call: for every q on the mesh, chi0 (as gw_chi0),
  * eps~ and W^c (as gw_screen) and the Sigma_c term (as gw_sigma), accumulated into sigma_acc
  * (device [N_k][n_sigma][n_freq], caller zeroes it) or, if NULL, the plan's own accumulator.

@@ -193,6 +193,8 @@ struct gw_plan_s {
   c128* d_pq = nullptr;       // [ldm]
   void* d_A = nullptr;        // sigma rows [R][N]
   void* d_Apl[2] = {};        // split precision: bf16 / tf32 pieces of the sigma rows [R][2*Kx]
+  double* d_Sx = nullptr;     // gw_sigma_x: S per row; FP32 rows A V [R][Kx] and V(q) in fp32
+  c64 *d_Ux = nullptr, *d_Vx32 = nullptr;
   void* d_U = nullptr;        // [R][N]
   double* d_S_d = nullptr;    // [R][nw]
   float* d_S_f = nullptr;
@@ -1714,6 +1716,77 @@ gw_status gw_g0w0_batch(gw_plan P, gw_complex* const* sigma_accs, int32_t n_thre
 gw_status gw_plan_n_sys(gw_plan P, int32_t* n_sys) {
   if (!P || !n_sys) return fail(GW_ERR_ARG, "NULL argument");
   *n_sys = P->subs.empty() ? 1 : (int32_t)P->subs.size();
+  return GW_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Exchange self-energy (the bare-Coulomb part of Eq. GW_selfe_element, W = V + W^c):
+//   Sigma_x_n(k) = -(1/N_q) sum_q sum_{m occ} a^T V(q) a^*,  a = C_{nm}(k, k-q) = M_{nm}(k-q, q)
+// Rows a_r, r = ((kk * n_sigma) + n) * n_occ + m, as for Sigma_c but over the occupied bands;
+// U = A V(q) (FP64 GEMM on the FP64 path, FP32 on the split paths), S_r = Re U_r . conj(a_r).
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+__global__ void k_sigx_accum(int nkk, int kk0, int nsig, int nocc, const double* __restrict__ S, double scale,
+                             double* __restrict__ sigx) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nkk * nsig) return;
+  double acc = 0.0;
+  for (int m = 0; m < nocc; ++m) acc += S[(long long)e * nocc + m];
+  sigx[(long long)kk0 * nsig + e] += scale * acc;
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_sigma_x(gw_plan P, int32_t sys, double* sigx) {
+  gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (!sigx) return fail(GW_ERR_ARG, "gw_sigma_x: sigx is NULL");
+  cudaStream_t st = P->st;
+  const int N = P->N, nsig = P->nsig, nocc = P->nocc;
+  const long long NN = (long long)N * N;
+  const long long rows_max = (long long)P->sig_nkk * nsig * nocc;   // <= sig_rows
+  if (!P->d_Sx) {
+    GW_TRY(dalloc(P, &P->d_Sx, (size_t)rows_max));
+    if (!P->fp64) {
+      GW_TRY(dalloc(P, &P->d_Ux, (size_t)rows_max * P->Kx));
+      GW_TRY(dalloc(P, &P->d_Vx32, (size_t)NN));
+    }
+  }
+  const c128* evec = reinterpret_cast<const c128*>(P->p.evec);
+  const c128* V = reinterpret_cast<const c128*>(P->p.V);
+  GW_CUDA(cudaMemsetAsync(sigx, 0, sizeof(double) * P->NK * nsig, st));
+  for (int q = 0; q < P->NK; ++q) {
+    if (!P->fp64) launch_convert((int)NN, V + q * NN, P->d_Vx32, st);
+    for (int kk0 = 0; kk0 < P->NK; kk0 += P->sig_nkk) {
+      const int nkk = std::min(P->sig_nkk, P->NK - kk0);
+      const int R = nkk * nsig * nocc;
+      if (P->fp64) {
+        c128* A = static_cast<c128*>(P->d_A);
+        c128* U = static_cast<c128*>(P->d_U);
+        launch_mgen<double>(P->geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk,
+                            MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, nocc, A, N, 1, st);
+        launch_zgemm<double>(R, N, N, c128{1, 0}, A, N, 0, OP_N, V + q * NN, N, 0, OP_N, c128{0, 0}, U, N, 0, 1, st);
+        launch_rowdot<double>(R, N, U, A, N, nullptr, P->d_Sx, 0, 1, st);
+      } else {
+        c64* A = static_cast<c64*>(P->d_A);
+        launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK_MINUS_Q,
+                           P->p.sigma_lo, nsig, 0, nocc, A, P->Kx, 1, st);
+        launch_zgemm<float>(R, N, N, c64{1, 0}, A, P->Kx, 0, OP_N, P->d_Vx32, N, 0, OP_N, c64{0, 0}, P->d_Ux, P->Kx,
+                            0, 1, st);
+        launch_rowdot<float>(R, N, P->d_Ux, A, P->Kx, nullptr, P->d_Sx, 0, 1, st);
+      }
+      ++g_launch_count, k_sigx_accum<<<(nkk * nsig + 127) / 128, 128, 0, st>>>(nkk, kk0, nsig, nocc, P->d_Sx,
+                                                                             -1.0 / P->NK, sigx);
+    }
+    GW_TRY(check_launch(P, "gw_sigma_x"));
+  }
   return GW_OK;
 }
 

@@ -21,7 +21,8 @@ GW_FP64, GW_3XTF32, GW_3XBF16 = 0, 1, 2
 PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16}
 
 # every symbol include/gw.h declares
-EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_g0w0", "gw_g0w0_batch",
+EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_sigma_x", "gw_g0w0",
+           "gw_g0w0_batch",
            "gw_plan_n_sys", "gw_qp",
            "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_plan_chi0_terms", "gw_kernel_launches",
            "gw_surrogate_param_count", "gw_surrogate_create", "gw_surrogate_destroy", "gw_surrogate_get_params",
@@ -90,6 +91,7 @@ def load():
     lib.gw_screen.argtypes = [vp, i32, i32, vp]
     lib.gw_sigma.argtypes = [vp, i32, i32, vp]
     lib.gw_g0w0.argtypes = [vp, i32, vp]
+    lib.gw_sigma_x.argtypes = [vp, i32, vp]
     lib.gw_g0w0_batch.argtypes = [vp, ctypes.POINTER(vp), i32]
     lib.gw_plan_n_sys.argtypes = [vp, ctypes.POINTER(i32)]
     lib.gw_qp.argtypes = [vp, i32, vp, vp, dp, dp, ctypes.POINTER(i32)]
@@ -178,6 +180,11 @@ def gw_screen(plan, sys, q, wc_out=None):
 
 def gw_sigma(plan, sys, q, sigma_acc=None):
     _check(load().gw_sigma(plan, sys, q, _ptr(sigma_acc)))
+
+
+def gw_sigma_x(plan, sys, sigx):
+    """sigx: device float64 tensor [N_k][n_sigma] (overwritten)."""
+    _check(load().gw_sigma_x(plan, sys, _ptr(sigx)))
 
 
 def gw_g0w0(plan, sys, sigma_acc=None):

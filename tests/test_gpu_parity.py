@@ -139,3 +139,25 @@ def test_g0w0_driver_matches_per_q_calls(cfg0, prec):
     assert np.abs(sig - ref["sigma"]).max() * HA_MEV < (1e-6 if prec == "fp64" else 1.0)
     assert abs(gap - ref["gap"]) * HA_MEV < (1e-6 if prec == "fp64" else 1.0)
     assert ms > 0 and fl > 0
+
+
+@pytest.mark.parametrize("prec,tol_mev", [("fp64", 1e-6), ("3xtf32", 1.0), ("3xbf16", 1.0)])
+def test_sigma_x_cfg0(prec, tol_mev):
+    """Exchange self-energy against the oracle (FP64 path to rounding; split paths use FP32 products)."""
+    from paper_2011_01400_gb300 import gw
+    s = make_system("cfg0", seed=0)
+    ref = O.sigma_x(s)
+    pb = gw.Problem(s, prec)
+    plan = gw.gw_plan_create(pb.prob)
+    try:
+        out = torch.empty((s.n_k, s.sigma_hi - s.sigma_lo), dtype=torch.float64, device="cuda")
+        gw.gw_sigma_x(plan, 0, out)
+        gw.gw_sigma_x(plan, 0, out)      # overwritten, not accumulated
+        got = out.cpu().numpy()
+    finally:
+        gw.gw_plan_destroy(plan)
+    err = np.abs(got - ref).max() * HA_MEV
+    print(f"{prec}: Sigma_x max err {err:.3e} meV (|Sigma_x| max {np.abs(ref).max() * HA_MEV:.0f} meV)")
+    assert err <= tol_mev
+    if prec == "fp64":
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
