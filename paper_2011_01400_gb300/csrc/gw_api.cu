@@ -694,9 +694,9 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
     launch_rank1(N, P->d_Vh, P->d_x1, t_shift - P->h_v1, st);
   }
   if (P->fp64)
-    s = newton_schulz<double>(P, P->d_Vh, P->d_Vh, P->NK, 40);
+    s = newton_schulz<double>(P, P->d_Vh, P->d_Vh, P->NK, 24);
   else
-    s = newton_schulz<float>(P, P->d_Vh, P->d_Vh, P->NK, 40);
+    s = newton_schulz<float>(P, P->d_Vh, P->d_Vh, P->NK, 24);
   if (s != GW_OK) return cleanup(s);
   if (prob->head_wings) {
     // Vb0 = sqrt(B) - sqrt(t) x1 x1^H ;  Vh(0) = Vb0 + sqrt(v1) x1 x1^H

@@ -62,7 +62,71 @@ void launch_lri_halfT(const LriGeom& g, const double* ctil, const c128* evec, cp
   }
 }
 template void launch_lri_halfT<double>(const LriGeom&, const double*, const c128*, c128*, c128*, cudaStream_t);
-template void launch_lri_halfT<float>(const LriGeom&, const double*, const c128*, c64*, c64*, cudaStream_t);
+
+// fp32 (split-precision plans): the same sums as batched complex GEMMs, one per lattice vector R,
+//   T1[k] (+)= C~(R) [(mu,i)][j] . (e^{2 pi i k.R} c(k)) [j][b],   batched over k,
+// with C~(R) real (zero imaginary part) and the phase folded into a copy of c(k).
+namespace {
+
+__global__ void k_real_to_c64(long long n, const double* __restrict__ x, c64* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = c64{(float)x[e], 0.f};
+}
+
+// cR[k][j][b] = e^{2 pi i k.R_r} c(k)[j][b] (phase in FP64)
+__global__ void k_phase_evec(const __grid_constant__ LriGeom g, int r, const c128* __restrict__ evec,
+                             c64* __restrict__ cR) {
+  const long long per_k = (long long)g.NB * g.NBd, n = per_k * g.NK;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / per_k);
+    const int k3 = k % g.nk[2], k2 = (k / g.nk[2]) % g.nk[1], k1 = k / (g.nk[1] * g.nk[2]);
+    const double ph = 2.0 * ((double)k1 * g.R[r][0] / g.nk[0] + (double)k2 * g.R[r][1] / g.nk[1] +
+                             (double)k3 * g.R[r][2] / g.nk[2]);
+    double sn, cs;
+    sincospi(ph, &sn, &cs);
+    const c128 v = evec[e];
+    cR[e] = c64{(float)(cs * v.re - sn * v.im), (float)(cs * v.im + sn * v.re)};
+  }
+}
+
+}  // namespace
+
+template <>
+void launch_lri_halfT<float>(const LriGeom& g, const double* ctil, const c128* evec, c64* T1, c64* /*T2*/,
+                             cudaStream_t st) {
+  const long long per_k = (long long)g.NB * g.NBd;
+  long long amax = 0;
+  for (int A = 0; A < g.n_atoms; ++A) amax = std::max(amax, (long long)g.atom_nx[A] * g.atom_nb[A] * g.NB);
+  c64 *cR = nullptr, *At = nullptr;
+  if (cudaMallocAsync(&cR, sizeof(c64) * per_k * g.NK, st) != cudaSuccess ||
+      cudaMallocAsync(&At, sizeof(c64) * amax, st) != cudaSuccess) {
+    // fall back to the direct kernel (same sums, FP64 arithmetic) when the staging does not fit
+    cudaGetLastError();
+    if (cR) cudaFreeAsync(cR, st);
+    if (At) cudaFreeAsync(At, st);
+    for (int A = 0; A < g.n_atoms; ++A) {
+      long long total = (long long)g.NK * g.atom_nx[A] * g.atom_nb[A] * g.NBd;
+      int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 64);
+      ++::gw::g_launch_count, k_lri_halfT<float><<<blocks, 256, 0, st>>>(g, ctil, evec, T1, A);
+    }
+    return;
+  }
+  for (int r = 0; r < g.nR; ++r) {
+    ++::gw::g_launch_count, k_phase_evec<<<(unsigned)std::min<long long>((per_k * g.NK + 255) / 256, 152LL * 32), 256,
+                                           0, st>>>(g, r, evec, cR);
+    for (int A = 0; A < g.n_atoms; ++A) {
+      const int nx = g.atom_nx[A], nb = g.atom_nb[A];
+      const long long rows = (long long)nx * nb;
+      const double* cA = ctil + g.ctil_off[A] + (long long)r * rows * g.NB;
+      ++::gw::g_launch_count, k_real_to_c64<<<(unsigned)std::min<long long>((rows * g.NB + 255) / 256, 152LL * 32), 256,
+                                             0, st>>>(rows * g.NB, cA, At);
+      launch_zgemm<float>((int)rows, g.NBd, g.NB, c64{1, 0}, At, g.NB, 0, OP_N, cR, g.NBd, per_k, OP_N,
+                          c64{r == 0 ? 0.f : 1.f, 0}, T1 + g.t_off[A], g.NBd, rows * g.NBd, g.NK, st);
+    }
+  }
+  cudaFreeAsync(cR, st);
+  cudaFreeAsync(At, st);
+}
 
 // ---------------------------------------------------------------------------------------------
 // M generation. One block per (row-k kk, block of MU ABFs); threads over (a, b) pairs.
