@@ -296,6 +296,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_inv(int N, c128* __restri
 
 void launch_chol_inv_minus_I(int N, c128* A, int batch, long long stride, c128* work, int* status, cudaStream_t st) {
   size_t smem = sizeof(c128) * (size_t)N;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   ++::gw::g_launch_count, k_chol_inv<<<batch, CHOL_THREADS, smem, st>>>(N, A, stride, work, status);
 }
 
@@ -378,7 +379,9 @@ __global__ void k_power_iter(int N, const c128* __restrict__ A, c128* __restrict
   for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = cmul(v[i], ph);
 }
 void launch_power_iter(int N, const c128* A, c128* x, double* lam, int iters, cudaStream_t st) {
-  ++::gw::g_launch_count, k_power_iter<<<1, 512, 2 * N * sizeof(c128), st>>>(N, A, x, lam, iters);
+  const int smem = 2 * N * (int)sizeof(c128);   // above 48 KB from N = 1536 on: opt in
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k_power_iter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  ++::gw::g_launch_count, k_power_iter<<<1, 512, smem, st>>>(N, A, x, lam, iters);
 }
 
 __global__ void k_rank1(int N, c128* A, const c128* x, double alpha) {
