@@ -160,6 +160,34 @@ def chi0(sys, iq, omegas):
     return -(sys.spin / sys.n_k) * out
 
 
+def chi0_block(sys, iq, omegas, mus):
+    """chi0_{mu nu}(q, i w) of Eq. (chi0_matrix) for mu, nu in the ABF subset `mus` only (the
+    Hermitised form of `chi0`), from the rows C~^mu(k+q, k) of Eq. (AO_triple_split2) built one ABF
+    at a time: for sampled checks of systems whose full C~ does not fit. Returns [w, len(mus), len(mus)]."""
+    kp = kpoints(sys.nk)
+    occ, unocc = np.arange(sys.n_occ), np.arange(sys.n_occ, sys.n_bands)
+    om = np.asarray(omegas, dtype=np.float64)
+    out = np.zeros((len(om), len(mus), len(mus)), dtype=np.complex128)
+    for ik in range(sys.n_k):
+        ikq = k_plus(sys.nk, ik, iq)
+        k, kq = kp[ik], kp[ikq]
+        Ms = []
+        for mu in mus:
+            A = int(sys.aux_atom[mu])
+            a = mu - int(np.nonzero(sys.aux_atom == A)[0][0])
+            ias = np.nonzero(sys.basis_atom == A)[0]
+            C = np.zeros((sys.n_basis, sys.n_basis), dtype=np.complex128)
+            C[ias, :] += lri_ft(sys.ctil_R[A][:, a:a + 1], sys.R, k)[0]
+            C[:, ias] += lri_ft(sys.ctil_R[A][:, a:a + 1], sys.R, -kq)[0].T
+            Ms.append(np.conj(sys.evec[ikq][:, unocc]).T @ C @ sys.evec[ik][:, occ])   # [a, i]
+        D = sys.eps[ikq][unocc][:, None] - sys.eps[ik][occ][None, :]
+        Mf = np.array([m.ravel() for m in Ms])                                         # [mu, (a,i)]
+        for j, w in enumerate(om):
+            wt = (2.0 * D / (w * w + D * D)).ravel()
+            out[j] += (Mf * wt[None, :]) @ np.conj(Mf).T
+    return -(sys.spin / sys.n_k) * out
+
+
 def chi0_literal(sys, iq, omegas):
     """Eq. (chi0_matrix) taken literally with occupations (f_m^{k+q} - f_n^k), both band orders.
 

@@ -63,3 +63,28 @@ def test_cfg1_one_q_full_size(cfg1_q1, prec, tol_chi, tol_w, tol_sig_mev):
     es = np.abs(sig - sig_ref).max() * HA_MEV
     print(f"cfg1 q={Q} {prec}: chi0 {ec:.2e}, W^c {ew:.2e}, Sigma_c term {es:.2e} meV")
     assert ec <= tol_chi and ew <= tol_w and es <= tol_sig_mev
+
+
+def test_cfg2_chi0_sampled_block():
+    """cfg2 (ZnO-like: 4 atoms, 6x6x4 k, 300 bands with 36 occupied, 1600 ABF, 32 frequencies; M
+    streamed per chunk of k): chi0 at q = 1 on a sampled 6 x 6 block of ABFs spread over all atoms,
+    against the oracle's block form, relative Frobenius <= 1e-6 per frequency (3xBF16)."""
+    from paper_2011_01400_gb300 import gw
+    s = make_system("cfg2", seed=2000)
+    om, _ = O.freq_grid(s.n_freq, s.omega0)
+    mus = [0, 399, 400, 801, 1203, 1599]
+    js = [0, 7, 15, 23, 31]
+    ref = O.chi0_block(s, Q, om[js], mus)
+    pb = gw.Problem(s, "3xbf16")
+    plan = gw.gw_plan_create(pb.prob)
+    chi = torch.empty((s.n_freq, s.n_aux, s.n_aux), dtype=torch.complex128, device="cuda")
+    try:
+        gw.gw_chi0(plan, 0, Q, chi)
+    finally:
+        gw.gw_plan_destroy(plan)
+    idx = torch.tensor(mus, device="cuda")
+    got = chi[js][:, idx][:, :, idx].cpu().numpy()
+    del chi
+    err = max(rel_fro(got[j], ref[j]) for j in range(len(js)))
+    print(f"cfg2 q={Q} 3xbf16: chi0 sampled block {err:.2e}")
+    assert err <= 1e-6

@@ -295,3 +295,14 @@ def test_sigma_x_negative_and_matches_loops():
                     ref[ik, n - s.sigma_lo] -= (a @ s.V[iq] @ np.conj(a)).real
     ref /= s.n_k
     assert np.allclose(got, ref, rtol=1e-10, atol=0)
+
+
+def test_chi0_block_is_a_block_of_chi0():
+    """The ABF-subset form reproduces the matching block of the full chi0 (independent assembly of
+    C~ one ABF at a time)."""
+    s = make_system("cfg0", seed=9)
+    om, _ = O.freq_grid(s.n_freq, s.omega0)
+    mus = [0, 17, 48, 95]
+    full = O.chi0(s, 3, om[:3])
+    blk = O.chi0_block(s, 3, om[:3], mus)
+    assert np.abs(blk - full[:, mus][:, :, mus]).max() <= 1e-13 * np.abs(full).max()
