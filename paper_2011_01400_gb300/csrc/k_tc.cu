@@ -281,18 +281,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_b[s], 1);
-      mbar_init(&full_a[s], PRE ? 1 : 128);
+      mbar_init(&full_a[s], PRE ? 1 : 4);       // one elected arrival per transform warp
       mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&t1full[b], 1);
-      mbar_init(&t1empty[b], 256);
+      mbar_init(&t1empty[b], 8);                // one per epilogue warp
       mbar_init(&t2full[b], 1);
-      mbar_init(&t2empty[b], 256);
+      mbar_init(&t2empty[b], 8);
     }
     for (int r = 0; r < RING; ++r) {
       mbar_init(&rfull[r], 1);
-      mbar_init(&rempty[r], 128);
+      mbar_init(&rempty[r], 4);
     }
     mbar_init(done, 1);
     fence_mbar_init();
@@ -443,11 +443,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
       const float* wrow = p.wtab + (long long)w * p.wstride;
       for (int i = first_stage<MODE, RS>(p, n0); i < nst; ++i, ++gs) {
         const int s = gs % STAGES;
-        if (!mbar_wait(&empty[s], ((gs / STAGES) & 1) ^ 1, p.status)) { ok = false; break; }
+        // warp-uniform waits: the arrivals below are elected per warp
+        if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ((gs / STAGES) & 1) ^ 1, p.status))) { ok = false; break; }
         uint8_t* at = smem + s * STAGE + NP * TILE;
         for (int h = 0; h < RPS; ++h, ++gr) {
           const int slot = gr % RING;
-          if (!mbar_wait(&rfull[slot], (gr / RING) & 1, p.status)) { ok = false; break; }
+          // the 16 weights of this slot's pair rows, loaded before the ring wait so that their
+          // latency overlaps it (pair rows i * RS + 16 h .., 16-byte aligned: Kpad % 32 == 0)
+          float wv[16];
+          {
+            const float4* w4 = reinterpret_cast<const float4*>(wrow + i * RS + 16 * h);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const float4 v = w4[c];
+              wv[4 * c] = v.x;
+              wv[4 * c + 1] = v.y;
+              wv[4 * c + 2] = v.z;
+              wv[4 * c + 3] = v.w;
+            }
+          }
+          if (!__all_sync(0xffffffffu, mbar_wait(&rfull[slot], (gr / RING) & 1, p.status))) { ok = false; break; }
           // this thread's row: 16 complex pairs (8 chunks of 16 B, 128B-swizzled by TMA)
           float x[32];
           const uint8_t* rs = ring + slot * RAW;
@@ -461,7 +476,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
           }
           // order these generic-proxy reads before the TMA (async-proxy) refill of the slot
           fence_proxy_async();
-          mbar_arrive(&rempty[slot]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&rempty[slot]);
           const int r0 = i * RS + 16 * h;      // first pair row of this slot
           if constexpr (TF32) {
             // A row = 16 pairs = 8 chunks of 2 pairs
@@ -470,7 +486,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
               uint32_t o0[4], o1[4];
 #pragma unroll
               for (int q = 0; q < 2; ++q) {
-                const float wt = wrow[r0 + 2 * c + q];
+                const float wt = wv[2 * c + q];
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                   const float y = wt * x[4 * c + 2 * q + e];
@@ -491,7 +507,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
                 const int pr = 4 * cc + q;     // pair within the slot
-                const float wt = wrow[r0 + pr];
+                const float wt = wv[pr];
                 const float yr = wt * x[2 * pr], yi = wt * x[2 * pr + 1];
                 const __nv_bfloat162 hh = __floats2bfloat162_rn(yr, yi);
                 const float2 hf = __bfloat1622float2(hh);
@@ -516,7 +532,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
         }
         if (!ok) break;
         fence_proxy_async();
-        mbar_arrive(&full_a[s]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full_a[s]);
       }
     }
   } else if (warp >= 6 && warp <= 13) {
@@ -557,7 +574,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
             }
           }
           tc_fence_before();
-          mbar_arrive(&t1empty[b]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&t1empty[b]);
         }
         if (seg_end) {
           const int b2 = gseg & 1;
@@ -577,7 +595,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
             }
           }
           tc_fence_before();
-          mbar_arrive(&t2empty[b2]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&t2empty[b2]);
           ++gseg;
           const int nmax = p.Ncols - c0;
           if (m < p.Mrows) {
