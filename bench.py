@@ -26,6 +26,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "G0W0 Σc time-to-solution & χ0 TFLOP/s: split-prec vs FP64 on 1 GB300 @ ≤1 meV"
+# DRAM bytes of one chi0 contraction launch (dram__bytes_read.sum, dram__bytes_write.sum), from an
+# ncu capture of the cfg1 shape on a 4x4x4 k mesh (q = 1, 3xBF16; the k_tc capture under profiles/).
+# The reads stream the operand planes of every k and grow with the k count; the writes are the
+# compressed output rows, independent of it.
+CHI0_DRAM_CAPTURE = dict(prec="3xbf16", n_k=64, n_aux=400, read=436.19456e6, write=26.565888e6)
 WORKLOADS = {
     "cfg0": "tiny synthetic insulator: 2x2x2 k, 2 atoms, 32 NAO, 32 bands (4 occ), 96 ABF, 16 imaginary frequencies",
     "cfg1": "Si-like 2-atom fcc cell: 6x6x6 k (216 k, 216 q), 78 NAO, 78 bands (4 occ), 400 ABF, 32 imaginary "
@@ -475,6 +480,10 @@ def run_device(args, system, world, rank):
     peak = peak_bf16 * (0.5 if tf32 else 1.0) if args.prec != "fp64" else 1.25
     achieved = chi_flops / (chi_avg_ms * 1e-3) / 1e12
     products = {"3xbf16": 6, "3xtf32": 3, "fp64": 1}[args.prec]
+    cap = CHI0_DRAM_CAPTURE
+    traffic = None
+    if args.prec == cap["prec"] and s.n_aux == cap["n_aux"]:
+        traffic = cap["read"] * s.n_k / cap["n_k"] + cap["write"]
     line = dict(
         metric=METRIC,
         value=ms / 1e3 / world,
@@ -490,7 +499,10 @@ def run_device(args, system, world, rank):
         chi0_tflops=achieved,
         step_useful_tflops=fl["total"] / (ms * 1e-3) / 1e12,
         roofline=dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                      traffic=None, kernel="k_tc<chi0> (tcgen05 weighted Hermitian update)",
+                      traffic=traffic, kernel="k_tc<chi0> (tcgen05 weighted Hermitian update)",
+                      traffic_note=None if traffic is None else
+                      f"DRAM bytes per launch (one q), scaled from an ncu capture on {cap['n_k']} k: "
+                      f"reads x {s.n_k}/{cap['n_k']}, writes as captured",
                       peak_note=f"{'TF32' if tf32 else 'BF16'} dense {peak_kind}; achieved counts algorithmic "
                                 f"flops (8 per complex MAC, lower triangle, all {s.n_freq} frequencies); the "
                                 f"kernel runs {T_rows} compressed weight rows instead of {s.n_freq} frequencies and "
@@ -498,8 +510,8 @@ def run_device(args, system, world, rank):
                                 f"{T_rows}/{s.n_freq}",
                       chi0_weight_rows=T_rows,
                       tensor_issued_frac=achieved * products * T_rows / s.n_freq / peak),
-        e2e=dict(value=ms_e2e / 1e3 / world, unit="s", h2d_bytes_per_step=pb.nbytes(),
-                 d2h_bytes_per_step=s.n_k * (s.sigma_hi - s.sigma_lo) * 8 + 8),
+        e2e=None if args.no_e2e else dict(value=ms_e2e / 1e3 / world, unit="s", h2d_bytes_per_step=pb.nbytes(),
+                                          d2h_bytes_per_step=s.n_k * (s.sigma_hi - s.sigma_lo) * 8 + 8),
         gpu_launches=launches,
         clocks=ck,
         fp64_gpu=fp64,
