@@ -73,10 +73,109 @@ __global__ void __launch_bounds__(256) k_zgemm(int m, int n, int k, cplx<T> alph
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP32 complex GEMM for op(A) = A, op(B) = B (row-major, batched): C = alpha A B + beta C.
+// 80x80 tile (N = 400 = 5 tiles), 256 threads as 16 x 16, 5 x 5 outputs per thread (rows
+// ty + 16 i, columns tx + 16 j), K chunk 16 double-buffered through registers. The A tile is
+// stored K-major with a row pitch of 81 complex so that the 16 threads filling one A row write
+// 16 distinct bank pairs.
+// ---------------------------------------------------------------------------------------------
+constexpr int CG_T = 80, CG_K = 16, CG_AP = 81;
+
+__global__ void __launch_bounds__(256, 2) k_cgemm_nn(int m, int n, int k, c64 alpha, const c64* __restrict__ A,
+                                                    long long lda, long long sA, const c64* __restrict__ B,
+                                                    long long ldb, long long sB, c64 beta, c64* __restrict__ C,
+                                                    long long ldc, long long sC) {
+  __shared__ float2 As[2][CG_K][CG_AP];
+  __shared__ float2 Bs[2][CG_K][CG_T];
+  const int bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int m0 = blockIdx.y * CG_T, n0 = blockIdx.x * CG_T;
+  const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+  // global -> register staging: 5 A elements (row e / 16, k e % 16) and 5 B elements
+  // (k e / 80, column e % 80) for e = t + 256 c
+  float2 ra[5], rb[5];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const int e = t + 256 * c;
+      const int ar = m0 + e / CG_K, ak = k0 + e % CG_K;
+      ra[c] = (ar < m && ak < k) ? *reinterpret_cast<const float2*>(A + (long long)ar * lda + ak) : make_float2(0.f, 0.f);
+      const int bk = k0 + e / CG_T, bc = n0 + e % CG_T;
+      rb[c] = (bk < k && bc < n) ? *reinterpret_cast<const float2*>(B + (long long)bk * ldb + bc) : make_float2(0.f, 0.f);
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const int e = t + 256 * c;
+      As[buf][e % CG_K][e / CG_K] = ra[c];
+      Bs[buf][e / CG_T][e % CG_T] = rb[c];
+    }
+  };
+  float2 acc[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  fetch(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < k; k0 += CG_K) {
+    const bool more = k0 + CG_K < k;
+    if (more) fetch(k0 + CG_K);
+#pragma unroll
+    for (int kk = 0; kk < CG_K; ++kk) {
+      float2 a[5], b[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 5; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+          acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+          acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+          acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+        }
+    }
+    if (more) {
+      stash(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+  const bool use_beta = beta.re != 0.f || beta.im != 0.f;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+      if (gm < m && gn < n) {
+        c64* c = C + (long long)gm * ldc + gn;
+        c64 v = cmul(alpha, c64{acc[i][j].x, acc[i][j].y});
+        if (use_beta) v = cfma(beta, *c, v);
+        *c = v;
+      }
+    }
+}
+
 template <typename T>
 void launch_zgemm(int m, int n, int k, cplx<T> alpha, const cplx<T>* A, long long lda, long long sA, Op opA,
                   const cplx<T>* B, long long ldb, long long sB, Op opB, cplx<T> beta, cplx<T>* C, long long ldc,
                   long long sC, int batch, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (opA == OP_N && opB == OP_N) {
+      dim3 grid((n + CG_T - 1) / CG_T, (m + CG_T - 1) / CG_T, batch);
+      ++::gw::g_launch_count, k_cgemm_nn<<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC);
+      return;
+    }
+  }
   dim3 grid((n + 63) / 64, (m + 63) / 64, batch);
   ++::gw::g_launch_count, k_zgemm<T><<<grid, 256, 0, st>>>(m, n, k, alpha, A, lda, sA, (int)opA, B, ldb, sB, (int)opB, beta, C, ldc, sC);
 }

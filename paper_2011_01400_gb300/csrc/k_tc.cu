@@ -60,6 +60,8 @@ constexpr int ROWB = 128;                          // bytes per operand row per 
 constexpr int TILE = 128 * ROWB;                   // 16 KB: A piece (128 rows) or B piece ([B1; B2], 128 rows)
 constexpr int HALF = 64 * ROWB;                    // 8 KB: B1 or B2 part of a B piece
 constexpr int RAW = 128 * ROWB;                    // 16 KB: one ring slot = 16 complex pairs of 128 A rows
+constexpr int RAW_BOXES = 2 * BN / 32;             // fp32 boxes (32 floats x 128 rows) of one BN-column a tile
+constexpr int WBYTES = 16 * 4;                     // weights of the 16 pair rows of one ring slot
 constexpr int NTHREADS = 480;
 constexpr int MAX_TILES = 8192;
 constexpr long long WAIT_LIMIT = 4000000000LL;     // clock64 ticks (~2 s) per wait
@@ -73,7 +75,8 @@ template <bool TF32, int NP_> struct Cfg {
   static constexpr int RPS = TF32 ? 1 : 2;         // ring slots per stage
   static constexpr int RING = (NP_ == 3) ? 2 : 4;  // ring slots
   static constexpr int RS = 16 * RPS;              // complex pair rows per stage
-  static constexpr int BAR_OFF = STAGES * STAGE + RING * RAW;
+  static constexpr int WB_OFF = STAGES * STAGE + RING * RAW;   // the 16 weights of each ring slot
+  static constexpr int BAR_OFF = WB_OFF + RING * WBYTES;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;
 };
 static_assert(Cfg<false, 3>::SMEM <= 232448, "shared memory budget");
@@ -128,6 +131,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// 1-D bulk copy global -> shared (both 16-byte aligned, size a multiple of 16 bytes)
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
                : "memory");
@@ -160,19 +171,34 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 32 lanes x 32 consecutive 32-bit columns (one per thread row); the wait is separate.
-__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+// tcgen05.ld issues asynchronously; tmem_wait_ld() waits for this thread's loads.
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// 32 lanes x 16 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// sr[j] += D[re column t + j], si[j] += D[im column t + BN + j], j < 32, sixteen columns at a time
+// (keeps the running sums and one half of the drained columns in registers)
+__device__ __forceinline__ void drain_add(uint32_t t, float (&sr)[32], float (&si)[32]) {
+  uint32_t vr[16], vi[16], wr[16], wi[16];
+  tmem_ld16_nowait(t, vr);
+  tmem_ld16_nowait(t + BN, vi);
+  tmem_ld16_nowait(t + 16, wr);
+  tmem_ld16_nowait(t + BN + 16, wi);
+  tmem_wait_ld();
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    sr[j] += __uint_as_float(vr[j]);
+    si[j] += __uint_as_float(vi[j]);
+    sr[16 + j] += __uint_as_float(wr[j]);
+    si[16 + j] += __uint_as_float(wi[j]);
+  }
+}
 
 // UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -260,9 +286,11 @@ template <bool TF32, int NPC, int MODE, bool PRE>
 __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps maps, TcParams p) {
   using C = Cfg<TF32, NPC>;
   constexpr int NP = C::NP, STAGES = C::STAGES, STAGE = C::STAGE, RS = C::RS, RPS = C::RPS, RING = C::RING;
+  static_assert(!(MODE == 1 && PRE) || RING >= RAW_BOXES, "the a tile of the row dot must fit in the ring");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = smem + STAGES * STAGE;
+  float* wbuf = reinterpret_cast<float*>(smem + C::WB_OFF);   // [RING][16]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
   uint64_t* full_b = bars;                   // [STAGES]
   uint64_t* full_a = bars + STAGES;          // [STAGES]
@@ -292,7 +320,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
     }
     for (int r = 0; r < RING; ++r) {
       mbar_init(&rfull[r], 1);
-      mbar_init(&rempty[r], 4);
+      mbar_init(&rempty[r], PRE ? 8 : 4);        // PRE: the a tile of the row dot, read by the epilogue
     }
     mbar_init(done, 1);
     fence_mbar_init();
@@ -334,7 +362,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
   } else if (warp == 14 && PRE) {
     // ---------------- TMA producer: A pieces (split before the launch) into the stages ----------------
     if (lane == 0) {
-      uint32_t gs = 0;
+      uint32_t gs = 0, gt = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         int m0, n0, w;
@@ -348,21 +376,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
 #pragma unroll
           for (int pc = 0; pc < NP; ++pc) tma_load_2d(at + pc * TILE, &maps.a[pc], &full_a[s], x, m0);
         }
+        if (MODE == 1 && ok) {
+          // the fp32 a tile of the epilogue's row dot (rows m0.., columns n0..n0+BN-1) into the ring:
+          // RAW_BOXES boxes of 32 floats x 128 rows; issued after the item's stages, since it is read
+          // only at the item's end, once the previous item's epilogue has released it
+          const uint32_t par = (gt & 1) ^ 1;
+          if (!mbar_wait(&rempty[0], par, p.status)) break;
+          mbar_arrive_expect_tx(&rfull[0], RAW_BOXES * RAW);
+#pragma unroll
+          for (int c = 0; c < RAW_BOXES; ++c) tma_load_2d(ring + c * RAW, &maps.raw, &rfull[0], 2 * n0 + 32 * c, m0);
+          ++gt;
+        }
       }
     }
   } else if (warp == 14) {
-    // ---------------- TMA producer: A rows of the fp32 plane into the ring ----------------
+    // ---------------- TMA producer: A rows of the fp32 plane and their weights into the ring ----------------
     if (lane == 0) {
       uint32_t gr = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
         int m0, n0, w;
         decode_item<MODE>(p, item, m0, n0, w);
+        const float* wrow = p.wtab + (long long)w * p.wstride;
         for (int i = first_stage<MODE, RS>(p, n0) * RPS; i < nst * RPS; ++i, ++gr) {
           const int slot = gr % RING;
           if (!mbar_wait(&rempty[slot], ((gr / RING) & 1) ^ 1, p.status)) { ok = false; break; }
-          mbar_arrive_expect_tx(&rfull[slot], RAW);
+          mbar_arrive_expect_tx(&rfull[slot], RAW + WBYTES);
           tma_load_2d(ring + slot * RAW, &maps.raw, &rfull[slot], i * 32, m0);
+          // pair rows 16 i .. 16 i + 15 (16-byte aligned: the weight rows are Kpad = 0 mod 32 floats apart)
+          bulk_load(wbuf + slot * 16, wrow + 16 * i, WBYTES, &rfull[slot]);
         }
       }
     }
@@ -440,7 +482,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
     for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
       int m0, n0, w;
       decode_item<MODE>(p, item, m0, n0, w);
-      const float* wrow = p.wtab + (long long)w * p.wstride;
       for (int i = first_stage<MODE, RS>(p, n0); i < nst; ++i, ++gs) {
         const int s = gs % STAGES;
         // warp-uniform waits: the arrivals below are elected per warp
@@ -448,21 +489,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
         uint8_t* at = smem + s * STAGE + NP * TILE;
         for (int h = 0; h < RPS; ++h, ++gr) {
           const int slot = gr % RING;
-          // the 16 weights of this slot's pair rows, loaded before the ring wait so that their
-          // latency overlaps it (pair rows i * RS + 16 h .., 16-byte aligned: Kpad % 32 == 0)
-          float wv[16];
-          {
-            const float4* w4 = reinterpret_cast<const float4*>(wrow + i * RS + 16 * h);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const float4 v = w4[c];
-              wv[4 * c] = v.x;
-              wv[4 * c + 1] = v.y;
-              wv[4 * c + 2] = v.z;
-              wv[4 * c + 3] = v.w;
-            }
-          }
           if (!__all_sync(0xffffffffu, mbar_wait(&rfull[slot], (gr / RING) & 1, p.status))) { ok = false; break; }
+          // the 16 weights of this slot's pair rows (delivered with the slot; broadcast reads)
+          float wv[16];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float4 v = reinterpret_cast<const float4*>(wbuf + slot * 16)[c];
+            wv[4 * c] = v.x;
+            wv[4 * c + 1] = v.y;
+            wv[4 * c + 2] = v.z;
+            wv[4 * c + 3] = v.w;
+          }
           // this thread's row: 16 complex pairs (8 chunks of 16 B, 128B-swizzled by TMA)
           float x[32];
           const uint8_t* rs = ring + slot * RAW;
@@ -478,7 +515,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) mbar_arrive(&rempty[slot]);
-          const int r0 = i * RS + 16 * h;      // first pair row of this slot
           if constexpr (TF32) {
             // A row = 16 pairs = 8 chunks of 2 pairs
 #pragma unroll
@@ -542,13 +578,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
     const int half = (warp - 6) >> 2;          // output columns half*32 .. half*32+31
     const int row = quad * 32 + lane;
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
-    uint32_t gs = 0, gseg = 0;
+    uint32_t gs = 0, gseg = 0, gt = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
       int m0, n0, w;
       decode_item<MODE>(p, item, m0, n0, w);
       const int m = m0 + row;
       const int c0 = n0 + half * 32;
+      bool tile_ready = false;                 // MODE 1, PRE: the a tile of this item has landed
       float sr[32], si[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
@@ -561,18 +598,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
           ok = __all_sync(0xffffffffu, mbar_wait(&t1full[b], ph, p.status));
           if (!ok) break;
           tc_fence_after();
-          {
-            uint32_t vr[32], vi[32];
-            const uint32_t t = tmem + lane_off + D1_COL + b * DBUF + half * 32;
-            tmem_ld32_nowait(t, vr);
-            tmem_ld32_nowait(t + BN, vi);
-            tmem_wait_ld();
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              sr[j] += __uint_as_float(vr[j]);
-              si[j] += __uint_as_float(vi[j]);
-            }
-          }
+          drain_add(tmem + lane_off + D1_COL + b * DBUF + half * 32, sr, si);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&t1empty[b]);
@@ -582,23 +608,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
           ok = __all_sync(0xffffffffu, mbar_wait(&t2full[b2], (gseg >> 1) & 1, p.status));
           if (!ok) break;
           tc_fence_after();
-          {
-            uint32_t vr[32], vi[32];
-            const uint32_t t = tmem + lane_off + D2_COL + b2 * DBUF + half * 32;
-            tmem_ld32_nowait(t, vr);
-            tmem_ld32_nowait(t + BN, vi);
-            tmem_wait_ld();
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              sr[j] += __uint_as_float(vr[j]);
-              si[j] += __uint_as_float(vi[j]);
-            }
-          }
+          drain_add(tmem + lane_off + D2_COL + b2 * DBUF + half * 32, sr, si);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&t2empty[b2]);
           ++gseg;
           const int nmax = p.Ncols - c0;
+          if (MODE == 1 && PRE && !tile_ready) {
+            ok = __all_sync(0xffffffffu, mbar_wait(&rfull[0], gt & 1, p.status));
+            if (!ok) break;
+            tile_ready = true;
+          }
           if (m < p.Mrows) {
             if constexpr (MODE == 0) {
               c128* orow = p.out + ((long long)w * p.Ncols + m) * p.Ncols + c0;
@@ -611,6 +631,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
                   orow[j] = o;
                 }
               }
+            } else if constexpr (PRE) {
+              // S_r += Re sum_nu U_{r nu} conj(a_{r nu}) over this thread's 32 columns, a from the
+              // ring tile (complex column 32 half + j: box 2 half + j / 16, 16-B chunk (j % 16) / 2)
+              float acc = 0.f;
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const float4 a = *reinterpret_cast<const float4*>(ring + (2 * half + jj / 8) * RAW + swz(row, jj % 8));
+                if (2 * jj < nmax) acc = fmaf(sr[2 * jj], a.x, fmaf(si[2 * jj], a.y, acc));
+                if (2 * jj + 1 < nmax) acc = fmaf(sr[2 * jj + 1], a.z, fmaf(si[2 * jj + 1], a.w, acc));
+              }
+              const float wgt = (p.tri && i > first_stage<MODE, RS>(p, n0) + (BN / RS) - 1) ? 2.f : 1.f;
+              atomicAdd(p.S + (long long)m * p.nw + w, wgt * acc);
             } else {
               // S_r += Re sum_nu U_{r nu} conj(a_{r nu}) over this thread's 32 columns
               const float* arow = p.raw + (long long)m * p.ldk + 2LL * c0;
@@ -629,6 +661,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_tc(const __grid_constant__ Maps
           }
 #pragma unroll
           for (int j = 0; j < 32; ++j) sr[j] = si[j] = 0.f;
+          if (MODE == 1 && PRE && i == nst - 1) {
+            // last segment of the item: release the a tile (generic reads before the TMA refill)
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&rempty[0]);
+            ++gt;
+          }
         }
       }
     }
