@@ -132,19 +132,28 @@ __global__ void __launch_bounds__(256) k_wresid(int K, int nw, const double* __r
 __global__ void k_wtab_compressed(int K, int Kpad, int nw, int T, const double* __restrict__ delta,
                                   const double* __restrict__ freq, const double* __restrict__ Pm,
                                   float* __restrict__ wtab) {
-  const long long total = (long long)T * Kpad;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(e / Kpad), r = (int)(e % Kpad);
-    double s = 0.0;
-    if (r < K) {
-      const double d = delta[r];
-      for (int j = 0; j < nw; ++j) {
-        const double w = freq[j];
-        s += Pm[j * nw + t] * (2.0 * d / (w * w + d * d));
+  // one pair row per thread, 8 weight rows at a time: each Lorentzian weight is evaluated
+  // ceil(T / 8) times instead of T times (the sum over j runs in the same order)
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < Kpad;
+       r += (long long)gridDim.x * blockDim.x) {
+    const double d = r < K ? delta[r] : 0.0;
+    for (int t0 = 0; t0 < T; t0 += 8) {
+      double s[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s[u] = 0.0;
+      if (r < K) {
+        for (int j = 0; j < nw; ++j) {
+          const double w = freq[j];
+          const double wt = 2.0 * d / (w * w + d * d);
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (t0 + u < T) s[u] += Pm[j * nw + t0 + u] * wt;
+        }
       }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (t0 + u < T) wtab[(long long)(t0 + u) * Kpad + r] = (float)s[u];
     }
-    wtab[e] = (float)s;
   }
 }
 
@@ -194,8 +203,7 @@ void launch_wresid(int K, int nw, const double* delta, const double* freq, const
 
 void launch_wtab_compressed(int K, int Kpad, int nw, int T, const double* delta, const double* freq, const double* Pm,
                             float* wtab, cudaStream_t st) {
-  const long long total = (long long)T * Kpad;
-  ++g_launch_count, k_wtab_compressed<<<(unsigned)std::min<long long>((total + 255) / 256, 152 * 32), 256, 0, st>>>(
+  ++g_launch_count, k_wtab_compressed<<<(unsigned)std::min<long long>(((long long)Kpad + 255) / 256, 152 * 32), 256, 0, st>>>(
       K, Kpad, nw, T, delta, freq, Pm, wtab);
 }
 

@@ -270,10 +270,16 @@ template void launch_chi0_simt<float>(int, int, const c64*, long long, const flo
 
 // ---------------------------------------------------------------------------------------------
 // FP64 Cholesky factorisation and inversion of eps~ (Hermitian positive definite), one block
-// per matrix: eps~ = U^H U (up-looking, in place in the upper triangle), U^{-1} by backward
-// substitution (work buffer), then A := U^{-1} U^{-H} - I.
+// per matrix:
+//   1) eps~ = U^H U, up-looking, U in place in the upper triangle;
+//   2) W = U^{-1} (upper) by backward substitution into the work buffer;
+//   3) A := W W^H - I (= eps~^{-1} - I), lower 32 x 32 tiles from shared-memory K chunks, mirrored.
+// The dot products of one step of 1) and 2) have lengths up to N while only N - j of them exist,
+// so each is split over P threads (k strided, P = threads / dots, at least 16 terms per part) and
+// the parts are combined in shared memory: the late steps, few long dots, run in parallel.
 // ---------------------------------------------------------------------------------------------
 constexpr int CHOL_THREADS = 512;
+constexpr int CHOL_T = 32, CHOL_TP = CHOL_T + 1;   // phase-3 tile and its row pitch (complex)
 
 __device__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -292,21 +298,45 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
+// s += conj(c) u and s += u w as explicit fused multiply-adds (4 DFMA per complex product; the
+// unfused a*b + c*d form costs a multiply, a fused multiply-add and an add per pair)
+__device__ __forceinline__ void chol_cmac_conj(c128 c, c128 u, double& sr, double& si) {
+  sr = fma(c.im, u.im, fma(c.re, u.re, sr));
+  si = fma(-c.im, u.re, fma(c.re, u.im, si));
+}
+__device__ __forceinline__ void chol_cmac(c128 u, c128 w, double& sr, double& si) {
+  sr = fma(-u.im, w.im, fma(u.re, w.re, sr));
+  si = fma(u.im, w.re, fma(u.re, w.im, si));
+}
+
+// parts per dot: n dots of length up to len over `threads` threads
+__device__ __forceinline__ int chol_parts(int n, int len, int threads) {
+  if (n <= 0) return 1;
+  return max(1, min(threads / n, len / 16));
+}
+
+size_t chol_smem_bytes(int N) {
+  return sizeof(c128) * std::max<size_t>((size_t)N + CHOL_THREADS, (size_t)2 * CHOL_T * CHOL_TP);
+}
+
 __global__ void __launch_bounds__(CHOL_THREADS) k_chol_inv(int N, c128* __restrict__ Aall, long long stride,
                                                            c128* __restrict__ Wall, int* __restrict__ status) {
-  extern __shared__ c128 col[];      // [N]
+  extern __shared__ c128 dyn[];
+  c128* col = dyn;                   // [N]: the current column (1) or row (2) of U
+  c128* part = dyn + N;              // [CHOL_THREADS]: partial dot products
   __shared__ double red[32];
   __shared__ double s_piv;
+  const int t = threadIdx.x, bd = blockDim.x;
   c128* A = Aall + blockIdx.x * stride;
   c128* W = Wall + blockIdx.x * stride;
   // 1) eps~ = U^H U: U[j][i] = (A[j][i] - sum_{k<j} conj(U[k][j]) U[k][i]) / U[j][j]
   for (int j = 0; j < N; ++j) {
-    for (int k = threadIdx.x; k < j; k += blockDim.x) col[k] = A[(long long)k * N + j];
+    for (int k = t; k < j; k += bd) col[k] = A[(long long)k * N + j];
     __syncthreads();
-    double part = 0;
-    for (int k = threadIdx.x; k < j; k += blockDim.x) part += col[k].re * col[k].re + col[k].im * col[k].im;
-    double s = block_sum(part, red);
-    if (threadIdx.x == 0) {
+    double pp = 0;
+    for (int k = t; k < j; k += bd) pp = fma(col[k].im, col[k].im, fma(col[k].re, col[k].re, pp));
+    const double s = block_sum(pp, red);
+    if (t == 0) {
       double piv = A[(long long)j * N + j].re - s;
       if (!(piv > 0.0)) {
         atomicOr(status, ST_NOT_PD);
@@ -317,84 +347,132 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_inv(int N, c128* __restri
     }
     __syncthreads();
     const double inv = 1.0 / s_piv;
-    for (int i = j + 1 + threadIdx.x; i < N; i += blockDim.x) {
-      double sr = A[(long long)j * N + i].re, si = A[(long long)j * N + i].im;
-      for (int k = 0; k < j; ++k) {
-        c128 u = A[(long long)k * N + i];
-        c128 c = col[k];  // U[k][j]; subtract conj(c) * u
-        sr -= c.re * u.re + c.im * u.im;
-        si -= c.re * u.im - c.im * u.re;
+    const int R = N - j - 1;                    // rows i = j + 1 .. N - 1
+    const int P = chol_parts(R, j, bd);
+    if (P == 1) {
+      for (int i = j + 1 + t; i < N; i += bd) {
+        double sr = 0, si = 0;
+        for (int k = 0; k < j; ++k) {
+          const c128 u = A[(long long)k * N + i], c = col[k];
+          chol_cmac_conj(c, u, sr, si);
+        }
+        const c128 a = A[(long long)j * N + i];
+        A[(long long)j * N + i] = c128{(a.re - sr) * inv, (a.im - si) * inv};
       }
-      A[(long long)j * N + i] = c128{sr * inv, si * inv};
+    } else {
+      double sr = 0, si = 0;
+      if (t < R * P) {
+        const int i = j + 1 + t % R;
+        for (int k = t / R; k < j; k += P) {
+          const c128 u = A[(long long)k * N + i], c = col[k];
+          chol_cmac_conj(c, u, sr, si);
+        }
+        part[t] = c128{sr, si};
+      }
+      __syncthreads();
+      if (t < R) {
+        for (int p = 1; p < P; ++p) {
+          sr += part[p * R + t].re;
+          si += part[p * R + t].im;
+        }
+        const int i = j + 1 + t;
+        const c128 a = A[(long long)j * N + i];
+        A[(long long)j * N + i] = c128{(a.re - sr) * inv, (a.im - si) * inv};
+      }
     }
     __syncthreads();
   }
   // 2) W = U^{-1} (upper), rows from the bottom:
   //    W[i][i] = 1/U[i][i];  W[i][l] = -(1/U[i][i]) sum_{k=i+1}^{l} U[i][k] W[k][l]
-  for (int e = threadIdx.x; e < N * N; e += blockDim.x) W[e] = c128{0.0, 0.0};
+  for (long long e = t; e < (long long)N * N; e += bd) W[e] = c128{0.0, 0.0};
   __syncthreads();
   for (int i = N - 1; i >= 0; --i) {
-    for (int k = i + threadIdx.x; k < N; k += blockDim.x) col[k] = A[(long long)i * N + k];
+    for (int k = i + t; k < N; k += bd) col[k] = A[(long long)i * N + k];
     __syncthreads();
     const double dinv = 1.0 / col[i].re;
-    for (int l = i + threadIdx.x; l < N; l += blockDim.x) {
-      if (l == i) {
-        W[(long long)i * N + i] = c128{dinv, 0.0};
-      } else {
+    const int R = N - i;                        // columns l = i .. N - 1
+    const int P = chol_parts(R, R - 1, bd);
+    if (P == 1) {
+      for (int l = i + t; l < N; l += bd) {
         double sr = 0, si = 0;
         for (int k = i + 1; k <= l; ++k) {
-          c128 u = col[k], w = W[(long long)k * N + l];
-          sr += u.re * w.re - u.im * w.im;
-          si += u.re * w.im + u.im * w.re;
+          const c128 u = col[k], w = W[(long long)k * N + l];
+          chol_cmac(u, w, sr, si);
         }
-        W[(long long)i * N + l] = c128{-sr * dinv, -si * dinv};
+        W[(long long)i * N + l] = (l == i) ? c128{dinv, 0.0} : c128{-sr * dinv, -si * dinv};
+      }
+    } else {
+      double sr = 0, si = 0;
+      if (t < R * P) {
+        const int l = i + t % R;
+        for (int k = i + 1 + t / R; k <= l; k += P) {
+          const c128 u = col[k], w = W[(long long)k * N + l];
+          chol_cmac(u, w, sr, si);
+        }
+        part[t] = c128{sr, si};
+      }
+      __syncthreads();
+      if (t < R) {
+        for (int p = 1; p < P; ++p) {
+          sr += part[p * R + t].re;
+          si += part[p * R + t].im;
+        }
+        const int l = i + t;
+        W[(long long)i * N + l] = (l == i) ? c128{dinv, 0.0} : c128{-sr * dinv, -si * dinv};
       }
     }
     __syncthreads();
   }
-  // 3) A = W W^H - I: A[i][l] = sum_{k >= max(i,l)} W[i][k] conj(W[l][k]); lower tiles, mirrored
-  const int TT = 16;
-  __shared__ c128 Ti[16][17], Tl[16][17];
-  const int nt = (N + TT - 1) / TT;
+  // 3) A = W W^H - I: A[i][l] = sum_{k >= max(i,l)} W[i][k] conj(W[l][k]) over lower tiles (ti >= tl);
+  //    W[i][k] = 0 for k < i, so K starts at the tile row ti. Each thread owns the outputs
+  //    (orow, oc) and (orow + 16, oc) of the tile.
+  c128(*Ti)[CHOL_TP] = reinterpret_cast<c128(*)[CHOL_TP]>(dyn);
+  c128(*Tl)[CHOL_TP] = reinterpret_cast<c128(*)[CHOL_TP]>(dyn + CHOL_T * CHOL_TP);
+  const int nt = (N + CHOL_T - 1) / CHOL_T;
+  const int oc = t % CHOL_T, orow = t / CHOL_T;   // orow < 16 with 512 threads
   for (int ti = 0; ti < nt; ++ti) {
     for (int tl = 0; tl <= ti; ++tl) {
-      // 512 threads: 256 outputs, two k-halves
-      const int o = threadIdx.x % 256, half = threadIdx.x / 256;
-      const int ii = ti * TT + o / TT, ll = tl * TT + o % TT;
-      double sr = 0, si = 0;
-      for (int k0 = ti * TT; k0 < N; k0 += TT) {
-        for (int e = threadIdx.x; e < 2 * TT * TT; e += blockDim.x) {
-          int which = e / (TT * TT), r = (e % (TT * TT)) / TT, c = e % TT;
-          int row = (which == 0 ? ti : tl) * TT + r, kk = k0 + c;
-          c128 v = (row < N && kk < N) ? W[(long long)row * N + kk] : c128{0.0, 0.0};
+      double s0r = 0, s0i = 0, s1r = 0, s1i = 0;
+      for (int k0 = ti * CHOL_T; k0 < N; k0 += CHOL_T) {
+        for (int e = t; e < 2 * CHOL_T * CHOL_T; e += bd) {
+          const int which = e / (CHOL_T * CHOL_T), r = (e % (CHOL_T * CHOL_T)) / CHOL_T, c = e % CHOL_T;
+          const int row = (which == 0 ? ti : tl) * CHOL_T + r, kk = k0 + c;
+          const c128 v = (row < N && kk < N) ? W[(long long)row * N + kk] : c128{0.0, 0.0};
           if (which == 0) Ti[r][c] = v; else Tl[r][c] = v;
         }
         __syncthreads();
-        for (int c = half; c < TT; c += 2) {
-          c128 a = Ti[o / TT][c], b = Tl[o % TT][c];
-          sr += a.re * b.re + a.im * b.im;
-          si += a.im * b.re - a.re * b.im;
+        if (orow < CHOL_T / 2) {
+#pragma unroll 8
+          for (int c = 0; c < CHOL_T; ++c) {
+            const c128 b = Tl[oc][c], a0 = Ti[orow][c], a1 = Ti[orow + CHOL_T / 2][c];
+            chol_cmac_conj(b, a0, s0r, s0i);      // a0 conj(b)
+            chol_cmac_conj(b, a1, s1r, s1i);
+          }
         }
         __syncthreads();
       }
-      // combine the two halves through shared memory
-      __shared__ double part_re[256], part_im[256];
-      if (half == 1) { part_re[o] = sr; part_im[o] = si; }
-      __syncthreads();
-      if (half == 0 && ii < N && ll < N && ii >= ll) {
-        sr += part_re[o];
-        si += part_im[o];
-        if (ii == ll) { sr -= 1.0; si = 0.0; }
-        A[(long long)ii * N + ll] = c128{sr, si};
-        if (ii != ll) A[(long long)ll * N + ii] = c128{sr, -si};
+      if (orow < CHOL_T / 2) {
+        const int ll = tl * CHOL_T + oc;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int ii = ti * CHOL_T + orow + h * (CHOL_T / 2);
+          double sr = h ? s1r : s0r, si = h ? s1i : s0i;
+          if (ii < N && ll < N && ii >= ll) {
+            if (ii == ll) {
+              sr -= 1.0;
+              si = 0.0;
+            }
+            A[(long long)ii * N + ll] = c128{sr, si};
+            if (ii != ll) A[(long long)ll * N + ii] = c128{sr, -si};
+          }
+        }
       }
-      __syncthreads();
     }
   }
 }
 
 void launch_chol_inv_minus_I(int N, c128* A, int batch, long long stride, c128* work, int* status, cudaStream_t st) {
-  size_t smem = sizeof(c128) * (size_t)N;
+  const size_t smem = chol_smem_bytes(N);
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   ++::gw::g_launch_count, k_chol_inv<<<batch, CHOL_THREADS, smem, st>>>(N, A, stride, work, status);
 }
