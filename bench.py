@@ -30,7 +30,7 @@ METRIC = "G0W0 Σc time-to-solution & χ0 TFLOP/s: split-prec vs FP64 on 1 GB300
 # ncu capture of the cfg1 shape on a 4x4x4 k mesh (q = 1, 3xBF16; the k_tc capture under profiles/).
 # The reads stream the operand planes of every k and grow with the k count; the writes are the
 # compressed output rows, independent of it.
-CHI0_DRAM_CAPTURE = None   # no capture of the current chi0 kernel yet: traffic is reported as null
+CHI0_DRAM_CAPTURE = dict(prec="3xbf16", n_k=64, n_aux=400, read=436.279552e6, write=25.975808e6)
 WORKLOADS = {
     "cfg0": "tiny synthetic insulator: 2x2x2 k, 2 atoms, 32 NAO, 32 bands (4 occ), 96 ABF, 16 imaginary frequencies",
     "cfg1": "Si-like 2-atom fcc cell: 6x6x6 k (216 k, 216 q), 78 NAO, 78 bands (4 occ), 400 ABF, 32 imaginary "
