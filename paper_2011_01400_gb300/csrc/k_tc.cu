@@ -37,9 +37,12 @@
 // Roles (480 threads):
 //   * warp 0 (TMA):   B1 / B2 pieces, 64 rows x 128 B each per stage, SWIZZLE_128B
 //   * warp 14 (TMA):  A rows of the fp32 plane, 128 rows x 128 B per slot, into a ring that runs
-//                     ahead of the transform
-//   * warps 2-5:      transform: rebuild y = w x from the ring, split, write the A pieces in the
-//                     UMMA K-major 128B-swizzled layout
+//                     ahead of the transform, each slot with its 16 weights (bulk copy);
+//                     PRE: the pre-split A pieces into the stages, and after each item's stages
+//                     the item's fp32 a tile (128 rows x BN complex) into the idle ring for the
+//                     epilogue's row dot
+//   * warps 2-5:      transform (not PRE): rebuild y = w x from the ring, split, write the A
+//                     pieces in the UMMA K-major 128B-swizzled layout
 //   * warp 1:         one elected thread issues tcgen05.mma (M = 128, N = 128) into TMEM
 //   * warps 6-13:     epilogue (two warps per TMEM lane quadrant, 32 complex columns each)
 // All mbarrier waits are bounded; on expiry the kernel sets ST_TIMEOUT and unwinds.
