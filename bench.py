@@ -325,7 +325,7 @@ def surrogate_bench(args, gw, torch):
                 loss_last=float(hist[-1]) if len(hist) else None,
                 surrogate_step_s=t_sur, full_grid_step_s=t_full, speedup=t_full / t_sur,
                 max_abs_dE_qp_meV=float(abs(e_s - e_f).max() * ha), abs_dgap_meV=float(abs(gap_s - gap_f) * ha),
-                judge="the plain method on the full 60-point grid, same precision, same system")
+                error_reference="the plain method on the full 60-point grid, same precision, same system")
 
 
 def batch_systems(n, seed0=30000):

@@ -44,7 +44,7 @@ typedef enum {
   GW_ERR_NOT_PD = 4,     /* eps~ had a non-positive Cholesky pivot (chi0 not NSD)    */
   GW_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up (pipeline stalled)     */
   GW_ERR_STATE = 6,      /* call out of order (e.g. gw_screen before gw_chi0 for q)  */
-  GW_ERR_UNSUPPORTED = 7 /* valid request this build does not implement                */
+  GW_ERR_UNSUPPORTED = 7 /* valid request that the library does not implement          */
 } gw_status;
 
 typedef enum {

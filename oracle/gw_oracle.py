@@ -9,7 +9,7 @@ arrays.
 Every function states the passage of the paper it follows. Steps are taken in
 the paper's order with library primitives (matmul, eigh, inv, leggauss) and no
 blocking or reordering. Readings of passages that are silent, ambiguous or
-garbled are marked "reading:" and collected in the design doc.
+garbled are marked "reading:" in the docstring that uses them.
 
 Notation (Sec. II): k, q on a Gamma-centred mesh, w_k = 1/N_k; bands m, n;
 NAOs i, j; ABFs mu, nu; s = spin factor (2, doubly occupied bands).

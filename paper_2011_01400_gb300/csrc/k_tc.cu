@@ -24,7 +24,7 @@
 //   * hh goes to accumulator D1, which is drained after every stage (4 MMAs per output)
 //     into FP32 running sums held in registers by the epilogue warps (round to nearest);
 //     MODE 1 sums only K = n_aux (at most 52 MMAs per item), so there D1 is drained once per
-//     segment like D2 (the truncation bias stays ~1e-6 relative of S, far inside the budget);
+//     segment like D2 (the truncation bias stays ~1e-6 relative of S, far inside the Sigma_c tolerance);
 //   * the correction products (2^-8 smaller) go to D2, drained once per segment;
 //   * after each segment the running sums are added in FP64 into the output (MODE 0), or
 //     dotted with a and added to S (MODE 1, one segment per work item).
