@@ -2,10 +2,13 @@
 #include "gw_internal.h"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -154,6 +157,56 @@ struct SurState {
   float *d_d = nullptr, *d_x = nullptr, *d_sig = nullptr, *d_g = nullptr, *d_coef = nullptr;
 };
 
+// Autotuner of the fp32 shared-memory M kernels. Per device and call shape (kernel, na, nb) both
+// thread mappings are run at first use on the calling plan's stream -- one warm-up launch, then one
+// timed launch each (CUDA events) -- and the faster one is recorded process-wide for every later
+// call of that shape. The two mappings write bit-identical rows, so the repeated launches only cost
+// time; results never depend on the choice.
+struct MgenTuner {
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  static std::map<std::array<int, 4>, int>& table() {
+    static std::map<std::array<int, 4>, int> t;
+    return t;
+  }
+  static std::mutex& table_mutex() {
+    static std::mutex m;
+    return m;
+  }
+  ~MgenTuner() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+  // launch(variant) issues the kernel on st; returns false on a CUDA error
+  template <typename F> bool run(int kind, int na, int nb, cudaStream_t st, F&& launch) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const std::array<int, 4> key{dev, kind, na, nb};
+    {
+      std::lock_guard<std::mutex> lk(table_mutex());
+      auto it = table().find(key);
+      if (it != table().end()) {
+        const int v = it->second;
+        launch(v);
+        return true;
+      }
+    }
+    for (cudaEvent_t& e : ev)
+      if (!e && cudaEventCreate(&e) != cudaSuccess) return false;
+    launch(0);
+    if (cudaEventRecord(ev[0], st) != cudaSuccess) return false;
+    launch(0);
+    if (cudaEventRecord(ev[1], st) != cudaSuccess) return false;
+    launch(1);
+    if (cudaEventRecord(ev[2], st) != cudaSuccess || cudaEventSynchronize(ev[2]) != cudaSuccess) return false;
+    float t0 = 0.f, t1 = 0.f;
+    if (cudaEventElapsedTime(&t0, ev[0], ev[1]) != cudaSuccess || cudaEventElapsedTime(&t1, ev[1], ev[2]) != cudaSuccess)
+      return false;
+    std::lock_guard<std::mutex> lk(table_mutex());
+    table()[key] = (t1 < t0) ? 1 : 0;
+    return true;
+  }
+};
+
 struct gw_plan_s {
   gw_problem p{};
   gw_precision prec;
@@ -225,6 +278,7 @@ struct gw_plan_s {
   c128 *g_chi0 = nullptr, *g_E = nullptr, *g_work = nullptr;
   int qb = 0;
   double group_budget = 8.0e9;  // bytes for the q-group buffers of gw_g0w0
+  MgenTuner mtune;              // picks the thread mapping of the fp32 M kernels per call shape
   SurState sur;
   // batch plan (n_sys > 1): one plan per system, each on its own stream; the batch plan itself
   // holds no device memory
@@ -891,8 +945,11 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
                                     pad * esz, N, st));
         GW_CUDA(cudaMemsetAsync(P->d_delta_f + K, 0, sizeof(float) * (P->ldm - K), st));
       }
-      launch_mgen_planes(P->geom, static_cast<const c64*>(P->d_T1), evec, q, kk0, nkk, P->nocc, na, 0, nb,
-                         P->d_Praw, P->d_Pb, 2 * P->ldm, 0, tf32, st);
+      if (!P->mtune.run(1, na, nb, st, [&](int v) {
+            launch_mgen_planes(P->geom, static_cast<const c64*>(P->d_T1), evec, q, kk0, nkk, P->nocc, na, 0, nb,
+                               P->d_Praw, P->d_Pb, 2 * P->ldm, 0, tf32, st, v);
+          }))
+        return fail(GW_ERR_CUDA, "M kernel autotuner: CUDA error");
       TcChi0Args a{};
       a.N = N;
       a.Kpad = (int)P->ldm;
@@ -923,8 +980,11 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
       GW_CUDA(cudaEventRecord(e1, st));
       if (hw) {
         c64* M = static_cast<c64*>(P->d_M);
-        launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK,
-                           P->nocc, na, 0, nb, M, 1, P->ldm, st);
+        if (!P->mtune.run(0, na, nb, st, [&](int v) {
+              launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK,
+                                 P->nocc, na, 0, nb, M, 1, P->ldm, st, v);
+            }))
+          return fail(GW_ERR_CUDA, "M kernel autotuner: CUDA error");
         launch_head_wings<float>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
                                  4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
       }
@@ -1019,8 +1079,11 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig) {
     } else {
       // rows a_r as an fp32 plane [R][Kx] (zero beyond n_aux), then the tensor-core contraction
       c64* A = static_cast<c64*>(P->d_A);
-      launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK_MINUS_Q,
-                         P->p.sigma_lo, nsig, 0, NBd, A, P->Kx, 1, st);
+      if (!P->mtune.run(0, nsig, NBd, st, [&](int v) {
+            launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk,
+                               MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, P->Kx, 1, st, v);
+          }))
+        return fail(GW_ERR_CUDA, "M kernel autotuner: CUDA error");
       GW_CUDA(cudaMemsetAsync(P->d_S_f, 0, sizeof(float) * (size_t)R * nw, st));
       TcSigmaArgs a{};
       a.R = R;
@@ -1429,8 +1492,11 @@ gw_status sigma_core_sur(gw_plan_s* P, int q, const c128* Wc_c, const c128* U, c
       launch_sur_assemble<double>(R, nc, nw, k, S.d_jmap, S.d_Sc_d, Pm, coef, nf, Lmat, P->d_S_d, st);
     } else {
       c64* A = static_cast<c64*>(P->d_A);
-      launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK_MINUS_Q,
-                         P->p.sigma_lo, nsig, 0, NBd, A, P->Kx, 1, st);
+      if (!P->mtune.run(0, nsig, NBd, st, [&](int v) {
+            launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk,
+                               MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, P->Kx, 1, st, v);
+          }))
+        return fail(GW_ERR_CUDA, "M kernel autotuner: CUDA error");
       GW_CUDA(cudaMemsetAsync(S.d_Sc, 0, sizeof(float) * (size_t)R * nc, st));
       TcSigmaArgs a{};
       a.R = R;
@@ -1776,8 +1842,11 @@ gw_status gw_sigma_x(gw_plan P, int32_t sys, double* sigx) {
         launch_rowdot<double>(R, N, U, A, N, nullptr, P->d_Sx, 0, 1, st);
       } else {
         c64* A = static_cast<c64*>(P->d_A);
-        launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk, MAP_K_IS_KK_MINUS_Q,
-                           P->p.sigma_lo, nsig, 0, nocc, A, P->Kx, 1, st);
+        if (!P->mtune.run(0, nsig, nocc, st, [&](int v) {
+              launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk,
+                                 MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, nocc, A, P->Kx, 1, st, v);
+            }))
+          return fail(GW_ERR_CUDA, "M kernel autotuner: CUDA error");
         launch_zgemm<float>(R, N, N, c64{1, 0}, A, P->Kx, 0, OP_N, P->d_Vx32, N, 0, OP_N, c64{0, 0}, P->d_Ux, P->Kx,
                             0, 1, st);
         launch_rowdot<float>(R, N, P->d_Ux, A, P->Kx, nullptr, P->d_Sx, 0, 1, st);

@@ -65,16 +65,18 @@ void launch_lri_halfT(const LriGeom& g, const double* ctil, const c128* evec, cp
 // M^mu_{ab}(k', q) for a in [a0, a0+na) at k'+q and b in [b0, b0+nb) at k', for the k' of each row block.
 // Row index r = ((kk * na) + a) * nb + b for kk in [0, nkk); k' = kmap(kk) (see MapMode).
 // out element (r, mu) at out[r * s_r + mu * s_mu].
+// variant (fp32 shared-memory kernels): thread mapping, 0 = one output per thread, 1 = one (a, b)
+// pair per thread over the tile's ABFs; both give bit-identical rows (picked by MgenTuner).
 enum MapMode { MAP_K_IS_KK = 0, MAP_K_IS_KK_MINUS_Q = 1 };
 template <typename T>
 void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* T2, const c128* evec, int q,
                  int kk0, int nkk, MapMode mode, int a0, int na, int b0, int nb, cplx<T>* out, long long s_r,
-                 long long s_mu, cudaStream_t st);
+                 long long s_mu, cudaStream_t st, int variant = 0);
 // split planes for the tensor-core chi0 B operand: for row mu, K index 2r + {0: re, 1: im}
 // raw fp32 plane + B1/B2 split planes (3 BF16 pieces or 2 TF32 pieces each), see k_lri.cu
 void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
                         int b0, int nb, float* raw, void* const* bplanes, long long ldk, long long kofs, int tf32,
-                        cudaStream_t st);
+                        cudaStream_t st, int variant = 0);
 
 // k_linalg.cu
 template <typename T>

@@ -200,7 +200,12 @@ __device__ __forceinline__ void mgen_body(const LriGeom& g, const cplx<T>* __res
 // i.e. a complex product of K = 2 n_b(A) per ABF. The block (512 threads: one block of ~130 KB
 // fits an SM, so the width buys the latency hiding) stages cK, cQ and the T1 slices of its ABFs
 // in shared memory (fp32) once; threads run over (mu, a, b) outputs with the K loop in shared memory. Tiles never straddle atoms (tile t -> atom by the cumulative tile counts).
+// Two thread mappings, picked per call shape by the plan's autotuner (both give bit-identical rows):
+//   PAIR = false: one output (m, a, b) per thread, 512 threads;
+//   PAIR = true:  one (a, b) pair per thread for all MGT ABFs of the tile (cK, cQ loaded once per
+//                 j for MGT outputs), as many threads as pairs up to MGEN_SMEM_THREADS.
 constexpr int MGT = 4;
+constexpr int MGEN_SMEM_THREADS = 640;
 
 __device__ __forceinline__ bool mgen_tile(const LriGeom& g, int t, int& A, int& mu0, int& cnt) {
   for (A = 0; A < g.n_atoms; ++A) {
@@ -215,7 +220,7 @@ __device__ __forceinline__ bool mgen_tile(const LriGeom& g, int t, int& A, int& 
   return false;
 }
 
-template <typename Store>
+template <bool PAIR, typename Store>
 __device__ __forceinline__ void mgen_smem_body(const LriGeom& g, const c64* __restrict__ T1,
                                                const c128* __restrict__ evec, int q, int kk0, int mode, int a0, int na,
                                                int b0, int nb, Store store) {
@@ -263,20 +268,45 @@ __device__ __forceinline__ void mgen_smem_body(const LriGeom& g, const c64* __re
   }
   __syncthreads();
   const int npair = na * nb;
-  for (int idx = threadIdx.x; idx < cnt * npair; idx += blockDim.x) {
-    const int m = idx / npair, pr = idx % npair, a = pr / nb, b = pr % nb;
-    const float2* tqm = tq + m * nbA * na;
-    const float2* tkm = tk + m * nbA * nb;
-    float sr = 0.f, si = 0.f;
-    for (int j = 0; j < nbA; ++j) {
-      const float2 c = cK[j * nb + b], t = tqm[j * na + a];     // c conj(t)
-      sr = fmaf(c.x, t.x, fmaf(c.y, t.y, sr));
-      si = fmaf(c.y, t.x, fmaf(-c.x, t.y, si));
-      const float2 d = cQ[j * na + a], u = tkm[j * nb + b];     // conj(d) u
-      sr = fmaf(d.x, u.x, fmaf(d.y, u.y, sr));
-      si = fmaf(d.x, u.y, fmaf(-d.y, u.x, si));
+  if constexpr (PAIR) {
+    for (int pr = threadIdx.x; pr < npair; pr += blockDim.x) {
+      const int a = pr / nb, b = pr % nb;
+      float sr[MGT], si[MGT];
+#pragma unroll
+      for (int m = 0; m < MGT; ++m) sr[m] = si[m] = 0.f;
+      for (int j = 0; j < nbA; ++j) {
+        const float2 c = cK[j * nb + b], d = cQ[j * na + a];
+#pragma unroll
+        for (int m = 0; m < MGT; ++m) {
+          if (m < cnt) {
+            const float2 t = tq[(m * nbA + j) * na + a], u = tk[(m * nbA + j) * nb + b];
+            sr[m] = fmaf(c.x, t.x, fmaf(c.y, t.y, sr[m]));     // c conj(t)
+            si[m] = fmaf(c.y, t.x, fmaf(-c.x, t.y, si[m]));
+            sr[m] = fmaf(d.x, u.x, fmaf(d.y, u.y, sr[m]));     // conj(d) u
+            si[m] = fmaf(d.x, u.y, fmaf(-d.y, u.x, si[m]));
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < MGT; ++m)
+        if (m < cnt) store(((long long)kk * na + a) * nb + b, mu0 + m, sr[m], si[m]);
     }
-    store(((long long)kk * na + a) * nb + b, mu0 + m, sr, si);
+  } else {
+    for (int idx = threadIdx.x; idx < cnt * npair; idx += blockDim.x) {
+      const int m = idx / npair, pr = idx % npair, a = pr / nb, b = pr % nb;
+      const float2* tqm = tq + m * nbA * na;
+      const float2* tkm = tk + m * nbA * nb;
+      float sr = 0.f, si = 0.f;
+      for (int j = 0; j < nbA; ++j) {
+        const float2 c = cK[j * nb + b], t = tqm[j * na + a];     // c conj(t)
+        sr = fmaf(c.x, t.x, fmaf(c.y, t.y, sr));
+        si = fmaf(c.y, t.x, fmaf(-c.x, t.y, si));
+        const float2 d = cQ[j * na + a], u = tkm[j * nb + b];     // conj(d) u
+        sr = fmaf(d.x, u.x, fmaf(d.y, u.y, sr));
+        si = fmaf(d.x, u.y, fmaf(-d.y, u.x, si));
+      }
+      store(((long long)kk * na + a) * nb + b, mu0 + m, sr, si);
+    }
   }
 }
 
@@ -286,15 +316,23 @@ int mgen_tiles(const LriGeom& g) {
   return t;
 }
 
+// threads per block of the shared-memory M kernels
+int mgen_threads(bool pair, int na, int nb) {
+  if (!pair) return 512;
+  const int n = ((na * nb + 31) / 32) * 32;
+  return std::max(64, std::min(MGEN_SMEM_THREADS, n));
+}
+
 size_t mgen_smem(const LriGeom& g, int na, int nb) {
   int nbA = 0;
   for (int A = 0; A < g.n_atoms; ++A) nbA = std::max(nbA, g.atom_nb[A]);
   return sizeof(float2) * (size_t)nbA * (na + nb) * (1 + MGT);
 }
 
-__global__ void k_mgen_smem(const __grid_constant__ LriGeom g, const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int mode, int a0,
+template <bool PAIR>
+__global__ void __launch_bounds__(MGEN_SMEM_THREADS) k_mgen_smem(const __grid_constant__ LriGeom g, const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int mode, int a0,
                             int na, int b0, int nb, c64* __restrict__ out, long long s_r, long long s_mu) {
-  mgen_smem_body(g, T1, evec, q, kk0, mode, a0, na, b0, nb, [&](long long r, int mu, float re, float im) {
+  mgen_smem_body<PAIR>(g, T1, evec, q, kk0, mode, a0, na, b0, nb, [&](long long r, int mu, float re, float im) {
     out[r * s_r + (long long)mu * s_mu] = c64{re, im};
   });
 }
@@ -310,18 +348,18 @@ __global__ void k_mgen(const __grid_constant__ LriGeom g, const cplx<T>* __restr
 template <typename T>
 void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* /*T2*/, const c128* evec, int q, int kk0,
                  int nkk, MapMode mode, int a0, int na, int b0, int nb, cplx<T>* out, long long s_r, long long s_mu,
-                 cudaStream_t st) {
+                 cudaStream_t st, int /*variant*/) {
   dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
   ++::gw::g_launch_count, k_mgen<T><<<grid, 256, 0, st>>>(g, T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r, s_mu);
 }
 template void launch_mgen<double>(const LriGeom&, const c128*, const c128*, const c128*, int, int, int, MapMode, int,
-                                  int, int, int, c128*, long long, long long, cudaStream_t);
+                                  int, int, int, c128*, long long, long long, cudaStream_t, int);
 
 // fp32: the shared-memory kernel when its staging fits, else the plain one
 template <>
 void launch_mgen<float>(const LriGeom& g, const c64* T1, const c64* T2, const c128* evec, int q, int kk0, int nkk,
                         MapMode mode, int a0, int na, int b0, int nb, c64* out, long long s_r, long long s_mu,
-                        cudaStream_t st) {
+                        cudaStream_t st, int variant) {
   const size_t sm = mgen_smem(g, na, nb);
   if (sm > 200 * 1024) {
     dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
@@ -330,10 +368,17 @@ void launch_mgen<float>(const LriGeom& g, const c64* T1, const c64* T2, const c1
     return;
   }
   (void)T2;
-  cudaFuncSetAttribute(k_mgen_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   dim3 grid(nkk, mgen_tiles(g));
-  ++::gw::g_launch_count, k_mgen_smem<<<grid, 512, sm, st>>>(g, T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out, s_r,
-                                                            s_mu);
+  const int nt = mgen_threads(variant != 0, na, nb);
+  if (variant) {
+    cudaFuncSetAttribute(k_mgen_smem<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    ++::gw::g_launch_count, k_mgen_smem<true><<<grid, nt, sm, st>>>(g, T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out,
+                                                                    s_r, s_mu);
+  } else {
+    cudaFuncSetAttribute(k_mgen_smem<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    ++::gw::g_launch_count, k_mgen_smem<false><<<grid, nt, sm, st>>>(g, T1, evec, q, kk0, (int)mode, a0, na, b0, nb, out,
+                                                                     s_r, s_mu);
+  }
 }
 
 // Operand planes for the tensor-core chi0 (row mu, K index kofs + 2r + {0, 1}):
@@ -355,8 +400,8 @@ struct PlanePtrs {
   void* b[6];      // B1 pieces then B2 pieces
 };
 
-template <bool SMEM>
-__global__ void k_mgen_planes(const __grid_constant__ LriGeom g, const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int a0,
+template <bool SMEM, bool PAIR>
+__global__ void __launch_bounds__(MGEN_SMEM_THREADS) k_mgen_planes(const __grid_constant__ LriGeom g, const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int a0,
                               int na, int b0, int nb, PlanePtrs P, long long ldk, long long kofs, int tf32) {
   auto st = [&](long long r, int mu, float re, float im) {
     const long long e = (long long)mu * ldk + kofs + 2 * r;
@@ -386,27 +431,34 @@ __global__ void k_mgen_planes(const __grid_constant__ LriGeom g, const c64* __re
     }
   };
   if constexpr (SMEM)
-    mgen_smem_body(g, T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
+    mgen_smem_body<PAIR>(g, T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
   else
     mgen_body<float>(g, T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
 }
 
 void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
                         int b0, int nb, float* raw, void* const* bplanes, long long ldk, long long kofs, int tf32,
-                        cudaStream_t st) {
+                        cudaStream_t st, int variant) {
   PlanePtrs P{};
   P.raw = raw;
   for (int i = 0; i < (tf32 ? 4 : 6); ++i) P.b[i] = bplanes[i];
   const size_t sm = mgen_smem(g, na, nb);
   if (sm <= 200 * 1024) {
-    cudaFuncSetAttribute(k_mgen_planes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     dim3 grid(nkk, mgen_tiles(g));
-    ++::gw::g_launch_count, k_mgen_planes<true><<<grid, 512, sm, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
-                                                                       tf32);
+    const int nt = mgen_threads(variant != 0, na, nb);
+    if (variant) {
+      cudaFuncSetAttribute(k_mgen_planes<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      ++::gw::g_launch_count, k_mgen_planes<true, true><<<grid, nt, sm, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, P, ldk,
+                                                                              kofs, tf32);
+    } else {
+      cudaFuncSetAttribute(k_mgen_planes<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      ++::gw::g_launch_count, k_mgen_planes<true, false><<<grid, nt, sm, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, P, ldk,
+                                                                               kofs, tf32);
+    }
   } else {
     dim3 grid(nkk, (g.N + MGEN_MU - 1) / MGEN_MU);
-    ++::gw::g_launch_count, k_mgen_planes<false><<<grid, 256, 0, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, P, ldk, kofs,
-                                                                        tf32);
+    ++::gw::g_launch_count, k_mgen_planes<false, false><<<grid, 256, 0, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, P, ldk,
+                                                                               kofs, tf32);
   }
 }
 
