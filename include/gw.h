@@ -26,6 +26,11 @@
  *     gw_last_error() returns a text for the last failure of this thread.
  *   - Matrices are row-major. Hermitian outputs are written in full.
  *   - No call uses more than the one current CUDA device.
+ *   - Autotuning: the first split-precision call that generates band-pair rows
+ *     of a given shape in this process times two thread mappings of that kernel
+ *     (one warm-up and one timed launch each). It then waits for the plan's stream
+ *     once, to read the timings. Both mappings write identical rows, so the
+ *     results never depend on the choice, and later calls of that shape do not wait.
  */
 #ifndef GW_H
 #define GW_H
