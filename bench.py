@@ -166,6 +166,31 @@ def oracle_sample(system, seconds_hint=20.0):
                 slice_seconds=t_chi + t_scr + t_sig)
 
 
+def max_over_ranks(vals, world, device="cpu"):
+    """Each value's maximum over the ranks of the process group (any backend: NCCL with
+    device="cuda", gloo with "cpu"); the values themselves for a single process."""
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64)
+    if world > 1:
+        import torch.distributed as dist
+        t = t.to(device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t = t.cpu()
+    return [float(x) for x in t]
+
+
+def seconds_per_system(ms_per_step_max, world):
+    """Whole-job value: every rank processes one system per step, so the job finishes `world`
+    systems in the slowest rank's step time."""
+    return ms_per_step_max / 1e3 / world
+
+
+def replica_seed(config, rank):
+    """Seed of the system a rank processes: the configuration's seed, offset by the rank, so the
+    replicas of a multi-GPU run work on different systems."""
+    return 1000 * int(config[-1]) + rank
+
+
 def run_reference(args, system, world, rank):
     if rank != 0:
         return
@@ -458,12 +483,7 @@ def run_device(args, system, world, rank):
                     speedup_q=q64 / qsp,
                     fp64_step_s_extrapolated=(p64 + s.n_k * q64) / 1e3,
                     speedup_step_extrapolated=(p64 + s.n_k * q64) / ms)
-    t = torch.tensor([ms, ms_e2e], dtype=torch.float64)
-    if world > 1:
-        t = t.cuda()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t = t.cpu()
-    ms, ms_e2e = float(t[0]), float(t[1])
+    ms, ms_e2e = max_over_ranks([ms, ms_e2e], world, "cuda")
     if rank != 0:
         return
     fl = algorithmic_flops(s)
@@ -486,7 +506,7 @@ def run_device(args, system, world, rank):
         traffic = cap["read"] * s.n_k / cap["n_k"] + cap["write"]
     line = dict(
         metric=METRIC,
-        value=ms / 1e3 / world,
+        value=seconds_per_system(ms, world),
         unit="s",
         n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
         higher_is_better=False, scaling="weak", vs_baseline=None,
@@ -556,7 +576,7 @@ def main():
     over = {}
     if args.nk:
         over["nk"] = tuple(int(x) for x in args.nk.split(","))
-    system = make_system(args.config, seed=1000 * int(args.config[-1]) + rank, **over)
+    system = make_system(args.config, seed=replica_seed(args.config, rank), **over)
     if args.impl == "reference":
         run_reference(args, system, world, rank)
     else:
