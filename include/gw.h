@@ -26,6 +26,11 @@
  *     gw_last_error() returns a text for the last failure of this thread.
  *   - Matrices are row-major. Hermitian outputs are written in full.
  *   - No call uses more than the one current CUDA device.
+ *   - Environment (read at gw_plan_create, split precision only):
+ *     GW_CHI0_SEG_ROWS      pair rows per FP64 promotion segment of the tensor-core
+ *                           chi0 (default 2048; at least 32);
+ *     GW_CHI0_COMPRESS_TOL  per-frequency residual bound of the chi0 weight-matrix
+ *                           compression (default 3e-8; 0 keeps all frequencies).
  *   - Autotuning: the first split-precision call that generates band-pair rows
  *     of a given shape in this process times two thread mappings of that kernel
  *     (one warm-up and one timed launch each). It then waits for the plan's stream
