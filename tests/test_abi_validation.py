@@ -1,4 +1,4 @@
-"""gw_plan_create rejects every malformed problem with GW_ERR_ARG before touching the GPU.
+"""gw_plan_create and the surrogate calls reject malformed arguments with GW_ERR_ARG before touching the GPU.
 
 Each case breaks one field of a problem that is otherwise valid up to its last check, and the
 base problem also carries a decreasing aux_atom (the last check), so that no case can ever reach
@@ -108,3 +108,23 @@ def test_batch_count_is_checked(lib):
     assert lib.gw_plan_create(ctypes.byref(p), 0, None, ctypes.byref(h)) == gw.GW_ERR_ARG
     assert lib.gw_plan_create(ctypes.byref(p), 5000, None, ctypes.byref(h)) == gw.GW_ERR_ARG
     assert "n_sys out of range" in lib.gw_last_error().decode()
+
+
+@pytest.mark.parametrize("dims", [(12, 256, 48), (5, 40, 7), (1, 1, 1), (64, 4096, 1024)])
+def test_surrogate_parameter_count_matches_the_layout(lib, dims):
+    """The flat parameter vector of the network (W1 b1 W2 b2 W3 b3 W4 b4, then L and s) has the
+    length the oracle's layout gives; the count needs no GPU."""
+    from oracle import surrogate as S
+    assert gw.gw_surrogate_param_count(*dims) == S.n_params(*dims)
+
+
+@pytest.mark.parametrize("dims", [(0, 256, 48), (65, 256, 48), (12, 0, 48), (12, 4097, 48), (12, 256, 0),
+                                  (12, 256, 1025)])
+def test_surrogate_dims_are_checked(lib, dims):
+    with pytest.raises(gw.GwError) as ei:
+        gw.gw_surrogate_param_count(*dims)
+    assert ei.value.status == gw.GW_ERR_ARG
+    h = ctypes.c_void_p()
+    d = gw.gw_surrogate_dims(*dims)
+    assert lib.gw_surrogate_create(ctypes.byref(d), None, None, ctypes.byref(h)) == gw.GW_ERR_ARG
+    assert not h.value
