@@ -2,11 +2,13 @@
 
 Translation units are compiled in parallel and linked into
 paper_2011_01400_gb300/libgw.so. Rebuilds only when a source or header is newer
-than the library.
+than the library. Concurrent callers (one process per GPU rank) are serialised by a
+file lock; a caller that waited finds the library fresh and returns.
 """
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -47,8 +49,19 @@ def build(force=False, verbose=False, extra=()):
     """Compile every .cu under csrc/ and link libgw.so. Returns the library path."""
     if not force and not _stale():
         return LIB
-    nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and not _stale():
+                return LIB
+            return _build_locked(verbose, extra)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose, extra):
+    nvcc = _nvcc()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
