@@ -31,6 +31,10 @@
  *                           chi0 (default 2048; at least 32);
  *     GW_CHI0_COMPRESS_TOL  per-frequency residual bound of the chi0 weight-matrix
  *                           compression (default 3e-8; 0 keeps all frequencies).
+ *   - Environment (read at gw_plan_create, all precisions):
+ *     GW_WORKSPACE_LIMIT    bytes of device memory one plan may allocate for its workspace
+ *                           (default: no limit). An allocation that would pass it fails with
+ *                           GW_ERR_NOMEM before cudaMalloc is called.
  *   - Autotuning: the first split-precision call that generates band-pair rows
  *     of a given shape in this process times two thread mappings of that kernel
  *     (one warm-up and one timed launch each). It then waits for the plan's stream
@@ -192,12 +196,17 @@ gw_status gw_qp(gw_plan plan, int32_t sys, const gw_complex* sigma, const double
  * or a serving loop that must not take the device-wide synchronisation of cudaFree.
  * The plan itself still owns the workspace gw_plan_create allocated.
  * - N_k * (sigma_hi - sigma_lo) > GW_QP_STATIC_MAX: GW_ERR_ARG, nothing launched (use gw_qp).
+ * - The current CUDA device must be the plan's device (the one current at gw_plan_create):
+ *   the scratch address is per device. Otherwise GW_ERR_STATE, nothing launched.
  * - The first call on a device looks up the scratch address with cudaGetSymbolAddress (this
- *   may load the library's device code); make that first call before any stream capture.
+ *   may load the library's device code) and caches it for the life of the process.
+ * - The call is synchronous: it reads the energies back to the host and waits for the plan's
+ *   stream, so it cannot be called while that stream is being captured.
  * - Nothing in the scratch has to start at zero: every call writes each element it reads.
  * - One scratch array per device: calls that overlap in time on the same device (from any
  *   thread, stream or plan) race on it. Serialise them.
- * Errors: as gw_qp, plus GW_ERR_CUDA if the address lookup fails. */
+ * Errors: as gw_qp, plus GW_ERR_STATE (wrong current device) and GW_ERR_CUDA if the address
+ * lookup fails. */
 gw_status gw_qp_static(gw_plan plan, int32_t sys, const gw_complex* sigma, const double* dxv,
                        double* e_qp, double* gap, int32_t* n_conv);
 
@@ -221,6 +230,10 @@ gw_status gw_plan_chi0_terms(gw_plan plan, int32_t* terms);
 
 /* Number of CUDA kernels this library has launched in the calling process so far (host-side count). */
 gw_status gw_kernel_launches(uint64_t* count);
+
+/* Number of device allocations (cudaMalloc calls) this library has made in the calling process
+ * so far (host-side count; failed attempts included). */
+gw_status gw_device_allocations(uint64_t* count);
 
 /* ------------------------------------------------------------------------------------------
  * Learned frequency surrogate (no counterpart in the paper).

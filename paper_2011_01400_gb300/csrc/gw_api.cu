@@ -15,6 +15,7 @@
 
 namespace gw {
 std::atomic<unsigned long long> g_launch_count{0};
+std::atomic<unsigned long long> g_alloc_count{0};
 }
 
 using namespace gw;
@@ -221,6 +222,10 @@ struct gw_plan_s {
   int chi0_q = -1, wc_q = -1;
   // device memory owned by the plan
   std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;  // size of each entry of allocs
+  size_t ws_bytes = 0;              // sum of alloc_bytes
+  size_t ws_limit = 0;              // GW_WORKSPACE_LIMIT (bytes; 0 = no limit)
+  int dev = -1;                     // CUDA device that was current at gw_plan_create
   double *d_freq = nullptr, *d_fw = nullptr, *d_mu = nullptr;
   void* d_T1 = nullptr;     // c128 (FP64) or c64 (split)
   c128* d_Vh = nullptr;     // [NK][N][N] V(q)^1/2 (full, truncated at q=0)
@@ -323,16 +328,32 @@ struct gw_plan_s {
 namespace {
 
 template <typename T> gw_status dalloc(gw_plan_s* P, T** ptr, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (P->ws_limit && P->ws_bytes + bytes > P->ws_limit)
+    return fail(GW_ERR_NOMEM, "workspace limit GW_WORKSPACE_LIMIT = " + std::to_string(P->ws_limit) +
+                                  " bytes reached: " + std::to_string(P->ws_bytes) + " held, " +
+                                  std::to_string(bytes) + " more requested");
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+  ++g_alloc_count;
+  cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(GW_ERR_NOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " +
+    return fail(GW_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
                                   cudaGetErrorString(e));
   }
   P->allocs.push_back(p);
+  P->alloc_bytes.push_back(bytes);
+  P->ws_bytes += bytes;
   *ptr = static_cast<T*>(p);
   return GW_OK;
+}
+
+// frees the most recent dalloc
+void dfree_last(gw_plan_s* P) {
+  cudaFree(P->allocs.back());
+  P->allocs.pop_back();
+  P->ws_bytes -= P->alloc_bytes.back();
+  P->alloc_bytes.pop_back();
 }
 
 #define GW_TRY(x)                    \
@@ -406,8 +427,7 @@ gw_status newton_schulz(gw_plan_s* P, const c128* V, c128* out, int batch, int i
   if (e != cudaSuccess) return fail(GW_ERR_CUDA, std::string("newton_schulz: ") + cudaGetErrorString(e));
   // release the temporaries (they were the last five allocations)
   for (int i = 0; i < 5; ++i) {
-    cudaFree(P->allocs.back());
-    P->allocs.pop_back();
+    dfree_last(P);
   }
   return GW_OK;
 }
@@ -488,6 +508,12 @@ extern "C" {
 
 const char* gw_last_error(void) { return g_last_error.c_str(); }
 
+gw_status gw_device_allocations(uint64_t* count) {
+  if (!count) return fail(GW_ERR_ARG, "count is NULL");
+  *count = g_alloc_count.load();
+  return GW_OK;
+}
+
 gw_status gw_kernel_launches(uint64_t* count) {
   if (!count) return fail(GW_ERR_ARG, "count is NULL");
   *count = (uint64_t)::gw::g_launch_count;
@@ -547,12 +573,17 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
   P->p.basis_atom = P->basis_atom.data();
   P->p.aux_atom = P->aux_atom.data();
   P->p.R = P->R.data();
+  if (const char* v = std::getenv("GW_WORKSPACE_LIMIT")) {
+    const double lim = std::atof(v);
+    if (lim > 0) P->ws_limit = (size_t)lim;
+  }
   auto cleanup = [&](gw_status s) {
     std::string msg = g_last_error;
     gw_plan_destroy(P);
     g_last_error = msg;
     return s;
   };
+  if (cudaGetDevice(&P->dev) != cudaSuccess) return cleanup(fail(GW_ERR_CUDA, "cudaGetDevice failed"));
   // geometry
   LriGeom& g = P->geom;
   g.n_atoms = P->natoms;
@@ -1230,10 +1261,8 @@ gw_status gw_qp(gw_plan P, int32_t sys, const gw_complex* sigma, const double* d
   GW_CUDA(cudaMemcpyAsync(e_qp, d_e, n * sizeof(double), cudaMemcpyDeviceToHost, st));
   GW_CUDA(cudaMemcpyAsync(conv.data(), d_c, n * sizeof(int), cudaMemcpyDeviceToHost, st));
   GW_CUDA(cudaStreamSynchronize(st));
-  cudaFree(P->allocs.back());
-  P->allocs.pop_back();
-  cudaFree(P->allocs.back());
-  P->allocs.pop_back();
+  dfree_last(P);
+  dfree_last(P);
   int nc = 0;
   for (int i = 0; i < n; ++i) nc += conv[i];
   if (n_conv) *n_conv = nc;
@@ -1327,6 +1356,11 @@ gw_status gw_qp_static(gw_plan P, int32_t sys, const gw_complex* sigma, const do
     return fail(GW_ERR_ARG, "gw_qp_static: N_k * n_sigma = " + std::to_string(n) +
                                 " exceeds the static scratch capacity GW_QP_STATIC_MAX = " +
                                 std::to_string(GW_QP_STATIC_MAX) + "; use gw_qp");
+  int cur = -1;
+  GW_CUDA(cudaGetDevice(&cur));
+  if (cur != P->dev)
+    return fail(GW_ERR_STATE, "gw_qp_static: the current device (" + std::to_string(cur) +
+                                  ") is not the plan's device (" + std::to_string(P->dev) + ")");
   QpScratch* sc = nullptr;
   GW_TRY(qp_scratch(&sc));
   cudaStream_t st = P->st;

@@ -14,6 +14,7 @@ namespace gw {
 
 // number of kernels this library has launched (process-wide, host side)
 extern std::atomic<unsigned long long> g_launch_count;
+extern std::atomic<unsigned long long> g_alloc_count;   // device allocations (cudaMalloc) made by the library
 
 // complex helpers (device and host)
 template <typename T> struct cplx { T re, im; };

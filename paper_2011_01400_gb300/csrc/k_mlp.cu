@@ -379,6 +379,7 @@ struct gw_surrogate_s {
 namespace {
 
 gw_status salloc(gw_surrogate_s* m, void** p, size_t bytes) {
+  ++::gw::g_alloc_count;
   cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
   if (e != cudaSuccess) {
     cudaGetLastError();

@@ -848,6 +848,7 @@ gw_status TcWorkspace::ensure(int ntiles_needed, int ones_needed, cudaStream_t s
   if (ntiles_needed > tile_cap) {
     if (tiles) cudaFree(tiles);
     tiles = nullptr;
+    ++::gw::g_alloc_count;
     if (cudaMalloc(&tiles, sizeof(short2) * ntiles_needed) != cudaSuccess) {
       err = "tile table allocation failed";
       tile_cap = 0;
@@ -858,6 +859,7 @@ gw_status TcWorkspace::ensure(int ntiles_needed, int ones_needed, cudaStream_t s
   if (ones_needed > ones_cap) {
     if (ones) cudaFree(ones);
     ones = nullptr;
+    ++::gw::g_alloc_count;
     if (cudaMalloc(&ones, sizeof(float) * ones_needed) != cudaSuccess) {
       err = "weight table allocation failed";
       ones_cap = 0;

@@ -25,6 +25,7 @@ EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigm
            "gw_g0w0_batch",
            "gw_plan_n_sys", "gw_qp",
            "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_plan_chi0_terms", "gw_kernel_launches",
+           "gw_device_allocations",
            "gw_surrogate_param_count", "gw_surrogate_create", "gw_surrogate_destroy", "gw_surrogate_get_params",
            "gw_surrogate_set_params", "gw_surrogate_forward", "gw_surrogate_loss_grad", "gw_surrogate_fit_linear",
            "gw_surrogate_train", "gw_surrogate_enable", "gw_surrogate_modes", "gw_surrogate_data", "gw_surrogate_fit_moments",
@@ -101,6 +102,7 @@ def load():
     lib.gw_plan_last_chi0_stats.argtypes = [vp, dp, dp]
     lib.gw_plan_chi0_terms.argtypes = [vp, ctypes.POINTER(i32)]
     lib.gw_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    lib.gw_device_allocations.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     i64, u64, dpp = ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)
     dimp = ctypes.POINTER(gw_surrogate_dims)
     lib.gw_surrogate_param_count.argtypes = [dimp, ctypes.POINTER(i64)]
@@ -228,6 +230,12 @@ def gw_plan_mu(plan):
 def gw_kernel_launches():
     n = ctypes.c_uint64()
     _check(load().gw_kernel_launches(ctypes.byref(n)))
+    return n.value
+
+
+def gw_device_allocations():
+    n = ctypes.c_uint64()
+    _check(load().gw_device_allocations(ctypes.byref(n)))
     return n.value
 
 

@@ -1,7 +1,8 @@
 """Parity at the benchmark's full size: cfg1 (6x6x6 k, 78 bands, 400 ABF, 32 frequencies), the
-system bench.py times (seed 1000), through the same C-ABI calls. The oracle can afford one q of
-it (about a minute and a half on the host cores): chi0 at every frequency, eps~ / W^c and the
-q = 1 term of Sigma_c for every k and band of the window."""
+system bench.py times (seed 1000), through the same C-ABI calls. The oracle can afford two q of
+it (about a minute and a half each on the host cores): chi0 at every frequency, eps~ / W^c and the
+q term of Sigma_c for every k and band of the window, at q = 1 and at q = 0 (the head and wings of
+the dielectric matrix, Eq. dielectric_func_gamma)."""
 import numpy as np
 import pytest
 
@@ -33,18 +34,32 @@ def cfg1_q1():
     return s, chi, W, sig
 
 
+@pytest.fixture(scope="module")
+def cfg1_q0():
+    s = make_system("cfg1", seed=1000)
+    assert s.head_wings == 1
+    om, g = O.freq_grid(s.n_freq, s.omega0)
+    chi = O.chi0(s, 0, om)
+    _, W = O.screen(s, 0, chi, om)
+    sig = O.sigma_q(s, 0, W, om, g, O.mu_midgap(s))
+    return s, chi, W, sig
+
+
 def rel_fro(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("prec,tol_chi,tol_w,tol_sig_mev", [("3xbf16", 1e-6, 1e-4, 1.0), ("fp64", 1e-11, 1e-10, 1e-6)])
-def test_cfg1_one_q_full_size(cfg1_q1, prec, tol_chi, tol_w, tol_sig_mev):
+@pytest.mark.parametrize("qcase", ["cfg1_q1", "cfg1_q0"])
+@pytest.mark.parametrize("prec,tol_chi,tol_w,tol_sig_mev",
+                         [("3xbf16", 1e-6, 1e-4, 1.0), ("3xtf32", 1e-6, 1e-4, 1.0), ("fp64", 1e-11, 1e-10, 1e-6)])
+def test_cfg1_one_q_full_size(request, qcase, prec, tol_chi, tol_w, tol_sig_mev):
     """chi0 and Sigma_c hold their targets (1e-6 relative, 1 meV). W^c has none of its own: on the
     split path its screen products are FP32 (~1e-7 relative per term), and at the highest
     frequencies W^c = V^1/2 (eps~^-1 - 1) V^1/2 is a difference 1e-2..1e-3 of its terms, so its
     relative error is bounded by 1e-4 (cfg1, q = 1: 1.2e-5)."""
     from paper_2011_01400_gb300 import gw
-    s, chi_ref, W_ref, sig_ref = cfg1_q1
+    s, chi_ref, W_ref, sig_ref = request.getfixturevalue(qcase)
+    Q = 0 if qcase == "cfg1_q0" else 1
     N, nw, nsig = s.n_aux, s.n_freq, s.sigma_hi - s.sigma_lo
     pb = gw.Problem(s, prec)
     plan = gw.gw_plan_create(pb.prob)

@@ -120,7 +120,7 @@ def test_sigma_qp_gap_cfg0(cfg0, prec, tol_mev):
     assert err_sig <= tol_mev and err_e <= tol_mev and err_gap <= tol_mev
 
 
-@pytest.mark.parametrize("prec", ["fp64", "3xtf32"])
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "3xbf16"])
 def test_g0w0_driver_matches_per_q_calls(cfg0, prec):
     """gw_g0w0 (q groups, batched FP64 factorisations) gives the per-q result and the oracle's."""
     from paper_2011_01400_gb300 import gw
@@ -164,3 +164,28 @@ def test_sigma_x_cfg0(prec, tol_mev):
     assert err <= tol_mev
     if prec == "fp64":
         assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("window", [(0, 4), (1, 3)])
+def test_qp_gap_selection_hand_built(window):
+    """gw_qp and gw_qp_static on the hand-built case of tests/qp_case.py (caller-owned Sigma_c
+    and Sigma_x - v_xc): the QP energies, the indirect gap known by construction, and the
+    midgap chemical potential."""
+    import qp_case as C
+    from paper_2011_01400_gb300 import gw
+    s = C.system(window)
+    nsig = s.sigma_hi - s.sigma_lo
+    pb = gw.Problem(s, "fp64")
+    plan = gw.gw_plan_create(pb.prob)
+    try:
+        f, _ = gw.gw_plan_freq(plan, s.n_freq)
+        sig = torch.from_numpy(C.sigma_c(s, f)).cuda()
+        dxv = torch.from_numpy(C.dxv(s)).cuda()
+        for call in (gw.gw_qp, gw.gw_qp_static):
+            e, gap, nconv = call(plan, 0, s.n_k, nsig, sigma=sig, dxv=dxv)
+            assert nconv == s.n_k * nsig
+            assert np.abs(e - C.e_expected(s)).max() < 1e-8
+            assert abs(gap - C.GAP) < 1e-8
+        assert abs(gw.gw_plan_mu(plan) - C.MU) < 1e-15
+    finally:
+        gw.gw_plan_destroy(plan)

@@ -306,3 +306,23 @@ def test_chi0_block_is_a_block_of_chi0():
     full = O.chi0(s, 3, om[:3])
     blk = O.chi0_block(s, 3, om[:3], mus)
     assert np.abs(blk - full[:, mus][:, :, mus]).max() <= 1e-13 * np.abs(full).max()
+
+
+@pytest.mark.parametrize("window", [(0, 4), (1, 3)])
+def test_qp_gap_selection_hand_built(window):
+    """The indirect gap takes band n_occ - 1 (HOMO) and band n_occ (LUMO) at every k, after the
+    QP shift, and the window offset sigma_lo; the case (tests/qp_case.py) is built so that every
+    other plausible selection gives another number."""
+    import qp_case as C
+    s = C.system(window)
+    om, _ = O.freq_grid(s.n_freq, s.omega0)
+    E, gap, conv = O.qp(s, C.sigma_c(s, om), om, O.mu_midgap(s), C.dxv(s))
+    assert conv.all()
+    assert np.abs(E - C.e_expected(s)).max() < 1e-8
+    assert abs(gap - C.GAP) < 1e-8
+
+
+def test_mu_midgap_hand_built():
+    """Midgap chemical potential of the hand-built energies: (max_k HOMO + min_k LUMO) / 2."""
+    import qp_case as C
+    assert abs(O.mu_midgap(C.system()) - C.MU) < 1e-15
