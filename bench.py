@@ -35,6 +35,8 @@ WORKLOADS = {
     "cfg0": "tiny synthetic insulator: 2x2x2 k, 2 atoms, 32 NAO, 32 bands (4 occ), 96 ABF, 16 imaginary frequencies",
     "cfg1": "Si-like 2-atom fcc cell: 6x6x6 k (216 k, 216 q), 78 NAO, 78 bands (4 occ), 400 ABF, 32 imaginary "
             "frequencies, Sigma_c for the 8 bands at the gap",
+    "cfg2": "ZnO-like 4-atom cell: 6x6x4 k (144 k, 144 q), 300 NAO, 300 bands (36 occ), 1600 ABF, 32 imaginary "
+            "frequencies, Sigma_c for the 8 bands at the gap; M generated per chunk of k and never stored whole",
 }
 
 
@@ -179,16 +181,17 @@ def max_over_ranks(vals, world, device="cpu"):
     return [float(x) for x in t]
 
 
-def seconds_per_system(ms_per_step_max, world):
-    """Whole-job value: every rank processes one system per step, so the job finishes `world`
-    systems in the slowest rank's step time."""
-    return ms_per_step_max / 1e3 / world
+def seconds_per_system(ms_per_step_max, world, parallel="replicas"):
+    """Whole-job value. Replicas: every rank processes one system per step, so the job finishes
+    `world` systems in the slowest rank's step time. q-parallel: the ranks share one system per
+    step, which is done when the slowest rank is."""
+    return ms_per_step_max / 1e3 / (world if parallel == "replicas" else 1)
 
 
-def replica_seed(config, rank):
-    """Seed of the system a rank processes: the configuration's seed, offset by the rank, so the
-    replicas of a multi-GPU run work on different systems."""
-    return 1000 * int(config[-1]) + rank
+def replica_seed(config, rank, parallel="replicas"):
+    """Seed of the system a rank processes: the configuration's seed, offset by the rank for
+    replicas (different systems); the same system on every rank of a q-parallel run."""
+    return 1000 * int(config[-1]) + (rank if parallel == "replicas" else 0)
 
 
 def run_reference(args, system, world, rank):
@@ -212,10 +215,16 @@ def run_reference(args, system, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def g0w0_step(gw, plan_prob, s, torch, chi_ms, qloop="g0w0"):
-    """One complete pass: plan, the q loop (one native call, or per-q calls), QP. Returns (e_qp, gap)."""
+def g0w0_step(gw, plan_prob, s, torch, chi_ms, qloop="g0w0", qshard=False):
+    """One complete pass: plan, the q loop (one native call, per-q calls, or this rank's part of
+    the q mesh followed by the sum of Sigma_c over the ranks), QP. Returns (e_qp, gap)."""
     plan = gw.gw_plan_create(plan_prob)
     try:
+        if qshard:
+            from paper_2011_01400_gb300 import shard
+            _, e, gap = shard.g0w0_sharded(gw, plan, 0, s)
+            chi_ms.append(gw.gw_plan_last_chi0_stats(plan))
+            return e, gap
         if qloop == "g0w0":
             gw.gw_g0w0(plan, 0)
             chi_ms.append(gw.gw_plan_last_chi0_stats(plan))
@@ -233,6 +242,46 @@ def g0w0_step(gw, plan_prob, s, torch, chi_ms, qloop="g0w0"):
     finally:
         gw.gw_plan_destroy(plan)
     return e, gap
+
+
+def timed_pass(gw, s, prec, torch, warm=1, qs=None):
+    """One G0W0 pass of system s at precision prec (plan, the q loop, QP), CUDA-event timed on the
+    current stream after `warm` untimed passes. qs: only these q points (gw_g0w0_qset, no QP).
+    Returns (seconds, e_qp, gap, (chi0 ms, chi0 flops))."""
+    pb = gw.Problem(s, prec)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    nsig = s.sigma_hi - s.sigma_lo
+    out = None
+    for i in range(warm + 1):
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        plan = gw.gw_plan_create(pb.prob)
+        try:
+            if qs is None:
+                gw.gw_g0w0(plan, 0)
+                e, gap, _ = gw.gw_qp(plan, 0, s.n_k, nsig)
+            else:
+                acc = torch.zeros((s.n_k, nsig, s.n_freq), dtype=torch.complex128, device="cuda")
+                gw.gw_g0w0_qset(plan, 0, qs, acc)
+                e, gap = None, None
+            chi = gw.gw_plan_last_chi0_stats(plan)
+        finally:
+            gw.gw_plan_destroy(plan)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        out = (ev[0].elapsed_time(ev[1]) / 1e3, e, gap, chi)
+    return out
+
+
+def chi0_frac(prec, chi, s, T_rows, peak_bf16):
+    """chi0 TFLOP/s (algorithmic), its fraction of the dense peak of the precision's operand type
+    and the tensor-issued fraction (split products, compressed weight rows)."""
+    ms, fl = chi
+    a = fl / (ms * 1e-3) / 1e12
+    peak = peak_bf16 * (0.5 if prec == "3xtf32" else 1.0)
+    products = {"3xfp16": 3, "3xbf16": 6, "3xtf32": 3}[prec]
+    return dict(chi0_tflops=a, frac=a / peak, tensor_issued_frac=a * products * T_rows / s.n_freq / peak)
 
 
 def q_slice_ms(gw, s, prec, torch, q=1, reps=2):
@@ -419,6 +468,70 @@ def batch_bench(args, gw, torch):
                      "the time covers the whole G0W0 pass of every system, plans built beforehand")
 
 
+def run_slice(args, gw, torch, s, world, rank):
+    """Large workloads (cfg2): a whole pass takes tens of minutes, so a step is a labelled bounded
+    slice: plan creation plus the complete q loop (chi0 over all k and frequencies, eps~ / W^c,
+    Sigma_c) of `--qslice` q points through gw_g0w0_qset. value extrapolates the pass as plan +
+    N_q x (slice time per q); the slice itself is reported as measured."""
+    qs = list(range(1, 1 + args.qslice))
+    pb = gw.Problem(s, args.prec)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    nsig = s.sigma_hi - s.sigma_lo
+    res = []
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    l0 = None
+    for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            clocks.start()
+            l0 = gw.gw_kernel_launches()
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        plan = gw.gw_plan_create(pb.prob)
+        ev[1].record(stream)
+        try:
+            acc = torch.zeros((s.n_k, nsig, s.n_freq), dtype=torch.complex128, device="cuda")
+            ev[2].record(stream)
+            gw.gw_g0w0_qset(plan, 0, qs, acc)
+            ev[3].record(stream)
+            chi = gw.gw_plan_last_chi0_stats(plan)
+            T_rows = gw.gw_plan_chi0_terms(plan) or s.n_freq
+        finally:
+            gw.gw_plan_destroy(plan)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            res.append((ev[0].elapsed_time(ev[1]) / 1e3, ev[2].elapsed_time(ev[3]) / 1e3, chi))
+    ck = clocks.stop()
+    launches = gw.gw_kernel_launches() - l0
+    if rank != 0:
+        return
+    plan_s = statistics.median(r[0] for r in res)
+    slice_s = statistics.median(r[1] for r in res)
+    chi = res[-1][2]
+    peak_bf16, _, peak_kind = load_peaks()
+    fr = chi0_frac(args.prec, chi, s, T_rows, peak_bf16)
+    peak = peak_bf16 * (0.5 if args.prec == "3xtf32" else 1.0)
+    est = plan_s + s.n_k * slice_s / len(qs)
+    line = dict(metric=METRIC, value=est, unit="s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=(plan_s + slice_s) * 1e3, higher_is_better=False, scaling="weak", vs_baseline=None,
+                dtype={"3xfp16": "fp16x2-split/f32-acc/f64", "3xbf16": "bf16x3-split/f32-acc/f64",
+                       "3xtf32": "tf32x2-split/f32-acc/f64", "fp64": "f64"}[args.prec],
+                data="synthetic",
+                config=dict(workload=WORKLOADS[args.config], name=args.config, precision=args.prec,
+                            slice=f"plan + the q loop of q = {qs} (all k, all {s.n_freq} frequencies); value = "
+                                  f"plan + {s.n_k} x slice per q (extrapolated, labelled)",
+                            global_batch=1, seq_len=0, parallelism="single",
+                            l2="inputs larger than L2 (chi0 operand plane 7 GB per q)"),
+                value_kind="extrapolated from the measured slice", plan_s=plan_s, slice_s=slice_s,
+                slice_q=len(qs), chi0_tflops=fr["chi0_tflops"],
+                roofline=dict(bound="tensor", achieved=fr["chi0_tflops"], peak=peak, unit="TFLOP/s",
+                              frac=fr["frac"], traffic=None, kernel="k_chi0",
+                              tensor_issued_frac=fr["tensor_issued_frac"], chi0_weight_rows=T_rows,
+                              peak_note=f"dense peak of the operand type, {peak_kind}"),
+                e2e=None, gpu_launches=launches, clocks=ck)
+    print(json.dumps(line), flush=True)
+
+
 def run_device(args, system, world, rank):
     import torch
     import torch.distributed as dist
@@ -430,6 +543,8 @@ def run_device(args, system, world, rank):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     s = system
+    if args.config == "cfg2":
+        return run_slice(args, gw, torch, s, world, rank)
     pb = gw.Problem(s, args.prec, host=True)
     stream = torch.cuda.current_stream()
 
@@ -437,9 +552,11 @@ def run_device(args, system, world, rank):
         if world > 1:
             dist.barrier()
 
+    qshard = world > 1 and args.parallel == "qshard"
+    mode = "qshard" if qshard else "replicas"
     chi_ms = []
     for _ in range(args.warmup):
-        g0w0_step(gw, pb.prob, s, torch, chi_ms, args.qloop)
+        g0w0_step(gw, pb.prob, s, torch, chi_ms, args.qloop, qshard)
     torch.cuda.synchronize()
     # device-resident timed region
     chi_ms.clear()
@@ -451,7 +568,7 @@ def run_device(args, system, world, rank):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        e, gap = g0w0_step(gw, pb.prob, s, torch, chi_ms, args.qloop)
+        e, gap = g0w0_step(gw, pb.prob, s, torch, chi_ms, args.qloop, qshard)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -468,7 +585,7 @@ def run_device(args, system, world, rank):
         e0.record(stream)
         for _ in range(args.steps):
             pb.upload()
-            e_qp, gap = g0w0_step(gw, pb.prob, s, torch, chi_e2e, args.qloop)
+            e_qp, gap = g0w0_step(gw, pb.prob, s, torch, chi_e2e, args.qloop, qshard)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -499,44 +616,72 @@ def run_device(args, system, world, rank):
     tf32 = args.prec == "3xtf32"
     peak = peak_bf16 * (0.5 if tf32 else 1.0) if args.prec != "fp64" else 1.25
     achieved = chi_flops / (chi_avg_ms * 1e-3) / 1e12
-    products = {"3xbf16": 6, "3xtf32": 3, "fp64": 1}[args.prec]
+    products = {"3xfp16": 3, "3xbf16": 6, "3xtf32": 3, "fp64": 1}[args.prec]
     cap = CHI0_DRAM_CAPTURE
     traffic = None
     if cap is not None and args.prec == cap["prec"] and s.n_aux == cap["n_aux"]:
         traffic = cap["read"] * s.n_k / cap["n_k"] + cap["write"]
     line = dict(
         metric=METRIC,
-        value=seconds_per_system(ms, world),
+        value=seconds_per_system(ms, world, mode),
         unit="s",
         n_gpus=world, steps=args.steps, warmup=args.warmup, ms_per_step=ms,
-        higher_is_better=False, scaling="weak", vs_baseline=None,
-        dtype={"3xbf16": "bf16x3-split/f32-acc/f64", "3xtf32": "tf32x2-split/f32-acc/f64", "fp64": "f64"}[args.prec],
+        higher_is_better=False, scaling="strong" if qshard else "weak", vs_baseline=None,
+        dtype={"3xfp16": "fp16x2-split/f32-acc/f64", "3xbf16": "bf16x3-split/f32-acc/f64",
+               "3xtf32": "tf32x2-split/f32-acc/f64", "fp64": "f64"}[args.prec],
         data="synthetic",
         config=dict(workload=WORKLOADS[args.config] + (f" (k mesh overridden to {args.nk})" if args.nk else ""),
-                    name=args.config, precision=args.prec, systems_per_step=world, q_loop=args.qloop,
-                    global_batch=world, seq_len=0, parallelism="replicas" if world > 1 else "single",
+                    name=args.config, precision=args.prec, systems_per_step=1 if qshard else world,
+                    q_loop="q-parallel (gw_g0w0_qset + Sigma_c sum over ranks)" if qshard else args.qloop,
+                    global_batch=1 if qshard else world, seq_len=0, parallelism=mode if world > 1 else "single",
                     l2="inputs larger than L2 (chi0 operand planes 0.8 GB per q)"),
         chi0_tflops=achieved,
         step_useful_tflops=fl["total"] / (ms * 1e-3) / 1e12,
         roofline=dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                      traffic=traffic, kernel="k_tc<chi0> (tcgen05 weighted Hermitian update)",
+                      traffic=traffic, kernel="k_chi0 (tcgen05 weighted Hermitian update, Re/Im rows stacked on M)",
                       traffic_note=None if traffic is None else
                       f"DRAM bytes per launch (one q), scaled from an ncu capture on {cap['n_k']} k: "
                       f"reads x {s.n_k}/{cap['n_k']}, writes as captured",
-                      peak_note=f"{'TF32' if tf32 else 'BF16'} dense {peak_kind}; achieved counts algorithmic "
+                      peak_note=f"{'TF32' if tf32 else ('FP16' if args.prec == '3xfp16' else 'BF16')} dense "
+                                f"{peak_kind} (FP16 and BF16 share the rate); achieved counts algorithmic "
                                 f"flops (8 per complex MAC, lower triangle, all {s.n_freq} frequencies); the "
                                 f"kernel runs {T_rows} compressed weight rows instead of {s.n_freq} frequencies and "
                                 f"x{products} split products: tensor-issued = achieved x {products} x "
                                 f"{T_rows}/{s.n_freq}",
                       chi0_weight_rows=T_rows,
                       tensor_issued_frac=achieved * products * T_rows / s.n_freq / peak),
-        e2e=None if args.no_e2e else dict(value=ms_e2e / 1e3 / world, unit="s", h2d_bytes_per_step=pb.nbytes(),
+        e2e=None if args.no_e2e else dict(value=seconds_per_system(ms_e2e, world, mode), unit="s", h2d_bytes_per_step=pb.nbytes(),
                                           d2h_bytes_per_step=s.n_k * (s.sigma_hi - s.sigma_lo) * 8 + 8),
         gpu_launches=launches,
         clocks=ck,
         fp64_gpu=fp64,
         gap_ha=gap,
     )
+    ha = 27211.386
+    if world == 1 and not args.no_extras and args.prec != "fp64":
+        # the other split precisions on the same system: one timed pass each after one warm-up
+        others = {}
+        for p in ("3xfp16", "3xbf16", "3xtf32"):
+            if p == args.prec:
+                continue
+            t, e_p, gap_p, chi = timed_pass(gw, s, p, torch)
+            others[p] = dict(step_s=t, **chi0_frac(p, chi, s, T_rows, peak_bf16),
+                             max_abs_dE_qp_meV_vs_main=float(abs(e_p - e).max() * ha),
+                             abs_dgap_meV_vs_main=float(abs(gap_p - gap) * ha))
+        line["other_precisions"] = others
+        # like for like at matched accuracy: the whole pass in FP64 and split precision on the
+        # workload's band / ABF / frequency shape with a 3x3x3 k mesh
+        from paper_2011_01400_gb300.synth import make_system
+        s3 = make_system(args.config, seed=replica_seed(args.config, 0), nk=(3, 3, 3))
+        t64, e64, g64, _ = timed_pass(gw, s3, "fp64", torch, warm=0)
+        fp64_pass = dict(system=f"{args.config} shape on a 3x3x3 k mesh (27 k, 27 q), seed "
+                                f"{replica_seed(args.config, 0)}; plan + gw_g0w0 + gw_qp, CUDA events",
+                         fp64_s=t64)
+        for p in ("3xfp16", "3xbf16", "3xtf32"):
+            tp, ep, gp, _ = timed_pass(gw, s3, p, torch)
+            fp64_pass[p] = dict(step_s=tp, speedup=t64 / tp, max_abs_dE_qp_meV=float(abs(ep - e64).max() * ha),
+                                abs_dgap_meV=float(abs(gp - g64) * ha))
+        line["fp64_pass"] = fp64_pass
     if args.surrogate:
         line["surrogate"] = surrogate_bench(args, gw, torch)
     if args.batch:
@@ -553,10 +698,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", default="cfg1", choices=list(WORKLOADS))
-    ap.add_argument("--prec", default="3xbf16", choices=["3xbf16", "3xtf32", "fp64"])
+    ap.add_argument("--prec", default="3xbf16", choices=["3xfp16", "3xbf16", "3xtf32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-slice", action="store_true")
+    ap.add_argument("--qslice", type=int, default=2, help="cfg2: q points of the timed slice")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other split precisions and the FP64 pass on the 3x3x3 mesh")
     ap.add_argument("--qloop", default="g0w0", choices=["g0w0", "perq"],
                     help="q loop in one gw_g0w0 call (default) or as per-q gw_chi0/gw_screen/gw_sigma calls")
     ap.add_argument("--nk", default=None, help="override the k mesh, e.g. 4,4,4 (profiling captures)")
@@ -564,6 +712,9 @@ def main():
                     help="also train the frequency surrogate and time it against the full 60-point grid")
     ap.add_argument("--sur-systems", type=int, default=64, help="training systems of the surrogate")
     ap.add_argument("--sur-epochs", type=int, default=40, help="training epochs of the surrogate")
+    ap.add_argument("--parallel", default="qshard", choices=["qshard", "replicas"],
+                    help="N > 1: split the q mesh of one system over the ranks and sum Sigma_c (default), or "
+                         "run one independent system per rank")
     ap.add_argument("--batch", type=int, default=0,
                     help="also run a batch of this many seeded systems of uneven size (e.g. 64)")
     args = ap.parse_args()
@@ -576,7 +727,7 @@ def main():
     over = {}
     if args.nk:
         over["nk"] = tuple(int(x) for x in args.nk.split(","))
-    system = make_system(args.config, seed=replica_seed(args.config, rank), **over)
+    system = make_system(args.config, seed=replica_seed(args.config, rank, args.parallel), **over)
     if args.impl == "reference":
         run_reference(args, system, world, rank)
     else:

@@ -64,7 +64,10 @@ typedef enum {
 typedef enum {
   GW_FP64 = 0,    /* plain method: every contraction in FP64 on CUDA cores          */
   GW_3XTF32 = 1,  /* contractions as 3 TF32 split products on tcgen05, FP32 accum.   */
-  GW_3XBF16 = 2   /* contractions as 3 BF16 split products on tcgen05, FP32 accum.   */
+  GW_3XBF16 = 2,  /* contractions as BF16 split products on tcgen05 (chi0: 3 pieces, 6
+                     products; Sigma_c: 2 pieces, 3 products), FP32 accumulation          */
+  GW_3XFP16 = 3   /* chi0 as 3 FP16 split products (2 pieces, power-of-two scaled) on
+                     tcgen05, FP32 accumulation; the other contractions as GW_3XBF16     */
 } gw_precision;
 
 typedef struct { double re, im; } gw_complex;
@@ -160,6 +163,14 @@ gw_status gw_sigma_x(gw_plan plan, int32_t sys, double* sigx);
  * the group buffers (about 8 GB at most) are allocated on the first call and kept by the plan.
  * Results equal those of the per-q calls. Errors: as gw_chi0 / gw_screen / gw_sigma. */
 gw_status gw_g0w0(gw_plan plan, int32_t sys, gw_complex* sigma_acc);
+
+/* gw_g0w0 over the listed q points only (q_list: host [n_q], distinct, in [0, N_k)): their chi0,
+ * eps~, W^c and Sigma_c terms, accumulated into sigma_acc (device [N_k][n_sigma][n_freq]; the
+ * caller zeroes it). The q terms are independent, so disjoint lists that cover the mesh, run
+ * on several devices (one plan each) and summed, give gw_g0w0's Sigma_c: the q-parallel form of
+ * the pass, whose only exchange is that sum. Not available with a surrogate attached.
+ * Errors: GW_ERR_ARG (NULL, out-of-range or repeated q), GW_ERR_UNSUPPORTED, as gw_g0w0. */
+gw_status gw_g0w0_qset(gw_plan plan, int32_t sys, const int32_t* q_list, int32_t n_q, gw_complex* sigma_acc);
 
 /* gw_g0w0 for every system of a batch plan: the systems' q loops run concurrently, each on its
  * own stream, driven by n_threads host threads (0: min(n_sys, 8)), so that small systems

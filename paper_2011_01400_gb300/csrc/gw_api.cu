@@ -262,6 +262,10 @@ struct gw_plan_s {
   int n_bpl = 0;
   int seg_rows = 2048;        // pair rows per FP64 promotion segment of the tensor-core chi0
   float* d_wtab = nullptr;    // [nw][ldm] Lorentzian weights
+  unsigned* d_absmax = nullptr;  // largest |re|, |im| of the chi0 M plane (float bits)
+  int* d_eB = nullptr;        // FP16: exponent of the B plane scale
+  double* d_escale = nullptr; // [nw] factors of the drained chi0 sums
+  Chi0Plan* chi0plan = nullptr;   // work lists of the tcgen05 chi0 kernel
   // frequency compression of the split-precision chi0 (k_compress.cu)
   // largest relative residual |W_j - sum_{t<T} E_jt v_t| / |W_j| over the frequencies j that the
   // compression may leave (computed in FP64 over all pair rows); 0 disables. 3e-8 is below the
@@ -271,7 +275,8 @@ struct gw_plan_s {
   double* d_wlam = nullptr;   // [NK][nw]
   double *d_wn = nullptr, *d_wE = nullptr, *d_wP = nullptr, *d_werr = nullptr;  // [NK][nw], [NK][nw][nw] x2,
                                                                                // [NK][nw][nw+1]
-  int comp_q0 = -1, comp_nq = 0, comp_nw = 0;  // q range (and grid size) whose weight spectra are ready
+  std::vector<int> comp_qs;   // q points (in order) whose weight spectra are ready
+  int comp_nw = 0;            // grid size they were computed for
   std::vector<int> comp_T;    // components kept per q of that range
   int last_T = 0;             // components kept for the last q
   int Kx = 0;                 // n_aux rounded up to 32 (K of the Sigma contraction)
@@ -451,7 +456,8 @@ gw_status validate(const gw_problem* p, int n_sys) {
   if (p->sigma_lo < 0 || p->sigma_hi > p->n_bands || p->sigma_lo >= p->sigma_hi)
     return fail(GW_ERR_ARG, "sigma window must satisfy 0 <= lo < hi <= n_bands");
   if (!(p->spin > 0.0)) return fail(GW_ERR_ARG, "spin must be > 0");
-  if (p->prec != GW_FP64 && p->prec != GW_3XTF32 && p->prec != GW_3XBF16) return fail(GW_ERR_ARG, "bad precision");
+  if (p->prec != GW_FP64 && p->prec != GW_3XTF32 && p->prec != GW_3XBF16 && p->prec != GW_3XFP16)
+    return fail(GW_ERR_ARG, "bad precision");
   for (int i = 0; i < p->n_basis; ++i) {
     if (p->basis_atom[i] < 0 || p->basis_atom[i] >= p->n_atoms) return fail(GW_ERR_ARG, "basis_atom out of range");
     if (i && p->basis_atom[i] < p->basis_atom[i - 1]) return fail(GW_ERR_ARG, "basis_atom must be non-decreasing");
@@ -710,7 +716,10 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
   if (!P->fp64) {
     const size_t pe = (size_t)N * 2 * P->ldm * (P->prec == GW_3XTF32 ? 4 : 2);
     ALLOC(P->d_Praw, (size_t)N * 2 * P->ldm);
-    P->n_bpl = P->prec == GW_3XTF32 ? 4 : 6;
+    P->n_bpl = P->prec == GW_3XBF16 ? 3 : 2;
+    ALLOC(P->d_absmax, 1);
+    ALLOC(P->d_eB, 1);
+    ALLOC(P->d_escale, (size_t)nw);
     for (int i = 0; i < P->n_bpl; ++i) {
       uint8_t* pp;
       ALLOC(pp, pe);
@@ -812,6 +821,7 @@ gw_status gw_plan_destroy(gw_plan P) {
   if (P->st) cudaStreamSynchronize(P->st);
   else cudaDeviceSynchronize();
   for (void* a : P->allocs) cudaFree(a);
+  if (P->chi0plan) chi0_plan_free(P->chi0plan);
   if (P->ev0) cudaEventDestroy(P->ev0);
   if (P->ev1) cudaEventDestroy(P->ev1);
   for (auto& e : P->evs) {
@@ -866,7 +876,7 @@ bool compress_on(const gw_plan_s* P) {
 // Jacobi), the expansion / projection matrices, and T_q = the smallest number of components whose
 // per-frequency residual (computed directly over all pair rows) is within compress_tol for every
 // frequency. One host synchronisation per call.
-gw_status chi0_prepare(gw_plan_s* P, int q0, int nq) {
+gw_status chi0_prepare(gw_plan_s* P, const int* qs, int nq) {
   if (!compress_on(P)) return GW_OK;
   cudaStream_t st = P->st;
   const int nw = P->nw, na = P->nunocc, nb = P->nocc;
@@ -875,7 +885,7 @@ gw_status chi0_prepare(gw_plan_s* P, int q0, int nq) {
   for (int j = 0; j < nq; ++j) {
     for (int kk0 = 0; kk0 < P->NK; kk0 += P->chi_nkk) {
       const int nkk = std::min(P->chi_nkk, P->NK - kk0);
-      launch_pairs(P->NK, P->NBd, P->p.nk, q0 + j, kk0, nkk, P->nocc, na, 0, nb, P->p.eps, nullptr, P->p.qhat,
+      launch_pairs(P->NK, P->NBd, P->p.nk, qs[j], kk0, nkk, P->nocc, na, 0, nb, P->p.eps, nullptr, P->p.qhat,
                    P->d_delta, P->d_delta_f, nullptr, st);
       launch_wgram(nkk * na * nb, nw, P->d_delta, P->d_freq, P->d_wG + j * sG, st);
     }
@@ -888,7 +898,7 @@ gw_status chi0_prepare(gw_plan_s* P, int q0, int nq) {
   for (int j = 0; j < nq; ++j) {
     for (int kk0 = 0; kk0 < P->NK; kk0 += P->chi_nkk) {
       const int nkk = std::min(P->chi_nkk, P->NK - kk0);
-      launch_pairs(P->NK, P->NBd, P->p.nk, q0 + j, kk0, nkk, P->nocc, na, 0, nb, P->p.eps, nullptr, P->p.qhat,
+      launch_pairs(P->NK, P->NBd, P->p.nk, qs[j], kk0, nkk, P->nocc, na, 0, nb, P->p.eps, nullptr, P->p.qhat,
                    P->d_delta, P->d_delta_f, nullptr, st);
       launch_wresid(nkk * na * nb, nw, P->d_delta, P->d_freq, P->d_wE + j * sG, P->d_wP + j * sG, P->d_werr + j * sE,
                     st);
@@ -912,8 +922,7 @@ gw_status chi0_prepare(gw_plan_s* P, int q0, int nq) {
       }
     }
   }
-  P->comp_q0 = q0;
-  P->comp_nq = nq;
+  P->comp_qs.assign(qs, qs + nq);
   P->comp_nw = nw;
   return check_launch(P, "chi0 weight spectra");
 }
@@ -935,12 +944,17 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
   const int na = P->nunocc, nb = P->nocc;
   // frequency compression (split precision): chi0(w_j) = sum_t U_jt C_t over T <= nw weight rows
   const bool comp = compress_on(P);
+  int jq = 0;                 // position of q in the list of prepared weight bases
   int T = nw;
   const double* Uw = nullptr;
   if (comp) {
-    if (q < P->comp_q0 || q >= P->comp_q0 + P->comp_nq || P->comp_nw != nw) GW_TRY(chi0_prepare(P, q, 1));
-    T = P->comp_T[q - P->comp_q0];
-    Uw = P->d_wE + (long long)(q - P->comp_q0) * nw * nw;
+    jq = (int)(std::find(P->comp_qs.begin(), P->comp_qs.end(), q) - P->comp_qs.begin());
+    if (jq == (int)P->comp_qs.size() || P->comp_nw != nw) {
+      GW_TRY(chi0_prepare(P, &q, 1));
+      jq = 0;
+    }
+    T = P->comp_T[jq];
+    Uw = P->d_wE + (long long)jq * nw * nw;
     P->last_T = T;
     GW_CUDA(cudaMemsetAsync(P->d_C, 0, sizeof(c128) * NN * T, st));
   }
@@ -963,52 +977,51 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
         launch_head_wings<double>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
                                   4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
     } else {
-      // split planes [N][2*ldm] (zero rows beyond K), then the tcgen05 contraction
-      const int tf32 = P->prec == GW_3XTF32;
-      const size_t esz = tf32 ? 4 : 2;
+      // the fp32 plane of M [N][2*ldm] (zero rows beyond K), its split pieces, then the tcgen05
+      // contraction
+      const int kind = P->prec == GW_3XFP16 ? 0 : (P->prec == GW_3XBF16 ? 1 : 2);
       if (K < P->ldm) {
-        // zero the padding pair rows K .. ldm-1 of every plane (and their transition energies)
+        // zero the padding pair rows K .. ldm-1 of the plane (and their transition energies)
         const size_t pad = (size_t)(P->ldm - K) * 2;
         GW_CUDA(cudaMemset2DAsync(P->d_Praw + 2 * (size_t)K, 2 * P->ldm * sizeof(float), 0, pad * sizeof(float), N,
                                   st));
-        for (int i = 0; i < P->n_bpl; ++i)
-          GW_CUDA(cudaMemset2DAsync(static_cast<uint8_t*>(P->d_Pb[i]) + 2 * (size_t)K * esz, 2 * P->ldm * esz, 0,
-                                    pad * esz, N, st));
         GW_CUDA(cudaMemsetAsync(P->d_delta_f + K, 0, sizeof(float) * (P->ldm - K), st));
       }
+      GW_CUDA(cudaMemsetAsync(P->d_absmax, 0, sizeof(unsigned), st));
       if (!P->mtune.run(1, na, nb, st, [&](int v) {
             launch_mgen_planes(P->geom, static_cast<const c64*>(P->d_T1), evec, q, kk0, nkk, P->nocc, na, 0, nb,
-                               P->d_Praw, P->d_Pb, 2 * P->ldm, 0, tf32, st, v);
+                               P->d_Praw, nullptr, 2 * P->ldm, 0, 0, st, v, P->d_absmax);
           }))
         return fail(GW_ERR_CUDA, "M kernel autotuner: CUDA error");
-      TcChi0Args a{};
+      Chi0hArgs a{};
+      a.kind = kind;
       a.N = N;
       a.Kpad = (int)P->ldm;
-      a.K = K;
+      a.T = comp ? T : nw;
       a.raw = P->d_Praw;
-      for (int i = 0; i < 6; ++i) a.bpl[i] = P->d_Pb[i];
-      a.delta = P->d_delta_f;
-      a.freq = P->d_freq;
-      a.nw = comp ? T : nw;
+      for (int i = 0; i < P->n_bpl; ++i) a.bpl[i] = P->d_Pb[i];
+      a.absmax = P->d_absmax;
+      a.eB = P->d_eB;
+      a.wtab = P->d_wtab;
+      a.escale = P->d_escale;
       a.scale = scale;
-      a.chi0 = comp ? P->d_C : chi0;
-      a.tf32 = tf32;
+      a.out = comp ? P->d_C : chi0;
       a.status = P->d_status;
       a.seg_rows = P->seg_rows;
-      a.wtab = P->d_wtab;
-      if (comp) {
+      cudaEvent_t ev[2] = {e0, e1};
+      a.events = ev;
+      GW_TRY(chi0h_pieces(a, st) == GW_OK ? GW_OK : fail(GW_ERR_CUDA, "chi0 operand pieces: launch failed"));
+      if (comp)
         launch_wtab_compressed(K, (int)P->ldm, nw, T, P->d_delta, P->d_freq,
-                               P->d_wP + (long long)(q - P->comp_q0) * nw * nw, P->d_wtab, st);
-        a.wtab_ready = 1;
-      }
+                               P->d_wP + (long long)jq * nw * nw, P->d_wtab, st);
+      else
+        chi0h_weights(K, (int)P->ldm, nw, P->d_delta_f, P->d_freq, P->d_wtab, st);
       std::string err;
-      GW_CUDA(cudaEventRecord(e0, st));
-      gw_status ts = tc_chi0_run(a, P->tcws, st, err);
+      gw_status ts = chi0h_run(a, &P->chi0plan, st, err);
       if (ts != GW_OK) {
         P->err = 1;
         return fail(ts, err);
       }
-      GW_CUDA(cudaEventRecord(e1, st));
       if (hw) {
         c64* M = static_cast<c64*>(P->d_M);
         if (!P->mtune.run(0, na, nb, st, [&](int v) {
@@ -1156,6 +1169,31 @@ gw_status ensure_groups(gw_plan_s* P) {
   return GW_OK;
 }
 
+// The q loop of gw_g0w0 over the listed q points: groups of up to qb points whose FP64
+// factorisations of eps~ run as one batched launch; Sigma_c terms accumulated into sig.
+gw_status g0w0_qlist(gw_plan_s* P, const std::vector<int>& qs, c128* sig) {
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw;
+  const long long NN = (long long)N * N;
+  const long long slot = NN * nw;
+  P->reset_timing();
+  for (size_t g0 = 0; g0 < qs.size(); g0 += P->qb) {
+    const int nq = (int)std::min<size_t>(P->qb, qs.size() - g0);
+    const int* q = qs.data() + g0;
+    GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+    GW_TRY(chi0_prepare(P, q, nq));
+    for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q[j], P->g_chi0 + j * slot));
+    for (int j = 0; j < nq; ++j) GW_TRY(eps_core(P, q[j], P->g_chi0 + j * slot, P->g_E + j * slot));
+    launch_chol_inv_minus_I(N, P->g_E, nq * nw, NN, P->g_work, P->d_status, st);
+    for (int j = 0; j < nq; ++j) GW_TRY(w_core(P, q[j], P->g_E + j * slot, P->g_chi0 + j * slot));
+    for (int j = 0; j < nq; ++j) GW_TRY(sigma_core(P, q[j], P->g_chi0 + j * slot, sig));
+    GW_TRY(read_status(P, "gw_g0w0"));
+  }
+  GW_TRY(P->collect_timing());
+  P->chi0_q = P->wc_q = -1;
+  return GW_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1223,23 +1261,28 @@ gw_status gw_g0w0(gw_plan P, int32_t sys, gw_complex* sigma_acc) {
   const long long slot = NN * nw;
   GW_TRY(ensure_groups(P));
   c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
-  P->reset_timing();
-  for (int q0 = 0; q0 < P->NK; q0 += P->qb) {
-    const int nq = std::min(P->qb, P->NK - q0);
-    GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
-    GW_TRY(chi0_prepare(P, q0, nq));
-    for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q0 + j, P->g_chi0 + j * slot));
-    for (int j = 0; j < nq; ++j) GW_TRY(eps_core(P, q0 + j, P->g_chi0 + j * slot, P->g_E + j * slot));
-    launch_chol_inv_minus_I(N, P->g_E, nq * nw, NN, P->g_work, P->d_status, st);
-    for (int j = 0; j < nq; ++j) GW_TRY(w_core(P, q0 + j, P->g_E + j * slot, P->g_chi0 + j * slot));
-    for (int j = 0; j < nq; ++j) GW_TRY(sigma_core(P, q0 + j, P->g_chi0 + j * slot, sig));
-    GW_TRY(read_status(P, "gw_g0w0"));
-  }
-  GW_TRY(P->collect_timing());
-  P->chi0_q = P->wc_q = -1;
-  return GW_OK;
+  std::vector<int> qs(P->NK);
+  for (int q = 0; q < P->NK; ++q) qs[q] = q;
+  return g0w0_qlist(P, qs, sig);
 }
 
+gw_status gw_g0w0_qset(gw_plan P, int32_t sys, const int32_t* q_list, int32_t n_q, gw_complex* sigma_acc) {
+  gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (n_q < 0 || (n_q > 0 && !q_list)) return fail(GW_ERR_ARG, "q_list is NULL or n_q < 0");
+  if (!sigma_acc) return fail(GW_ERR_ARG, "sigma_acc is NULL");
+  if (P->sur.on && P->sur.model) return fail(GW_ERR_UNSUPPORTED, "gw_g0w0_qset: a surrogate is attached");
+  std::vector<int> qs(q_list, q_list + n_q);
+  std::vector<char> seen(P->NK, 0);
+  for (int q : qs) {
+    if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "gw_g0w0_qset: q out of range");
+    if (seen[q]++) return fail(GW_ERR_ARG, "gw_g0w0_qset: q listed twice");
+  }
+  GW_TRY(ensure_groups(P));
+  return g0w0_qlist(P, qs, reinterpret_cast<c128*>(sigma_acc));
+}
 
 gw_status gw_qp(gw_plan P, int32_t sys, const gw_complex* sigma, const double* dxv, double* e_qp, double* gap,
                 int32_t* n_conv) {
@@ -1589,7 +1632,9 @@ gw_status g0w0_sur(gw_plan_s* P, c128* sig) {
     GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
     {
       FreqView fv(P, nc, S.d_freq_c);
-      GW_TRY(chi0_prepare(P, q0, nq));
+      std::vector<int> qg(nq);
+      for (int j = 0; j < nq; ++j) qg[j] = q0 + j;
+      GW_TRY(chi0_prepare(P, qg.data(), nq));
       for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q0 + j, S.g_chi0 + j * slot));
       for (int j = 0; j < nq; ++j) {
         GW_TRY(eps_core(P, q0 + j, S.g_chi0 + j * slot, S.g_E + j * slot));
@@ -1746,7 +1791,9 @@ gw_status gw_surrogate_data(gw_plan P, int32_t sys, float* x_out, float* y_out, 
   for (int q0 = 0; q0 < P->NK; q0 += P->qb) {
     const int nq = std::min(P->qb, P->NK - q0);
     GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
-    GW_TRY(chi0_prepare(P, q0, nq));
+    std::vector<int> qg(nq);
+    for (int j = 0; j < nq; ++j) qg[j] = q0 + j;
+    GW_TRY(chi0_prepare(P, qg.data(), nq));
     for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q0 + j, P->g_chi0 + j * slot));
     for (int j = 0; j < nq; ++j) {
       GW_TRY(eps_core(P, q0 + j, P->g_chi0 + j * slot, P->g_E + j * slot));

@@ -75,9 +75,11 @@ void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* T2, const c
                  long long s_mu, cudaStream_t st, int variant = 0);
 // split planes for the tensor-core chi0 B operand: for row mu, K index 2r + {0: re, 1: im}
 // raw fp32 plane + B1/B2 split planes (3 BF16 pieces or 2 TF32 pieces each), see k_lri.cu
+// bplanes may be NULL (raw plane only); absmax (may be NULL) receives max |re|, |im| of the rows
+// written, as float bits (atomicMax; the caller zeroes it)
 void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
                         int b0, int nb, float* raw, void* const* bplanes, long long ldk, long long kofs, int tf32,
-                        cudaStream_t st, int variant = 0);
+                        cudaStream_t st, int variant = 0, unsigned* absmax = nullptr);
 
 // k_linalg.cu
 template <typename T>
@@ -173,6 +175,29 @@ gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, s
 void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st);
 bool tc_available();
 void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st);
+
+// k_chi0.cu -- tcgen05 chi0 with Re / Im rows stacked on the M side (all split precisions)
+struct Chi0hArgs {
+  int kind;                 // 0: FP16 two pieces (scaled), 1: BF16 three pieces, 2: TF32 two pieces
+  int N, Kpad, T;           // n_aux, padded pair rows (multiple of 32), weight rows
+  const float* raw;         // [N][2*Kpad] fp32 (re, im) of M
+  void* bpl[3];             // B pieces [N][2*Kpad] (written by chi0h_pieces)
+  const unsigned* absmax;   // largest |re|, |im| of raw (float bits)
+  int* eB;                  // FP16: exponent of the B plane scale (device)
+  float* wtab;              // [T][Kpad] weight rows (FP16: multiplied in place by their scales)
+  double* escale;           // [T] device: factor of the drained sums
+  double scale;             // -(s / N_k)
+  c128* out;                // [T][N][N], lower triangle accumulated (caller zeroes it)
+  int* status;
+  int seg_rows;             // pair rows per FP64 promotion segment
+  cudaEvent_t* events;      // NULL or two events recorded around the contraction launch
+};
+struct Chi0Plan;
+void chi0_plan_free(Chi0Plan* p);
+gw_status chi0h_pieces(const Chi0hArgs& a, cudaStream_t st);
+gw_status chi0h_run(const Chi0hArgs& a, Chi0Plan** plan, cudaStream_t st, std::string& err);
+// wtab[j][r] = 2 D_r / (w_j^2 + D_r^2) (0 for padding rows r >= K)
+void chi0h_weights(int K, int Kpad, int nw, const float* delta, const double* freq, float* wtab, cudaStream_t st);
 
 // Ritz modes and the surrogate reconstruction (k_modes.cu); small sizes nb <= 64
 void launch_small_chol_linv(int nb, int batch, const c128* G, c128* Linv, int* status, cudaStream_t st);

@@ -98,6 +98,7 @@ void launch_lri_halfT<float>(const LriGeom& g, const double* ctil, const c128* e
   long long amax = 0;
   for (int A = 0; A < g.n_atoms; ++A) amax = std::max(amax, (long long)g.atom_nx[A] * g.atom_nb[A] * g.NB);
   c64 *cR = nullptr, *At = nullptr;
+  ::gw::g_alloc_count += 2;
   if (cudaMallocAsync(&cR, sizeof(c64) * per_k * g.NK, st) != cudaSuccess ||
       cudaMallocAsync(&At, sizeof(c64) * amax, st) != cudaSuccess) {
     // fall back to the direct kernel (same sums, FP64 arithmetic) when the staging does not fit
@@ -397,15 +398,19 @@ __device__ __forceinline__ float tf32_round(float x) {
 
 struct PlanePtrs {
   float* raw;
-  void* b[6];      // B1 pieces then B2 pieces
+  void* b[6];      // B1 pieces then B2 pieces (b[0] NULL: raw plane only)
+  unsigned* absmax;
 };
 
 template <bool SMEM, bool PAIR>
 __global__ void __launch_bounds__(MGEN_SMEM_THREADS) k_mgen_planes(const __grid_constant__ LriGeom g, const c64* __restrict__ T1, const c128* __restrict__ evec, int q, int kk0, int a0,
                               int na, int b0, int nb, PlanePtrs P, long long ldk, long long kofs, int tf32) {
+  float amax = 0.f;
   auto st = [&](long long r, int mu, float re, float im) {
     const long long e = (long long)mu * ldk + kofs + 2 * r;
     *reinterpret_cast<float2*>(P.raw + e) = make_float2(re, im);
+    amax = fmaxf(amax, fmaxf(fabsf(re), fabsf(im)));
+    if (!P.b[0]) return;
     const float v1[2] = {re, im}, v2[2] = {-im, re};
     if (tf32) {
       for (int half = 0; half < 2; ++half) {
@@ -434,14 +439,22 @@ __global__ void __launch_bounds__(MGEN_SMEM_THREADS) k_mgen_planes(const __grid_
     mgen_smem_body<PAIR>(g, T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
   else
     mgen_body<float>(g, T1, evec, q, kk0, MAP_K_IS_KK, a0, na, b0, nb, st);
+  if (P.absmax) {
+    // every thread of the block gets here (block sizes are multiples of 32); non-negative
+    // floats order like their bit patterns
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+    if ((threadIdx.x & 31) == 0) atomicMax(P.absmax, m);
+  }
 }
 
 void launch_mgen_planes(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
                         int b0, int nb, float* raw, void* const* bplanes, long long ldk, long long kofs, int tf32,
-                        cudaStream_t st, int variant) {
+                        cudaStream_t st, int variant, unsigned* absmax) {
   PlanePtrs P{};
   P.raw = raw;
-  for (int i = 0; i < (tf32 ? 4 : 6); ++i) P.b[i] = bplanes[i];
+  P.absmax = absmax;
+  if (bplanes)
+    for (int i = 0; i < (tf32 ? 4 : 6); ++i) P.b[i] = bplanes[i];
   const size_t sm = mgen_smem(g, na, nb);
   if (sm <= 200 * 1024) {
     dim3 grid(nkk, mgen_tiles(g));

@@ -17,11 +17,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgw.so")
 
 GW_OK, GW_ERR_ARG, GW_ERR_NOMEM, GW_ERR_CUDA, GW_ERR_NOT_PD, GW_ERR_TIMEOUT, GW_ERR_STATE, GW_ERR_UNSUPPORTED = range(8)
-GW_FP64, GW_3XTF32, GW_3XBF16 = 0, 1, 2
-PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16}
+GW_FP64, GW_3XTF32, GW_3XBF16, GW_3XFP16 = 0, 1, 2, 3
+PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16, "3xfp16": GW_3XFP16}
 
 # every symbol include/gw.h declares
-EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_sigma_x", "gw_g0w0",
+EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_sigma_x", "gw_g0w0", "gw_g0w0_qset",
            "gw_g0w0_batch",
            "gw_plan_n_sys", "gw_qp",
            "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_plan_chi0_terms", "gw_kernel_launches",
@@ -92,6 +92,7 @@ def load():
     lib.gw_screen.argtypes = [vp, i32, i32, vp]
     lib.gw_sigma.argtypes = [vp, i32, i32, vp]
     lib.gw_g0w0.argtypes = [vp, i32, vp]
+    lib.gw_g0w0_qset.argtypes = [vp, i32, ctypes.POINTER(i32), i32, vp]
     lib.gw_sigma_x.argtypes = [vp, i32, vp]
     lib.gw_g0w0_batch.argtypes = [vp, ctypes.POINTER(vp), i32]
     lib.gw_plan_n_sys.argtypes = [vp, ctypes.POINTER(i32)]
@@ -191,6 +192,13 @@ def gw_sigma_x(plan, sys, sigx):
 
 def gw_g0w0(plan, sys, sigma_acc=None):
     _check(load().gw_g0w0(plan, sys, _ptr(sigma_acc)))
+
+
+def gw_g0w0_qset(plan, sys, q_list, sigma_acc):
+    """q terms of the listed q points (host ints) accumulated into sigma_acc (device tensor)."""
+    qs = np.ascontiguousarray(np.asarray(list(q_list), dtype=np.int32))
+    _check(load().gw_g0w0_qset(plan, sys, qs.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(qs),
+                               _ptr(sigma_acc)))
 
 
 def gw_qp(plan, sys, n_k, n_sigma, sigma=None, dxv=None):

@@ -41,7 +41,7 @@ def single(gw, s, prec):
     return acc.cpu().numpy(), e, gap
 
 
-@pytest.mark.parametrize("prec,tol_same,tol_mev", [("fp64", 1e-12, 1e-6), ("3xtf32", 1e-6, 1.0), ("3xbf16", 1e-6, 1.0)])
+@pytest.mark.parametrize("prec,tol_same,tol_mev", [("fp64", 1e-12, 1e-6), ("3xtf32", 1e-6, 1.0), ("3xbf16", 1e-6, 1.0), ("3xfp16", 1e-6, 1.0)])
 def test_batch_matches_single_plans_and_oracle(prec, tol_same, tol_mev):
     from paper_2011_01400_gb300 import gw
     ss = systems()

@@ -43,7 +43,7 @@ def mesh3():
     return s, g0w0(s, "fp64")
 
 
-@pytest.mark.parametrize("prec", ["3xbf16", "3xtf32"])
+@pytest.mark.parametrize("prec", ["3xbf16", "3xtf32", "3xfp16"])
 def test_split_g0w0_matches_fp64_gpu_within_1mev(mesh3, prec):
     s, (sig64, e64, gap64, nc64) = mesh3
     nsig = s.sigma_hi - s.sigma_lo

@@ -51,7 +51,8 @@ def rel_fro(a, b):
 
 @pytest.mark.parametrize("qcase", ["cfg1_q1", "cfg1_q0"])
 @pytest.mark.parametrize("prec,tol_chi,tol_w,tol_sig_mev",
-                         [("3xbf16", 1e-6, 1e-4, 1.0), ("3xtf32", 1e-6, 1e-4, 1.0), ("fp64", 1e-11, 1e-10, 1e-6)])
+                         [("3xbf16", 1e-6, 1e-4, 1.0), ("3xtf32", 1e-6, 1e-4, 1.0), ("3xfp16", 1e-6, 1e-4, 1.0),
+                          ("fp64", 1e-11, 1e-10, 1e-6)])
 def test_cfg1_one_q_full_size(request, qcase, prec, tol_chi, tol_w, tol_sig_mev):
     """chi0 and Sigma_c hold their targets (1e-6 relative, 1 meV). W^c has none of its own: on the
     split path its screen products are FP32 (~1e-7 relative per term), and at the highest

@@ -94,7 +94,8 @@ def test_frequency_grid_and_mu_match(cfg0):
     assert abs(out["mu"] - ref["mu"]) < 1e-15
 
 
-@pytest.mark.parametrize("prec,tol_chi,tol_w", [("fp64", 1e-11, 1e-10), ("3xtf32", 1e-6, 1e-5), ("3xbf16", 1e-6, 1e-5)])
+@pytest.mark.parametrize("prec,tol_chi,tol_w", [("fp64", 1e-11, 1e-10), ("3xtf32", 1e-6, 1e-5), ("3xbf16", 1e-6, 1e-5),
+                                                ("3xfp16", 1e-6, 1e-5)])
 def test_chi0_and_wc_cfg0(cfg0, prec, tol_chi, tol_w):
     s, ref = cfg0
     out = run_gpu(s, prec, keep=True)
@@ -108,7 +109,7 @@ def test_chi0_and_wc_cfg0(cfg0, prec, tol_chi, tol_w):
     assert worst_w <= tol_w
 
 
-@pytest.mark.parametrize("prec,tol_mev", [("fp64", 1e-6), ("3xtf32", 1.0), ("3xbf16", 1.0)])
+@pytest.mark.parametrize("prec,tol_mev", [("fp64", 1e-6), ("3xtf32", 1.0), ("3xbf16", 1.0), ("3xfp16", 1.0)])
 def test_sigma_qp_gap_cfg0(cfg0, prec, tol_mev):
     s, ref = cfg0
     sig, e, gap, nconv = run_gpu_sigma(s, prec, range(s.n_k))
@@ -120,7 +121,7 @@ def test_sigma_qp_gap_cfg0(cfg0, prec, tol_mev):
     assert err_sig <= tol_mev and err_e <= tol_mev and err_gap <= tol_mev
 
 
-@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "3xbf16"])
+@pytest.mark.parametrize("prec", ["fp64", "3xtf32", "3xbf16", "3xfp16"])
 def test_g0w0_driver_matches_per_q_calls(cfg0, prec):
     """gw_g0w0 (q groups, batched FP64 factorisations) gives the per-q result and the oracle's."""
     from paper_2011_01400_gb300 import gw
