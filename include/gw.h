@@ -94,7 +94,11 @@ typedef struct {
                                     may be NULL when head_wings == 0                          */
   double omega_cell;             /* unit-cell volume (bohr^3), > 0 when head_wings != 0      */
   double qhat[3];                /* direction of q -> 0 for the head and wings               */
-  int32_t head_wings;            /* 1: Gamma point by Eq. dielectric_func_gamma; 0: regular  */
+  int32_t head_wings;            /* 1: Gamma point by Eq. dielectric_func_gamma along qhat;
+                                    2: the same with eps~^-1 - 1 averaged over the direction
+                                    of q -> 0 (128-point product rule on the sphere: 8 Gauss-
+                                    Legendre nodes in cos(theta) x 16 equally spaced phi,
+                                    offset by half a step; qhat unused); 0: regular formula */
   int32_t n_freq;                /* imaginary frequencies, modified Gauss-Legendre, 1..256   */
   double omega0;                 /* grid scale: w_j = omega0 (1+x_j)/(1-x_j) (Ha), > 0       */
   int32_t sigma_lo, sigma_hi;    /* self-energy bands [sigma_lo, sigma_hi), 0-based          */

@@ -222,13 +222,38 @@ def hsqrt(V):
 
 
 def coulomb_eig_q0(V0):
-    """Sec. III (Gamma point): eigenpairs of V^cut(q=0), lambda = 1 first (largest)."""
+    """Sec. III (Gamma point): eigenpairs of V^cut(q=0), lambda = 1 first (largest).
+
+    reading: the wings of Eq. dielectric_func_gamma change sign with the lambda = 1 eigenvector.
+    In the paper that vector is the G = 0 plane wave, the positive constant 1/sqrt(Omega), so
+    its sign is fixed by physics; synthetic inputs have no such function, so its phase is fixed
+    by convention: the largest-magnitude component (the first one on a tie) real and positive.
+    """
     lam, X = np.linalg.eigh(V0)
     order = np.argsort(lam)[::-1]
-    return lam[order], X[:, order]
+    lam, X = lam[order], X[:, order].copy()
+    i = int(np.argmax(np.abs(X[:, 0])))
+    X[:, 0] *= np.conj(X[i, 0]) / abs(X[i, 0])
+    return lam, X
 
 
-def head_wings_q0(sys, omegas, chi0_0):
+def sphere_rule(n_theta=8, n_phi=16):
+    """Product quadrature on the unit sphere for averages over the direction of q -> 0: Gauss-
+    Legendre nodes in cos(theta) times equally spaced phi (offset by half a step). Weights sum to
+    one; the point set is symmetric under q^ -> -q^, so odd moments vanish exactly.
+    Returns (directions [n, 3], weights [n])."""
+    u, wu = np.polynomial.legendre.leggauss(n_theta)
+    phi = 2.0 * np.pi * (np.arange(n_phi) + 0.5) / n_phi
+    dirs, wts = [], []
+    for ui, wi in zip(u, wu):
+        st = np.sqrt(1.0 - ui * ui)
+        for p in phi:
+            dirs.append((st * np.cos(p), st * np.sin(p), ui))
+            wts.append(wi / 2.0 / n_phi)
+    return np.array(dirs), np.array(wts)
+
+
+def head_wings_q0(sys, omegas, chi0_0, qhat=None):
     """Eq. (dielectric_func_gamma) in the Coulomb eigenbasis, insulator case.
 
     Returns eps_X[w] (matrix in the lambda basis, lambda=1 first) and X, v.
@@ -249,7 +274,7 @@ def head_wings_q0(sys, omegas, chi0_0):
     sv = np.sqrt(np.clip(v, 0.0, None))
     occ = np.arange(sys.n_occ)
     unocc = np.arange(sys.n_occ, sys.n_bands)
-    qh = np.asarray(sys.qhat, dtype=np.float64)
+    qh = np.asarray(sys.qhat if qhat is None else qhat, dtype=np.float64)
     omega_tot = NK * sys.omega_cell
     nw = len(omegas)
     head = np.ones(nw)
@@ -283,7 +308,8 @@ def screen(sys, iq, chi0_q, omegas):
     reading: the correlation part W^c = W - V is what enters Sigma_c.
     At q = 0 (head_wings set) eps~ is assembled in the Coulomb eigenbasis and
     transformed back, eps~_{mu nu} = sum X_{mu l} eps~_{l l'} X*_{nu l'},
-    and W^c uses the full (truncated) V(0)^{1/2}.
+    and W^c uses the full (truncated) V(0)^{1/2}. head_wings == 2: eps~^-1 - 1 averaged over
+    the directions of q -> 0 (sphere_rule); the returned eps~ is that of sys.qhat.
     Returns (eps_tilde [w, N, N], Wc [w, N, N]).
     """
     Vh = hsqrt(sys.V[iq])
@@ -291,6 +317,22 @@ def screen(sys, iq, chi0_q, omegas):
     N = sys.n_aux
     eps_t = np.zeros((nw, N, N), dtype=np.complex128)
     Wc = np.zeros((nw, N, N), dtype=np.complex128)
+    if iq == 0 and sys.head_wings == 2:
+        # reading: for anisotropic systems the head and wings depend on the direction of q -> 0
+        # (the discussion after Eq. dielectric_func_gamma); eps~^-1 - 1 is averaged over the
+        # directions of sphere_rule(), each direction's eps~ assembled and inverted as for one q^.
+        Xbar = np.zeros((nw, N, N), dtype=np.complex128)
+        dirs, wts = sphere_rule()
+        for d, wd in zip(dirs, wts):
+            eps_X, X, v = head_wings_q0(sys, omegas, chi0_q, qhat=d)
+            for w_i in range(nw):
+                e = X @ eps_X[w_i] @ np.conj(X).T
+                Xbar[w_i] += wd * (np.linalg.inv(e) - np.eye(N))
+        eps_X, X, v = head_wings_q0(sys, omegas, chi0_q)
+        for w_i in range(nw):
+            eps_t[w_i] = X @ eps_X[w_i] @ np.conj(X).T
+            Wc[w_i] = Vh @ Xbar[w_i] @ Vh
+        return eps_t, Wc
     if iq == 0 and sys.head_wings:
         eps_X, X, v = head_wings_q0(sys, omegas, chi0_q)
         for w_i in range(nw):

@@ -241,6 +241,13 @@ struct gw_plan_s {
   c128* d_sigma = nullptr;  // [NK][nsig][nw]
   double* d_head = nullptr; // [nw]
   c128* d_h = nullptr;      // [nw][N]
+  // direction-averaged q = 0 (head_wings = 2)
+  c128* d_pq3 = nullptr;    // [3][ldm] Cartesian components of p . q^
+  double* d_A6 = nullptr;   // [nw][6] head tensor
+  c128 *d_h3 = nullptr, *d_Y3 = nullptr, *d_G3 = nullptr;  // [nw][3][N] wings, y_a; [nw][N][3] g_a
+  double* d_m10 = nullptr;  // [nw][10] direction moments of the Schur complement
+  double* d_dirs = nullptr; // [n_dirs][4] direction rule (x, y, z, weight)
+  int n_dirs = 0;
   int* d_status = nullptr;
   // chunk workspaces
   int chi_nkk = 1, sig_nkk = 1;
@@ -449,6 +456,7 @@ gw_status validate(const gw_problem* p, int n_sys) {
   if (!p->basis_atom || !p->aux_atom || !p->R) return fail(GW_ERR_ARG, "basis_atom / aux_atom / R is NULL");
   if (p->n_R < 1 || p->n_R > 64) return fail(GW_ERR_ARG, "n_R out of range [1, 64]");
   if (!p->eps || !p->evec || !p->ctil_R || !p->V) return fail(GW_ERR_ARG, "a device input pointer is NULL");
+  if (p->head_wings < 0 || p->head_wings > 2) return fail(GW_ERR_ARG, "head_wings must be 0, 1 or 2");
   if (p->head_wings && (!p->pmom || !(p->omega_cell > 0.0)))
     return fail(GW_ERR_ARG, "head_wings needs pmom and omega_cell > 0");
   if (p->n_freq < 1 || p->n_freq > 256) return fail(GW_ERR_ARG, "n_freq out of range [1, 256]");
@@ -742,6 +750,27 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
   ALLOC(P->d_delta, P->ldm);
   ALLOC(P->d_delta_f, P->ldm);
   ALLOC(P->d_pq, P->ldm);
+  if (prob->head_wings == 2) {
+    ALLOC(P->d_pq3, 3 * (size_t)P->ldm);
+    ALLOC(P->d_A6, (size_t)nw * 6);
+    ALLOC(P->d_h3, (size_t)nw * 3 * N);
+    ALLOC(P->d_Y3, (size_t)nw * 3 * N);
+    ALLOC(P->d_G3, (size_t)nw * 3 * N);
+    ALLOC(P->d_m10, (size_t)nw * 10);
+    // direction rule: 8 Gauss-Legendre nodes in cos(theta) x 16 equally spaced phi (half-step
+    // offset), weights summing to one; symmetric under q^ -> -q^
+    std::vector<double> u, wu, rule;
+    gauss_legendre(8, u, wu);
+    for (int i = 0; i < 8; ++i)
+      for (int j = 0; j < 16; ++j) {
+        const double ph = 2.0 * M_PI * (j + 0.5) / 16.0, st = std::sqrt(1.0 - u[i] * u[i]);
+        rule.insert(rule.end(), {st * std::cos(ph), st * std::sin(ph), u[i], wu[i] / 2.0 / 16.0});
+      }
+    P->n_dirs = 128;
+    ALLOC(P->d_dirs, rule.size());
+    if (cudaMemcpy(P->d_dirs, rule.data(), sizeof(double) * rule.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup(fail(GW_ERR_CUDA, "direction rule upload failed"));
+  }
 #undef ALLOC
   if (cudaEventCreate(&P->ev0) != cudaSuccess || cudaEventCreate(&P->ev1) != cudaSuccess)
     return cleanup(fail(GW_ERR_CUDA, "cudaEventCreate failed"));
@@ -934,12 +963,26 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
   const c128* evec = reinterpret_cast<const c128*>(P->p.evec);
   GW_CUDA(cudaMemsetAsync(chi0, 0, sizeof(c128) * NN * nw, st));
   const bool hw = P->p.head_wings && q == 0;
+  const bool hw_avg = hw && P->p.head_wings == 2;
   if (hw) {
     std::vector<double> ones(nw, 1.0);
     GW_CUDA(cudaMemcpyAsync(P->d_head, ones.data(), nw * sizeof(double), cudaMemcpyHostToDevice, st));
     GW_CUDA(cudaStreamSynchronize(st));
     GW_CUDA(cudaMemsetAsync(P->d_h, 0, sizeof(c128) * nw * N, st));
   }
+  if (hw_avg) {
+    GW_CUDA(cudaMemsetAsync(P->d_A6, 0, sizeof(double) * nw * 6, st));
+    GW_CUDA(cudaMemsetAsync(P->d_h3, 0, sizeof(c128) * nw * 3 * N, st));
+  }
+  // Cartesian p . e_a tables of the chunk (direction-averaged q = 0)
+  auto pairs3 = [&](int kk0, int nkk) {
+    for (int a = 0; a < 3; ++a) {
+      const double e[3] = {a == 0 ? 1.0 : 0.0, a == 1 ? 1.0 : 0.0, a == 2 ? 1.0 : 0.0};
+      launch_pairs(P->NK, P->NBd, P->p.nk, q, kk0, nkk, P->nocc, P->nunocc, 0, P->nocc, P->p.eps,
+                   reinterpret_cast<const c128*>(P->p.pmom), e, nullptr, nullptr, P->d_pq3 + a * P->ldm, st);
+    }
+  };
+  const double hw_pref = 4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK);
   const double scale = -P->p.spin / P->NK;
   const int na = P->nunocc, nb = P->nocc;
   // frequency compression (split precision): chi0(w_j) = sum_t U_jt C_t over T <= nw weight rows
@@ -974,8 +1017,13 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
       launch_chi0_simt<double>(N, K, M, P->ldm, nullptr, P->d_delta, P->d_freq, nw, scale, chi0, st);
       GW_CUDA(cudaEventRecord(e1, st));
       if (hw)
-        launch_head_wings<double>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
-                                  4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
+        launch_head_wings<double>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw, hw_pref, P->d_head, P->d_h,
+                                  st);
+      if (hw_avg) {
+        pairs3(kk0, nkk);
+        launch_head_wings3<double>(N, K, M, P->ldm, P->d_delta, P->d_pq3, P->ldm, P->d_freq, nw, hw_pref, P->d_A6,
+                                   P->d_h3, st);
+      }
     } else {
       // the fp32 plane of M [N][2*ldm] (zero rows beyond K), its split pieces, then the tcgen05
       // contraction
@@ -1029,8 +1077,13 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
                                  P->nocc, na, 0, nb, M, 1, P->ldm, st, v);
             }))
           return fail(GW_ERR_CUDA, "M kernel autotuner: CUDA error");
-        launch_head_wings<float>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw,
-                                 4.0 * M_PI * P->p.spin / (P->p.omega_cell * P->NK), P->d_head, P->d_h, st);
+        launch_head_wings<float>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw, hw_pref, P->d_head, P->d_h,
+                                 st);
+        if (hw_avg) {
+          pairs3(kk0, nkk);
+          launch_head_wings3<float>(N, K, M, P->ldm, P->d_delta, P->d_pq3, P->ldm, P->d_freq, nw, hw_pref, P->d_A6,
+                                    P->d_h3, st);
+        }
       }
     }
     GW_TRY(check_launch(P, "chi0"));
@@ -1066,13 +1119,35 @@ gw_status eps_core(gw_plan_s* P, int q, const c128* chi0, c128* E) {
     launch_convert_back((int)(NN * nw), C32, E, st);
   }
   launch_axpby_identity<double>(N, E, NN, nw, 1.0, st);
-  if (hw) {
+  if (hw && P->p.head_wings == 1) {
     // Vbh[w] = Vb0 h[w], then the rank-2 head / wing correction
     launch_zgemm<double>(nw, N, N, one, P->d_h, N, 0, OP_N, P->d_Vb0, N, 0, OP_T, zero, P->d_tmp, N, 0, 1, st);
     const double c = (P->p.spin / P->NK) * std::sqrt(4.0 * M_PI / P->p.omega_cell);
     launch_q0_correction(N, nw, E, P->d_x1, P->d_tmp, P->d_head, c, st);
   }
   return check_launch(P, "eps~");
+}
+
+// Direction-averaged q = 0 (head_wings = 2; reading: the head and wings of Eq.
+// dielectric_func_gamma depend on the direction of q -> 0, and eps~^-1 - 1 is averaged over the
+// directions of a sphere rule). X holds G - 1 on entry, G the inverse of the body
+// eps~_b = 1 - Vb0 chi0 Vb0 (x1 is its eigenvector with eigenvalue 1). For a direction q^ the wing
+// column is y(q^) = sum_a q_a y_a, y_a = -c Vb0 h_a, and the head 1 + q^T A q^; the Schur complement
+// s = 1 + q^T (A - Re Gamma) q^, Gamma_ab = y_a^H G y_b, gives
+//   eps~(q^)^-1 - 1 = (G - 1) + (1/s - 1) x1 x1^H - (x1 g^H + g x1^H)/s + g g^H/s,  g = G y(q^),
+// whose average over the rule needs only <1/s>, <q_a/s> and <q_a q_b/s> (k_q0avg_moments).
+gw_status q0_average(gw_plan_s* P, c128* X) {
+  cudaStream_t st = P->st;
+  const int N = P->N, nw = P->nw;
+  const long long NN = (long long)N * N;
+  const double c = (P->p.spin / P->NK) * std::sqrt(4.0 * M_PI / P->p.omega_cell);
+  launch_zgemm<double>(3 * nw, N, N, c128{-c, 0}, P->d_h3, N, 0, OP_N, P->d_Vb0, N, 0, OP_T, c128{0, 0}, P->d_Y3, N,
+                       0, 1, st);
+  launch_zgemm<double>(N, 3, N, c128{1, 0}, X, N, NN, OP_N, P->d_Y3, N, 3LL * N, OP_T, c128{0, 0}, P->d_G3, 3,
+                       3LL * N, nw, st);
+  launch_q0avg_moments(N, nw, P->d_Y3, P->d_G3, P->d_A6, P->d_dirs, P->n_dirs, P->d_m10, P->d_status, st);
+  launch_q0avg_update(N, nw, X, NN, P->d_x1, P->d_G3, P->d_m10, st);
+  return check_launch(P, "q = 0 direction average");
 }
 
 // W^c(q) = V^1/2 X V^1/2 with X = eps~^-1 - 1 ([nw][N][N], FP64 in and out)
@@ -1185,6 +1260,8 @@ gw_status g0w0_qlist(gw_plan_s* P, const std::vector<int>& qs, c128* sig) {
     for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q[j], P->g_chi0 + j * slot));
     for (int j = 0; j < nq; ++j) GW_TRY(eps_core(P, q[j], P->g_chi0 + j * slot, P->g_E + j * slot));
     launch_chol_inv_minus_I(N, P->g_E, nq * nw, NN, P->g_work, P->d_status, st);
+    for (int j = 0; j < nq; ++j)
+      if (q[j] == 0 && P->p.head_wings == 2) GW_TRY(q0_average(P, P->g_E + j * slot));
     for (int j = 0; j < nq; ++j) GW_TRY(w_core(P, q[j], P->g_E + j * slot, P->g_chi0 + j * slot));
     for (int j = 0; j < nq; ++j) GW_TRY(sigma_core(P, q[j], P->g_chi0 + j * slot, sig));
     GW_TRY(read_status(P, "gw_g0w0"));
@@ -1229,6 +1306,7 @@ gw_status gw_screen(gw_plan P, int32_t sys, int32_t q, gw_complex* wc_out) {
   GW_TRY(eps_core(P, q, P->d_chi0, P->d_E));
   GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
   launch_chol_inv_minus_I(P->N, P->d_E, P->nw, NN, P->d_work, P->d_status, st);
+  if (q == 0 && P->p.head_wings == 2) GW_TRY(q0_average(P, P->d_E));
   GW_TRY(w_core(P, q, P->d_E, P->d_Wc));
   GW_TRY(read_status(P, "gw_screen"));
   if (wc_out) GW_CUDA(cudaMemcpyAsync(wc_out, P->d_Wc, sizeof(c128) * NN * P->nw, cudaMemcpyDeviceToDevice, st));
@@ -1667,6 +1745,8 @@ gw_status gw_surrogate_enable(gw_plan P, gw_surrogate model, const gw_surrogate_
   gw_status s;
   if (P && !P->subs.empty()) return fail(GW_ERR_UNSUPPORTED, "gw_surrogate_enable: not on a batch plan");
   if (!plan_ok(P, 0, &s)) return s;
+  if (P->p.head_wings == 2 && cfg)
+    return fail(GW_ERR_UNSUPPORTED, "gw_surrogate_enable: not with the direction-averaged q = 0 (head_wings = 2)");
   SurState& S = P->sur;
   if (!cfg) {
     if (model) return fail(GW_ERR_ARG, "gw_surrogate_enable: a model needs a configuration");

@@ -104,6 +104,16 @@ void launch_rank1(int N, c128* A, const c128* x, double alpha, cudaStream_t st);
 template <typename T>
 void launch_head_wings(int N, int K, const cplx<T>* Mt, long long ldm, const double* delta, const c128* pq,
                        const double* freq, int nw, double head_pref, double* head, c128* h, cudaStream_t st);
+// direction-averaged q = 0 (head_wings = 2): Cartesian head tensor A6[w][6] and wings h3[w][3][N]
+// (accumulated); the moments of the Schur complement over the direction rule; the rank-4 update
+template <typename T>
+void launch_head_wings3(int N, int K, const cplx<T>* Mt, long long ldm, const double* delta, const c128* pq3,
+                        long long ldp, const double* freq, int nw, double pref, double* A6, c128* h3,
+                        cudaStream_t st);
+void launch_q0avg_moments(int N, int nw, const c128* Y, c128* G, const double* A6, const double* dirs, int nd,
+                          double* m, int* status, cudaStream_t st);
+void launch_q0avg_update(int N, int nw, c128* X, long long sX, const c128* x1, const c128* G, const double* m,
+                         cudaStream_t st);
 // pair tables: delta[r] and (p.qhat)_{ia}(k) for r = ((kk*na)+a)*nb+b
 void launch_pairs(int NK, int NBd, const int* nk, int q, int kk0, int nkk, int a0, int na, int b0, int nb,
                   const double* eps, const c128* pmom, const double* qhat, double* delta, float* delta_f,

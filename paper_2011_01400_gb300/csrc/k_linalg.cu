@@ -683,6 +683,169 @@ void launch_q0_correction(int N, int nw, c128* eps_t, const c128* x1, const c128
   ++::gw::g_launch_count, k_q0_correction<<<grid, 256, 0, st>>>(N, eps_t, x1, Vbh, head, c);
 }
 
+// Direction-averaged head and wings at q -> 0 (head_wings = 2).
+// Cartesian pieces, accumulated over pair rows (all k): the head tensor
+//   A6[w] = pref sum_r 2 Re(conj(p_a) p_b) / (D (D^2 + w^2)),  (a, b) = xx, yy, zz, xy, xz, yz,
+// and the wing vectors h3[w][a][nu] = sum_r conj(p_a,r) M^nu_r 2 / (w^2 + D^2), pq3[a][r] = p_a(k)_{ia}.
+template <typename T>
+__global__ void k_head_wings3(int N, int K, const cplx<T>* __restrict__ Mt, long long ldm,
+                              const double* __restrict__ delta, const c128* __restrict__ pq3, long long ldp,
+                              const double* __restrict__ freq, double pref, double* A6, c128* h3) {
+  __shared__ double red[32];
+  const int nu = blockIdx.x, w_i = blockIdx.y;
+  const double om = freq[w_i];
+  if (nu == N) {
+    double part[6] = {0, 0, 0, 0, 0, 0};
+    for (int r = threadIdx.x; r < K; r += blockDim.x) {
+      const double d = delta[r];
+      const double f = 2.0 / (d * (d * d + om * om));
+      const c128 px = pq3[r], py = pq3[ldp + r], pz = pq3[2 * ldp + r];
+      part[0] += f * (px.re * px.re + px.im * px.im);
+      part[1] += f * (py.re * py.re + py.im * py.im);
+      part[2] += f * (pz.re * pz.re + pz.im * pz.im);
+      part[3] += f * (px.re * py.re + px.im * py.im);
+      part[4] += f * (px.re * pz.re + px.im * pz.im);
+      part[5] += f * (py.re * pz.re + py.im * pz.im);
+    }
+    for (int c = 0; c < 6; ++c) {
+      const double sc = block_sum(part[c], red);
+      if (threadIdx.x == 0) A6[w_i * 6 + c] += pref * sc;
+    }
+    return;
+  }
+  double sr[3] = {0, 0, 0}, si[3] = {0, 0, 0};
+  for (int r = threadIdx.x; r < K; r += blockDim.x) {
+    const double d = delta[r];
+    const double wt = 2.0 / (om * om + d * d);
+    const cplx<T> m = Mt[(long long)nu * ldm + r];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const c128 pp = pq3[a * ldp + r];
+      sr[a] += wt * (pp.re * (double)m.re + pp.im * (double)m.im);
+      si[a] += wt * (pp.re * (double)m.im - pp.im * (double)m.re);
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    const double x = block_sum(sr[a], red);
+    const double y = block_sum(si[a], red);
+    if (threadIdx.x == 0) {
+      h3[((long long)w_i * 3 + a) * N + nu].re += x;
+      h3[((long long)w_i * 3 + a) * N + nu].im += y;
+    }
+  }
+}
+template <typename T>
+void launch_head_wings3(int N, int K, const cplx<T>* Mt, long long ldm, const double* delta, const c128* pq3,
+                        long long ldp, const double* freq, int nw, double pref, double* A6, c128* h3,
+                        cudaStream_t st) {
+  dim3 grid(N + 1, nw);
+  ++::gw::g_launch_count, k_head_wings3<T><<<grid, 256, 0, st>>>(N, K, Mt, ldm, delta, pq3, ldp, freq, pref, A6, h3);
+}
+template void launch_head_wings3<double>(int, int, const c128*, long long, const double*, const c128*, long long,
+                                         const double*, int, double, double*, c128*, cudaStream_t);
+template void launch_head_wings3<float>(int, int, const c64*, long long, const double*, const c128*, long long,
+                                        const double*, int, double, double*, c128*, cudaStream_t);
+
+// Per frequency w (one block): with y_a = Y[w][a][:] and g_b = y_b + Xb[w] y_b (G[w][nu][b] holds
+// Xb y_b on entry), Gamma_ab = y_a^H g_b; the quadratic form of the Schur complement
+//   s(q^) = 1 + q^T (A - Re Gamma) q,
+// averaged over the direction rule (dirs [nd][4]: x, y, z, weight):
+//   m[w] = { <1/s>, <q_a/s> (3), <q_a q_b/s> (xx, yy, zz, xy, xz, yz) }.
+// G is completed to g in place. A non-positive s sets ST_NOT_PD.
+__global__ void k_q0avg_moments(int N, const c128* __restrict__ Y, c128* G, const double* __restrict__ A6,
+                                const double* __restrict__ dirs, int nd, double* m, int* status) {
+  __shared__ double red[32];
+  __shared__ double L[6];
+  const int w_i = blockIdx.x;
+  const c128* y = Y + (long long)w_i * 3 * N;
+  c128* g = G + (long long)w_i * 3 * N;
+  double gam[6] = {0, 0, 0, 0, 0, 0};
+  const int ia[6] = {0, 1, 2, 0, 0, 1}, ib[6] = {0, 1, 2, 1, 2, 2};
+  for (int nu = threadIdx.x; nu < N; nu += blockDim.x) {
+    c128 gv[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const c128 yb = y[b * N + nu];
+      gv[b] = c128{g[nu * 3 + b].re + yb.re, g[nu * 3 + b].im + yb.im};
+      g[nu * 3 + b] = gv[b];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const c128 ya = y[ia[c] * N + nu];
+      gam[c] += ya.re * gv[ib[c]].re + ya.im * gv[ib[c]].im;   // Re conj(y_a) g_b
+    }
+  }
+  for (int c = 0; c < 6; ++c) {
+    const double v = block_sum(gam[c], red);
+    if (threadIdx.x == 0) L[c] = A6[w_i * 6 + c] - v;
+  }
+  __syncthreads();
+  double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+    const double x = dirs[4 * d], yv = dirs[4 * d + 1], z = dirs[4 * d + 2], wt = dirs[4 * d + 3];
+    const double sq = 1.0 + L[0] * x * x + L[1] * yv * yv + L[2] * z * z +
+                      2.0 * (L[3] * x * yv + L[4] * x * z + L[5] * yv * z);
+    if (!(sq > 0.0)) atomicOr(status, ST_NOT_PD);
+    const double f = wt / sq;
+    acc[0] += f;
+    acc[1] += f * x;
+    acc[2] += f * yv;
+    acc[3] += f * z;
+    acc[4] += f * x * x;
+    acc[5] += f * yv * yv;
+    acc[6] += f * z * z;
+    acc[7] += f * x * yv;
+    acc[8] += f * x * z;
+    acc[9] += f * yv * z;
+  }
+  for (int c = 0; c < 10; ++c) {
+    const double v = block_sum(acc[c], red);
+    if (threadIdx.x == 0) m[w_i * 10 + c] = v;
+  }
+}
+void launch_q0avg_moments(int N, int nw, const c128* Y, c128* G, const double* A6, const double* dirs, int nd,
+                          double* m, int* status, cudaStream_t st) {
+  ++::gw::g_launch_count, k_q0avg_moments<<<nw, 256, 0, st>>>(N, Y, G, A6, dirs, nd, m, status);
+}
+
+// X[w] += (m0 - 1) x1 x1^H - sum_a m1_a (x1 g_a^H + g_a x1^H) + sum_ab m2_ab g_a g_b^H
+// (the direction average of eps~^-1 - 1 from the inverse of the body, Schur-complement form)
+__global__ void k_q0avg_update(int N, int nw, c128* X, long long sX, const c128* __restrict__ x1,
+                               const c128* __restrict__ G, const double* __restrict__ m) {
+  const int w_i = blockIdx.y;
+  const double* mm = m + w_i * 10;
+  const double m2[3][3] = {{mm[4], mm[7], mm[8]}, {mm[7], mm[5], mm[9]}, {mm[8], mm[9], mm[6]}};
+  const c128* g = G + (long long)w_i * 3 * N;
+  c128* Xw = X + (long long)w_i * sX;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)N * N;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / N), j = (int)(e % N);
+    const c128 xi = x1[i], xj = x1[j];
+    c128 v = cmulc(xi, xj);
+    v.re *= mm[0] - 1.0;
+    v.im *= mm[0] - 1.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const c128 t = cadd(cmulc(xi, g[j * 3 + a]), cmulc(g[i * 3 + a], xj));
+      v.re -= mm[1 + a] * t.re;
+      v.im -= mm[1 + a] * t.im;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const c128 u = cmulc(g[i * 3 + a], g[j * 3 + b]);
+        v.re += m2[a][b] * u.re;
+        v.im += m2[a][b] * u.im;
+      }
+    }
+    Xw[e].re += v.re;
+    Xw[e].im += v.im;
+  }
+}
+void launch_q0avg_update(int N, int nw, c128* X, long long sX, const c128* x1, const c128* G, const double* m,
+                         cudaStream_t st) {
+  dim3 grid(std::min((N * N + 255) / 256, 256), nw);
+  ++::gw::g_launch_count, k_q0avg_update<<<grid, 256, 0, st>>>(N, nw, X, sX, x1, G, m);
+}
+
 __global__ void k_midgap(int NK, int NBd, int nocc, const double* eps, double* mu) {
   __shared__ double hmax[256], lmin[256];
   double h = -1e300, l = 1e300;

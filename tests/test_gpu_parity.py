@@ -190,3 +190,40 @@ def test_qp_gap_selection_hand_built(window):
         assert abs(gw.gw_plan_mu(plan) - C.MU) < 1e-15
     finally:
         gw.gw_plan_destroy(plan)
+
+
+@pytest.fixture(scope="module")
+def cfg0_avg():
+    s = make_system("cfg0", seed=0, head_wings=2)
+    om, g = O.freq_grid(s.n_freq, s.omega0)
+    chi = O.chi0(s, 0, om)
+    _, W = O.screen(s, 0, chi, om)
+    ref = O.g0w0(s)
+    return s, W, ref
+
+
+@pytest.mark.parametrize("prec,tol_w,tol_mev", [("fp64", 1e-10, 1e-6), ("3xbf16", 1e-5, 1.0), ("3xfp16", 1e-5, 1.0)])
+def test_direction_averaged_q0(cfg0_avg, prec, tol_w, tol_mev):
+    """head_wings = 2: W^c(0) from eps~^-1 - 1 averaged over the directions of q -> 0 (the oracle
+    inverts eps~ for each of the 128 directions; the library uses the Schur-complement form on
+    the inverse of the body), then the whole pass: Sigma_c and the gap against the oracle."""
+    from paper_2011_01400_gb300 import gw
+    s, W_ref, ref = cfg0_avg
+    N, nw, nsig = s.n_aux, s.n_freq, s.sigma_hi - s.sigma_lo
+    pb = gw.Problem(s, prec)
+    plan = gw.gw_plan_create(pb.prob)
+    W = torch.empty((nw, N, N), dtype=torch.complex128, device="cuda")
+    acc = torch.zeros((s.n_k, nsig, nw), dtype=torch.complex128, device="cuda")
+    try:
+        gw.gw_chi0(plan, 0, 0)
+        gw.gw_screen(plan, 0, 0, W)
+        gw.gw_g0w0(plan, 0, acc)
+        e, gap, _ = gw.gw_qp(plan, 0, s.n_k, nsig, sigma=acc)
+    finally:
+        gw.gw_plan_destroy(plan)
+    W = W.cpu().numpy()
+    ew = max(rel_fro(W[j], W_ref[j]) for j in range(nw))
+    es = np.abs(acc.cpu().numpy() - ref["sigma"]).max() * HA_MEV
+    eg = abs(gap - ref["gap"]) * HA_MEV
+    print(f"{prec} averaged q=0: W^c {ew:.2e}, Sigma_c {es:.2e} meV, gap {eg:.2e} meV")
+    assert ew <= tol_w and es <= tol_mev and eg <= tol_mev

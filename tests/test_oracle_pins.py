@@ -326,3 +326,73 @@ def test_mu_midgap_hand_built():
     """Midgap chemical potential of the hand-built energies: (max_k HOMO + min_k LUMO) / 2."""
     import qp_case as C
     assert abs(O.mu_midgap(C.system()) - C.MU) < 1e-15
+
+
+def test_sphere_rule_moments_and_uniaxial_closed_form():
+    """The direction rule of the q -> 0 average: weights sum to 1, <q_a q_b> = delta_ab / 3 and
+    odd moments vanish exactly; the average of 1 / (1 + a q_z^2) is arctan(sqrt a) / sqrt a."""
+    dirs, w = O.sphere_rule()
+    assert abs(w.sum() - 1.0) < 1e-14
+    assert np.allclose(np.linalg.norm(dirs, axis=1), 1.0, atol=1e-14)
+    assert np.abs(np.einsum("n,na,nb->ab", w, dirs, dirs) - np.eye(3) / 3).max() < 1e-14
+    assert np.abs(w @ dirs).max() < 1e-15
+    for a in (0.1, 0.5, 1.0):
+        avg = w @ (1.0 / (1.0 + a * dirs[:, 2] ** 2))
+        assert abs(avg - math.atan(math.sqrt(a)) / math.sqrt(a)) < 2e-6
+
+
+def test_direction_average_of_a_uniaxial_head(monkeypatch):
+    """head_wings = 2 with no LRI coefficients (chi0 = 0, no wings) and a momentum matrix along z
+    only: eps~(q^) is 1 except its head 1 + a q_z^2, so the averaged eps~^-1 - 1 is
+    (arctan(sqrt a)/sqrt a - 1) x1 x1^H and W^c(0) = v1 times that (x1, v1 the Coulomb head pair)."""
+    s = make_system("tiny", seed=8, c_scale=0.0, head_wings=2)
+    s.pmom[:, 0:2] = 0.0
+    s.pmom *= 0.2
+    om, _ = O.freq_grid(s.n_freq, s.omega0)
+    chi = O.chi0(s, 0, om)
+    assert np.abs(chi).max() == 0.0
+    _, W = O.screen(s, 0, chi, om)
+    v, X = O.coulomb_eig_q0(s.V[0])
+    x1 = X[:, 0]
+    s1 = make_system("tiny", seed=8, c_scale=0.0)
+    s1.pmom[:] = s.pmom
+    s1.qhat = np.array([0.0, 0.0, 1.0])
+    eps_z, _, _ = O.head_wings_q0(s1, om, chi)
+    for j in range(len(om)):
+        a = eps_z[j][0, 0].real - 1.0
+        assert 0.0 < a < 1.0
+        ref = v[0] * (math.atan(math.sqrt(a)) / math.sqrt(a) - 1.0) * np.outer(x1, np.conj(x1))
+        assert np.abs(W[j] - ref).max() <= 3e-6 * np.abs(ref).max()
+
+
+def test_direction_average_matches_schur_form():
+    """The average of eps~(q^)^-1 - 1 over the directions (direct inversions) equals its Schur-
+    complement form: with G the inverse of the body block (the head row and column removed),
+    y(q^) the wing column and s(q^) = head - y^H G y, eps~^-1 - 1 = (G - 1) + (1/s - 1) x1 x1^H
+    - (x1 g^H + g x1^H)/s + g g^H / s, g = G y, whose average needs only <1/s>, <q^/s>, <q^ q^T/s>."""
+    s = make_system("tiny", seed=9, head_wings=2)
+    om, _ = O.freq_grid(s.n_freq, s.omega0)
+    chi = O.chi0(s, 0, om)
+    _, W = O.screen(s, 0, chi, om)
+    Vh = O.hsqrt(s.V[0])
+    dirs, wts = O.sphere_rule()
+    N = s.n_aux
+    for j in (0, len(om) - 1):
+        acc = np.zeros((N, N), dtype=np.complex128)
+        for d, wd in zip(dirs, wts):
+            eX, X, v = O.head_wings_q0(s, om[j:j + 1], chi[j:j + 1], qhat=d)
+            E = eX[0]
+            G = np.zeros((N, N), dtype=np.complex128)
+            G[0, 0] = 1.0
+            G[1:, 1:] = np.linalg.inv(E[1:, 1:])
+            y = np.zeros(N, dtype=np.complex128)
+            y[1:] = E[1:, 0]
+            g = G @ y
+            sc = (E[0, 0] - np.conj(y) @ g).real
+            e1 = np.zeros(N)
+            e1[0] = 1.0
+            Xl = G - np.eye(N) + (1 / sc - 1) * np.outer(e1, e1) - (np.outer(e1, np.conj(g)) + np.outer(g, e1)) / sc \
+                + np.outer(g, np.conj(g)) / sc
+            acc += wd * (X @ Xl @ np.conj(X).T)
+        ref = Vh @ acc @ Vh
+        assert np.linalg.norm(W[j] - ref) <= 1e-10 * np.linalg.norm(ref)
