@@ -40,12 +40,22 @@ WORKLOADS = {
 }
 
 
+def q_computed(s):
+    """q points whose chi0 / eps~ / W^c the pass computes: all of them, or one of each pair
+    (q, -q) when the system is time-reversal symmetric (W^c(-q) = conj(W^c(q)))."""
+    if not getattr(s, "trs", False):
+        return s.n_k
+    from paper_2011_01400_gb300.synth import minus_k
+    return sum(1 for q in range(s.n_k) if minus_k(s.nk, q) >= q)
+
+
 def algorithmic_flops(s):
     """Useful flops of one step (8 per complex multiply-add): chi0 Hermitian update, screen, Sigma_c."""
     NK, N, nw = s.n_k, s.n_aux, s.n_freq
     nocc, nun, nsig = s.n_occ, s.n_bands - s.n_occ, s.sigma_hi - s.sigma_lo
-    chi0 = 8.0 * NK * nocc * nun * (N * (N + 1) / 2) * nw * NK
-    screen = 4 * 8.0 * N ** 3 * nw * NK
+    nq = q_computed(s)
+    chi0 = 8.0 * NK * nocc * nun * (N * (N + 1) / 2) * nw * nq
+    screen = 4 * 8.0 * N ** 3 * nw * nq
     sigma = 8.0 * (NK * nsig * s.n_bands) * N * N * nw * NK
     return dict(chi0=chi0, screen=screen, sigma=sigma, total=chi0 + screen + sigma)
 
@@ -634,6 +644,9 @@ def run_device(args, system, world, rank):
                     name=args.config, precision=args.prec, systems_per_step=1 if qshard else world,
                     q_loop="q-parallel (gw_g0w0_qset + Sigma_c sum over ranks)" if qshard else args.qloop,
                     global_batch=1 if qshard else world, seq_len=0, parallelism=mode if world > 1 else "single",
+                    time_reversal=bool(getattr(s, "trs", False)),
+                    q_chi0_computed=f"{q_computed(s)} of {s.n_k} (W^c(-q) = conj(W^c(q)) for the pairs)"
+                    if getattr(s, "trs", False) else f"{s.n_k} of {s.n_k}",
                     l2="inputs larger than L2 (chi0 operand planes 0.8 GB per q)"),
         chi0_tflops=achieved,
         step_useful_tflops=fl["total"] / (ms * 1e-3) / 1e12,

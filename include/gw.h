@@ -105,6 +105,22 @@ typedef struct {
   double spin;                   /* spin factor in chi0 (2 for doubly occupied bands)        */
   double mu;                     /* chemical potential; NaN selects midgap                   */
   gw_precision prec;
+  int32_t time_reversal;         /* 1: the inputs are time-reversal symmetric (real NAOs and
+                                    ABFs, no magnetism): eps(-k) = eps(k), c(-k) = conj(c(k))
+                                    up to a phase per band, V(-q) = conj(V(q)), p(-k) =
+                                    -conj(p(k)). Then chi0(-q) = conj(chi0(q)) and W^c(-q) =
+                                    conj(W^c(q)), and gw_g0w0 / gw_g0w0_qset compute chi0, eps~
+                                    and W^c for one q of each pair (q, -q) of their q list, the
+                                    Sigma_c term of -q from the conjugate W^c. gw_plan_create
+                                    checks eps and V (GW_ERR_ARG beyond rounding). 0: no
+                                    symmetry assumed.                                          */
+  double k_offset[3];            /* shift of the k mesh in fractional coordinates, each in
+                                    [-1, 1]: the k points are k0 + (i1/n1, i2/n2, i3/n3), and
+                                    eps, evec and pmom are given at those points (same index
+                                    order); the q mesh is never shifted, so k + q and k - q stay
+                                    on the shifted mesh. All zero: the Gamma-centred mesh. A
+                                    shifted plan gives Sigma_c at off-mesh k (its point 0 is k0)
+                                    through gw_sigma_ext with the W^c of an unshifted plan.    */
 } gw_problem;
 
 /* Build a plan: validates `prob`, copies the host arrays, allocates the
@@ -150,6 +166,16 @@ gw_status gw_screen(gw_plan plan, int32_t sys, int32_t q, gw_complex* wc_out);
  * sigma_acc: device [N_k][sigma_hi-sigma_lo][n_freq], accumulated into (caller zeroes it),
  *            or NULL to accumulate into the plan's own buffer (zeroed at plan creation). */
 gw_status gw_sigma(gw_plan plan, int32_t sys, int32_t q, gw_complex* sigma_acc);
+
+/* The q term of Sigma_c (as gw_sigma) with a caller-supplied W^c(q) (device [n_freq][n_aux][n_aux],
+ * Hermitian, same grid), for the target k in [k_lo, k_hi) only. On a plan whose k mesh is shifted
+ * (gw_problem.k_offset = k0), with the W^c of an unshifted plan of the same system, the sum over
+ * q gives Sigma_c at the off-mesh points k0 + mesh (point 0 is k0 itself): band energies along
+ * lines through the Brillouin zone. sigma_acc: device [N_k][n_sigma][n_freq] (rows outside the
+ * k range untouched) or NULL for the plan's own accumulator.
+ * Errors: GW_ERR_ARG (q, k range, NULL wc), GW_ERR_CUDA. */
+gw_status gw_sigma_ext(gw_plan plan, int32_t sys, int32_t q, const gw_complex* wc, int32_t k_lo, int32_t k_hi,
+                       gw_complex* sigma_acc);
 
 /* Exchange self-energy, the bare-Coulomb part of Eq. (GW_selfe_element) (W = V + W^c): the
  * frequency integral of V G leaves the occupied bands,

@@ -35,6 +35,13 @@ def kpoints(nk):
     return np.array(out)
 
 
+def kfrac(sys):
+    """Fractional coordinates of the system's k points: the Gamma-centred mesh, shifted by
+    sys.k_offset when the system carries one (a shifted mesh k0 + i/n; the q mesh is never
+    shifted, so k + q and k - q stay on the shifted mesh)."""
+    return kpoints(sys.nk) + np.asarray(getattr(sys, "k_offset", np.zeros(3)), dtype=np.float64)[None, :]
+
+
 def k_of(nk, ik):
     n1, n2, n3 = nk
     return ik // (n2 * n3), (ik // n3) % n2, ik % n3
@@ -101,7 +108,7 @@ def ao_triple(sys, ik, iq):
     (Eq. two_center_coeff_determination), so the first term lives on
     mu in atom(j), the second on mu in atom(i); when atom(i) == atom(j) both add.
     """
-    kp = kpoints(sys.nk)
+    kp = kfrac(sys)
     k = kp[ik]
     kq = kp[k_plus(sys.nk, ik, iq)]
     C = np.zeros((sys.n_aux, sys.n_basis, sys.n_basis), dtype=np.complex128)
@@ -164,7 +171,7 @@ def chi0_block(sys, iq, omegas, mus):
     """chi0_{mu nu}(q, i w) of Eq. (chi0_matrix) for mu, nu in the ABF subset `mus` only (the
     Hermitised form of `chi0`), from the rows C~^mu(k+q, k) of Eq. (AO_triple_split2) built one ABF
     at a time: for sampled checks of systems whose full C~ does not fit. Returns [w, len(mus), len(mus)]."""
-    kp = kpoints(sys.nk)
+    kp = kfrac(sys)
     occ, unocc = np.arange(sys.n_occ), np.arange(sys.n_occ, sys.n_bands)
     om = np.asarray(omegas, dtype=np.float64)
     out = np.zeros((len(om), len(mus), len(mus)), dtype=np.complex128)

@@ -101,6 +101,37 @@ __global__ void k_frob_scale(int N, const c128* V, long long s, double* out) {
   if (threadIdx.x == 0) out[blockIdx.x] = sqrt(red[0]);
 }
 
+// Time-reversal check of the inputs: out[0] = max |eps_n(k) - eps_n(-k)|, out[1] = max |eps|,
+// out[2] = max |V(q) - conj(V(-q))|, out[3] = max |V| (as the bits of non-negative doubles).
+__global__ void k_trs_check(int n1, int n2, int n3, int NBd, const double* __restrict__ eps, int N,
+                            const c128* __restrict__ V, unsigned long long* out) {
+  const int NK = n1 * n2 * n3;
+  const long long NN = (long long)N * N;
+  double de = 0, ae = 0, dv = 0, av = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)NK * NBd;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / NBd), n = (int)(e % NBd);
+    const int i3 = k % n3, i2 = (k / n3) % n2, i1 = k / (n2 * n3);
+    const int mk = (((n1 - i1) % n1) * n2 + (n2 - i2) % n2) * n3 + (n3 - i3) % n3;
+    de = fmax(de, fabs(eps[e] - eps[(long long)mk * NBd + n]));
+    ae = fmax(ae, fabs(eps[e]));
+  }
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)NK * NN;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / NN);
+    const long long r = e % NN;
+    const int i3 = k % n3, i2 = (k / n3) % n2, i1 = k / (n2 * n3);
+    const int mk = (((n1 - i1) % n1) * n2 + (n2 - i2) % n2) * n3 + (n3 - i3) % n3;
+    const c128 a = V[e], b = V[(long long)mk * NN + r];
+    dv = fmax(dv, fmax(fabs(a.re - b.re), fabs(a.im + b.im)));
+    av = fmax(av, fmax(fabs(a.re), fabs(a.im)));
+  }
+  atomicMax(out, (unsigned long long)__double_as_longlong(de));
+  atomicMax(out + 1, (unsigned long long)__double_as_longlong(ae));
+  atomicMax(out + 2, (unsigned long long)__double_as_longlong(dv));
+  atomicMax(out + 3, (unsigned long long)__double_as_longlong(av));
+}
+
 // Y = V / c (typed), Z = I
 template <typename T>
 __global__ void k_ns_init(int N, const c128* V, long long s, const double* c, cplx<T>* Y, cplx<T>* Z) {
@@ -226,6 +257,7 @@ struct gw_plan_s {
   size_t ws_bytes = 0;              // sum of alloc_bytes
   size_t ws_limit = 0;              // GW_WORKSPACE_LIMIT (bytes; 0 = no limit)
   int dev = -1;                     // CUDA device that was current at gw_plan_create
+  bool trs = false;                 // time-reversal symmetric inputs (gw_problem.time_reversal)
   double *d_freq = nullptr, *d_fw = nullptr, *d_mu = nullptr;
   void* d_T1 = nullptr;     // c128 (FP64) or c64 (split)
   c128* d_Vh = nullptr;     // [NK][N][N] V(q)^1/2 (full, truncated at q=0)
@@ -457,6 +489,10 @@ gw_status validate(const gw_problem* p, int n_sys) {
   if (p->n_R < 1 || p->n_R > 64) return fail(GW_ERR_ARG, "n_R out of range [1, 64]");
   if (!p->eps || !p->evec || !p->ctil_R || !p->V) return fail(GW_ERR_ARG, "a device input pointer is NULL");
   if (p->head_wings < 0 || p->head_wings > 2) return fail(GW_ERR_ARG, "head_wings must be 0, 1 or 2");
+  for (int d = 0; d < 3; ++d)
+    if (!(std::fabs(p->k_offset[d]) <= 1.0)) return fail(GW_ERR_ARG, "k_offset components must be in [-1, 1]");
+  if (p->time_reversal && (p->k_offset[0] != 0.0 || p->k_offset[1] != 0.0 || p->k_offset[2] != 0.0))
+    return fail(GW_ERR_ARG, "time_reversal needs an unshifted k mesh (k_offset = 0)");
   if (p->head_wings && (!p->pmom || !(p->omega_cell > 0.0)))
     return fail(GW_ERR_ARG, "head_wings needs pmom and omega_cell > 0");
   if (p->n_freq < 1 || p->n_freq > 256) return fail(GW_ERR_ARG, "n_freq out of range [1, 256]");
@@ -606,7 +642,10 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
   g.NBd = P->NBd;
   g.N = P->N;
   g.nR = prob->n_R;
-  for (int d = 0; d < 3; ++d) g.nk[d] = prob->nk[d];
+  for (int d = 0; d < 3; ++d) {
+    g.nk[d] = prob->nk[d];
+    g.koff[d] = prob->k_offset[d];
+  }
   long long coff = 0, toff = 0;
   for (int A = 0; A < P->natoms; ++A) {
     int b0 = -1, nb = 0, x0 = -1, nx = 0;
@@ -799,6 +838,23 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
     launch_lri_halfT<float>(g, prob->ctil_R, reinterpret_cast<const c128*>(prob->evec), static_cast<c64*>(P->d_T1),
                             nullptr, st);
   if ((s = check_launch(P, "lri_halfT")) != GW_OK) return cleanup(s);
+  // time-reversal symmetry of the inputs, when the caller declares it
+  if (prob->time_reversal) {
+    unsigned long long* d_chk = nullptr;
+    if ((s = dalloc(P, &d_chk, 4)) != GW_OK) return cleanup(s);
+    CK(cudaMemsetAsync(d_chk, 0, 4 * sizeof(unsigned long long), st));
+    ++g_launch_count, k_trs_check<<<152 * 8, 256, 0, st>>>(prob->nk[0], prob->nk[1], prob->nk[2], P->NBd, prob->eps, N,
+                                                            reinterpret_cast<const c128*>(prob->V), d_chk);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(h, d_chk, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    double v[4];
+    for (int i = 0; i < 4; ++i) std::memcpy(&v[i], &h[i], sizeof(double));
+    if (!(v[0] <= 1e-12 * std::max(v[1], 1.0)) || !(v[2] <= 1e-12 * std::max(v[3], 1e-300)))
+      return cleanup(fail(GW_ERR_ARG, "time_reversal is set but eps(-k) != eps(k) or V(-q) != conj(V(q)) (max "
+                                      "differences " + std::to_string(v[0]) + ", " + std::to_string(v[2]) + ")"));
+    P->trs = true;
+  }
   // V(q)^1/2; at q = 0 with head_wings split off the lambda = 1 eigenvector first
   const c128* V = reinterpret_cast<const c128*>(prob->V);
   CK(cudaMemcpyAsync(P->d_Vh, V, sizeof(c128) * NN * P->NK, cudaMemcpyDeviceToDevice, st));
@@ -1175,16 +1231,18 @@ gw_status w_core(gw_plan_s* P, int q, const c128* X, c128* Wc) {
 }
 
 // q term of Sigma_c from W^c(q), accumulated into sig ([N_k][n_sigma][nw])
-gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig) {
+// target k in [k_lo, k_hi) (k_hi < 0: all)
+gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig, bool conjW = false, int k_lo = 0, int k_hi = -1) {
   cudaStream_t st = P->st;
   const int N = P->N, nw = P->nw, NBd = P->NBd, nsig = P->nsig;
   const long long NN = (long long)N * N;
   const c128* evec = reinterpret_cast<const c128*>(P->p.evec);
   const double pref = -1.0 / (2.0 * M_PI * P->NK);
   const int tf32 = P->prec == GW_3XTF32;
-  if (!P->fp64) tc_w_planes(N, nw, P->Kx, Wc, P->d_Wpl, tf32, st);
-  for (int kk0 = 0; kk0 < P->NK; kk0 += P->sig_nkk) {
-    const int nkk = std::min(P->sig_nkk, P->NK - kk0);
+  if (!P->fp64) tc_w_planes(N, nw, P->Kx, Wc, P->d_Wpl, tf32, st, conjW ? 1 : 0);
+  const int k_end = k_hi < 0 ? P->NK : k_hi;
+  for (int kk0 = k_lo; kk0 < k_end; kk0 += P->sig_nkk) {
+    const int nkk = std::min(P->sig_nkk, k_end - kk0);
     const int R = nkk * nsig * NBd;
     if (P->fp64) {
       c128* A = static_cast<c128*>(P->d_A);
@@ -1192,7 +1250,8 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig) {
       launch_mgen<double>(P->geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk,
                           MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, N, 1, st);
       for (int j = 0; j < nw; ++j) {
-        launch_zgemm<double>(R, N, N, c128{1, 0}, A, N, 0, OP_N, Wc + j * NN, N, 0, OP_N, c128{0, 0}, U, N, 0, 1, st);
+        launch_zgemm<double>(R, N, N, c128{1, 0}, A, N, 0, OP_N, Wc + j * NN, N, 0, conjW ? OP_CONJ : OP_N,
+                             c128{0, 0}, U, N, 0, 1, st);
         launch_rowdot<double>(R, N, U, A, N, nullptr, P->d_S_d, j, nw, st);
       }
     } else {
@@ -1246,15 +1305,36 @@ gw_status ensure_groups(gw_plan_s* P) {
 
 // The q loop of gw_g0w0 over the listed q points: groups of up to qb points whose FP64
 // factorisations of eps~ run as one batched launch; Sigma_c terms accumulated into sig.
-gw_status g0w0_qlist(gw_plan_s* P, const std::vector<int>& qs, c128* sig) {
+// -q on the mesh
+int minus_q(const gw_plan_s* P, int q) {
+  const int* n = P->p.nk;
+  const int i3 = q % n[2], i2 = (q / n[2]) % n[1], i1 = q / (n[1] * n[2]);
+  return (((n[0] - i1) % n[0]) * n[1] + (n[1] - i2) % n[1]) * n[2] + (n[2] - i3) % n[2];
+}
+
+gw_status g0w0_qlist(gw_plan_s* P, const std::vector<int>& qs_in, c128* sig) {
   cudaStream_t st = P->st;
   const int N = P->N, nw = P->nw;
   const long long NN = (long long)N * N;
   const long long slot = NN * nw;
+  // time reversal: W^c(-q) = conj(W^c(q)), so of a pair (q, -q) in the list only the smaller q
+  // goes through chi0 / eps~ / W^c; its W^c also gives the Sigma_c term of -q
+  std::vector<int> qs, partner;
+  {
+    std::vector<char> in(P->NK, 0);
+    for (int q : qs_in) in[q] = 1;
+    for (int q : qs_in) {
+      const int mq = P->trs ? minus_q(P, q) : q;
+      if (mq != q && in[mq] && mq < q) continue;
+      qs.push_back(q);
+      partner.push_back(mq != q && in[mq] ? mq : -1);
+    }
+  }
   P->reset_timing();
   for (size_t g0 = 0; g0 < qs.size(); g0 += P->qb) {
     const int nq = (int)std::min<size_t>(P->qb, qs.size() - g0);
     const int* q = qs.data() + g0;
+    const int* qp = partner.data() + g0;
     GW_CUDA(cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
     GW_TRY(chi0_prepare(P, q, nq));
     for (int j = 0; j < nq; ++j) GW_TRY(chi0_core(P, q[j], P->g_chi0 + j * slot));
@@ -1263,7 +1343,10 @@ gw_status g0w0_qlist(gw_plan_s* P, const std::vector<int>& qs, c128* sig) {
     for (int j = 0; j < nq; ++j)
       if (q[j] == 0 && P->p.head_wings == 2) GW_TRY(q0_average(P, P->g_E + j * slot));
     for (int j = 0; j < nq; ++j) GW_TRY(w_core(P, q[j], P->g_E + j * slot, P->g_chi0 + j * slot));
-    for (int j = 0; j < nq; ++j) GW_TRY(sigma_core(P, q[j], P->g_chi0 + j * slot, sig));
+    for (int j = 0; j < nq; ++j) {
+      GW_TRY(sigma_core(P, q[j], P->g_chi0 + j * slot, sig));
+      if (qp[j] >= 0) GW_TRY(sigma_core(P, qp[j], P->g_chi0 + j * slot, sig, true));
+    }
     GW_TRY(read_status(P, "gw_g0w0"));
   }
   GW_TRY(P->collect_timing());
@@ -1323,6 +1406,20 @@ gw_status gw_sigma(gw_plan P, int32_t sys, int32_t q, gw_complex* sigma_acc) {
   if (P->wc_q != q) return fail(GW_ERR_STATE, "gw_sigma needs gw_screen for the same q first");
   c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
   GW_TRY(sigma_core(P, q, P->d_Wc, sig));
+  return GW_OK;
+}
+
+gw_status gw_sigma_ext(gw_plan P, int32_t sys, int32_t q, const gw_complex* wc, int32_t k_lo, int32_t k_hi,
+                       gw_complex* sigma_acc) {
+  gw_status s;
+  Route rt;
+  if (!route(P, sys, rt, &s)) return s;
+  if (!plan_ok(P, sys, &s)) return s;
+  if (q < 0 || q >= P->NK) return fail(GW_ERR_ARG, "q out of range");
+  if (!wc) return fail(GW_ERR_ARG, "wc is NULL");
+  if (k_lo < 0 || k_hi > P->NK || k_lo >= k_hi) return fail(GW_ERR_ARG, "k range must satisfy 0 <= k_lo < k_hi <= N_k");
+  c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
+  GW_TRY(sigma_core(P, q, reinterpret_cast<const c128*>(wc), sig, false, k_lo, k_hi));
   return GW_OK;
 }
 

@@ -54,6 +54,7 @@ enum Op { OP_N = 0, OP_T = 1, OP_C = 2, OP_CONJ = 3 };   // as is, transpose, co
 struct LriGeom {
   int n_atoms, NK, NB, NBd, N, nR;
   int nk[3];
+  double koff[3];              // shift of the k mesh (fractional); the q mesh is not shifted
   int atom_b0[64], atom_nb[64], atom_x0[64], atom_nx[64];
   long long ctil_off[64];      // element offset of atom block in ctil_R
   long long t_off[64];         // element offset of atom block in T1/T2
@@ -182,7 +183,8 @@ struct TcSigmaArgs {
 };
 gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std::string& err);
 gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, std::string& err);
-void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st);
+// conj != 0: the planes of conj(W^c) (time reversal: W^c(-q) = conj(W^c(q)))
+void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st, int conj = 0);
 bool tc_available();
 void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st);
 

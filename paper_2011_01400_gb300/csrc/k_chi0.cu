@@ -67,15 +67,21 @@ constexpr int LSH = 11;                  // F16: the low piece is scaled by 2^11
 
 enum { K_F16 = 0, K_BF16 = 1, K_TF32 = 2 };
 
+// Shared memory: a ring of SB B stages (TMA runs up to SB - 1 stages ahead of the MMAs, which
+// covers the L2 / HBM latency), SA buffers of split A pieces (written by the transform just in
+// time), and the raw-row ring of RING slots with their weights.
 template <int KIND> struct Kd {
   static constexpr int NP = (KIND == K_BF16) ? 3 : 2;       // pieces per operand
   static constexpr int ESZ = (KIND == K_TF32) ? 4 : 2;      // bytes per element
   static constexpr int RPS = (KIND == K_TF32) ? 1 : 2;      // ring slots per stage
   static constexpr int RS = 16 * RPS;                       // complex pair rows per stage
-  static constexpr int STAGE = 2 * NP * TILE;               // B pieces then A pieces
-  static constexpr int STAGES = 2;
-  static constexpr int RING = (KIND == K_BF16) ? 2 : 4;     // ring slots
-  static constexpr int WB_OFF = STAGES * STAGE + RING * SLOT;
+  static constexpr int BST = NP * TILE;                     // one B stage (or one A buffer)
+  static constexpr int SB = (KIND == K_BF16) ? 2 : 4;       // B stages
+  static constexpr int SA = 2;                              // A buffers
+  static constexpr int RING = (KIND == K_BF16) ? 2 : 4;     // raw ring slots
+  static constexpr int A_OFF = SB * BST;
+  static constexpr int RING_OFF = A_OFF + SA * BST;
+  static constexpr int WB_OFF = RING_OFF + RING * SLOT;
   static constexpr int BAR_OFF = WB_OFF + RING * WBYTES;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;
 };
@@ -154,32 +160,36 @@ __device__ __forceinline__ void mma_k(uint32_t d, uint64_t a, uint64_t b, uint32
 template <int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Chi0Maps maps, Chi0Params p) {
   using C = Kd<KIND>;
-  constexpr int NP = C::NP, STAGES = C::STAGES, STAGE = C::STAGE, RPS = C::RPS, RING = C::RING;
+  constexpr int NP = C::NP, SB = C::SB, SA = C::SA, BST = C::BST, RPS = C::RPS, RING = C::RING;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* ring = smem + STAGES * STAGE;
+  uint8_t* ring = smem + C::RING_OFF;
   float* wbuf = reinterpret_cast<float*>(smem + C::WB_OFF);   // [RING][16]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
-  uint64_t* full_b = bars;                   // [STAGES]
-  uint64_t* full_a = bars + STAGES;          // [STAGES]
-  uint64_t* empty = bars + 2 * STAGES;       // [STAGES]
-  uint64_t* t1full = bars + 3 * STAGES;      // [2] D1 of a stage ready
-  uint64_t* t1empty = bars + 3 * STAGES + 2; // [2] D1 drained
-  uint64_t* t2full = bars + 3 * STAGES + 4;  // [2] D2 of a segment ready
-  uint64_t* t2empty = bars + 3 * STAGES + 6; // [2] D2 drained
-  uint64_t* done = bars + 3 * STAGES + 8;
-  uint64_t* rfull = bars + 3 * STAGES + 9;           // [RING]
-  uint64_t* rempty = bars + 3 * STAGES + 9 + RING;   // [RING]
-  uint32_t* tmem_base_p = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 9 + 2 * RING);
+  uint64_t* full_b = bars;                        // [SB] B stage landed
+  uint64_t* empty_b = bars + SB;                  // [SB] B stage consumed by the MMAs
+  uint64_t* full_a = bars + 2 * SB;               // [SA] A buffer written by the transform
+  uint64_t* empty_a = bars + 2 * SB + SA;         // [SA] A buffer consumed by the MMAs
+  uint64_t* t1full = bars + 2 * SB + 2 * SA;      // [2] D1 of a stage ready
+  uint64_t* t1empty = t1full + 2;                 // [2] D1 drained
+  uint64_t* t2full = t1full + 4;                  // [2] D2 of a segment ready
+  uint64_t* t2empty = t1full + 6;                 // [2] D2 drained
+  uint64_t* done = t1full + 8;
+  uint64_t* rfull = t1full + 9;                   // [RING]
+  uint64_t* rempty = t1full + 9 + RING;           // [RING]
+  uint32_t* tmem_base_p = reinterpret_cast<uint32_t*>(t1full + 9 + 2 * RING);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int it0 = p.cta_off[blockIdx.x], it1 = p.cta_off[blockIdx.x + 1];
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < SB; ++s) {
       mbar_init(&full_b[s], 1);
+      mbar_init(&empty_b[s], 1);
+    }
+    for (int s = 0; s < SA; ++s) {
       mbar_init(&full_a[s], 4);                 // one elected arrival per transform warp
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty_a[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&t1full[b], 1);
@@ -214,9 +224,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
         int t, s0, s1;
         decode(p, p.items[it], tl, t, s0, s1);
         for (int i = s0; i < s1; ++i, ++gs) {
-          const int s = gs % STAGES;
-          if (!mbar_wait(&empty[s], ((gs / STAGES) & 1) ^ 1, p.status)) { ok = false; break; }
-          uint8_t* st = smem + s * STAGE;
+          const int s = gs % SB;
+          if (!mbar_wait(&empty_b[s], ((gs / SB) & 1) ^ 1, p.status)) { ok = false; break; }
+          uint8_t* st = smem + s * BST;
           mbar_arrive_expect_tx(&full_b[s], NP * TILE);
           const int x = i * (ROWB / C::ESZ);
 #pragma unroll
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(tl.ncols >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
         for (int i = s0; i < s1; ++i, ++gs) {
-          const int s = gs % STAGES;
+          const int sb = gs % SB, sa = gs % SA;
           const int b = gs & 1, b2 = gseg & 1;
           const bool seg_first = ((i - s0) % F) == 0;
           const bool seg_end = ((i - s0) % F) == F - 1 || i == s1 - 1;
@@ -266,11 +276,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
             ok = false;
             break;
           }
-          if (!mbar_wait(&full_b[s], (gs / STAGES) & 1, p.status)) { ok = false; break; }
-          if (!mbar_wait(&full_a[s], (gs / STAGES) & 1, p.status)) { ok = false; break; }
+          if (!mbar_wait(&full_b[sb], (gs / SB) & 1, p.status)) { ok = false; break; }
+          if (!mbar_wait(&full_a[sa], (gs / SA) & 1, p.status)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t bbase = smem_u32(smem + s * STAGE);
-          const uint32_t abase = bbase + NP * TILE;
+          const uint32_t bbase = smem_u32(smem + sb * BST);
+          const uint32_t abase = smem_u32(smem + C::A_OFF + sa * BST);
           const uint32_t d1 = tmem + D1_COL + b * DBUF;
           const uint32_t d2 = tmem + D2_COL + b2 * DBUF;
 #pragma unroll
@@ -289,7 +299,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
             }
             mma_k<KIND>(d1, A0, B0, idesc, kk == 0 ? 0u : 1u);
           }
-          mma_commit(&empty[s]);
+          mma_commit(&empty_b[sb]);
+          mma_commit(&empty_a[sa]);
           mma_commit(&t1full[b]);
           if (seg_end) {
             mma_commit(&t2full[b2]);
@@ -312,10 +323,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
       int t, s0, s1;
       decode(p, p.items[it], tl, t, s0, s1);
       for (int i = s0; i < s1; ++i, ++gs, gr += RPS) {
-        const int s = gs % STAGES;
+        const int s = gs % SA;
         // warp-uniform waits: the arrivals below are elected per warp
-        if (!__all_sync(0xffffffffu, mbar_wait(&empty[s], ((gs / STAGES) & 1) ^ 1, p.status))) { ok = false; break; }
-        uint8_t* at = smem + s * STAGE + NP * TILE;
+        if (!__all_sync(0xffffffffu, mbar_wait(&empty_a[s], ((gs / SA) & 1) ^ 1, p.status))) { ok = false; break; }
+        uint8_t* at = smem + C::A_OFF + s * BST;
         const uint32_t g = gr + (RPS == 2 ? h : 0);
         const int slot = g % RING;
         if (!__all_sync(0xffffffffu, mbar_wait(&rfull[slot], (g / RING) & 1, p.status))) { ok = false; break; }

@@ -33,9 +33,9 @@ __global__ void k_lri_halfT(const __grid_constant__ LriGeom g, const double* __r
     double acc_re = 0.0, acc_im = 0.0;
     const c128* ck = evec + (long long)k * g.NB * g.NBd;
     for (int r = 0; r < g.nR; ++r) {
-      // phase e^{2 pi i k.R}, k in fractional coordinates
-      double ph = 2.0 * ((double)k1 * g.R[r][0] / g.nk[0] + (double)k2 * g.R[r][1] / g.nk[1] +
-                         (double)k3 * g.R[r][2] / g.nk[2]);
+      // phase e^{2 pi i k.R}, k = mesh point + offset in fractional coordinates
+      double ph = 2.0 * (((double)k1 / g.nk[0] + g.koff[0]) * g.R[r][0] + ((double)k2 / g.nk[1] + g.koff[1]) * g.R[r][1] +
+                         ((double)k3 / g.nk[2] + g.koff[2]) * g.R[r][2]);
       double s, c;
       sincospi(ph, &s, &c);
       const double* crow = ctil + g.ctil_off[A] + (((long long)r * nx_A + mu) * nb_A + i) * g.NB;
@@ -80,8 +80,9 @@ __global__ void k_phase_evec(const __grid_constant__ LriGeom g, int r, const c12
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(e / per_k);
     const int k3 = k % g.nk[2], k2 = (k / g.nk[2]) % g.nk[1], k1 = k / (g.nk[1] * g.nk[2]);
-    const double ph = 2.0 * ((double)k1 * g.R[r][0] / g.nk[0] + (double)k2 * g.R[r][1] / g.nk[1] +
-                             (double)k3 * g.R[r][2] / g.nk[2]);
+    const double ph = 2.0 * (((double)k1 / g.nk[0] + g.koff[0]) * g.R[r][0] +
+                             ((double)k2 / g.nk[1] + g.koff[1]) * g.R[r][1] +
+                             ((double)k3 / g.nk[2] + g.koff[2]) * g.R[r][2]);
     double sn, cs;
     sincospi(ph, &sn, &cs);
     const c128 v = evec[e];

@@ -604,9 +604,10 @@ __global__ void k_a_planes(long long n, const float* __restrict__ raw, void* p0,
   }
 }
 
-// B planes of W^c for the Sigma contraction: row (j, nu), K index 2 mu + {0, 1}:
+// B planes of W^c (conj: of conj(W^c)) for the Sigma contraction: row (j, nu), K index 2 mu + {0, 1}:
 // B1 = split(Re W_{nu mu}, Im W_{nu mu}), B2 = split(-Im, Re); mu >= N is zero padding.
-__global__ void k_w_planes(int N, int nw, int Kpad, const c128* __restrict__ Wc, PlaneSet P, int tf32, int np) {
+__global__ void k_w_planes(int N, int nw, int Kpad, const c128* __restrict__ Wc, PlaneSet P, int tf32, int np,
+                           int conj) {
   const long long total = (long long)nw * N * Kpad;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -616,7 +617,7 @@ __global__ void k_w_planes(int N, int nw, int Kpad, const c128* __restrict__ Wc,
     if (mu < N) {
       const c128 w = Wc[row * N + mu];
       v1[0] = (float)w.re;
-      v1[1] = (float)w.im;
+      v1[1] = conj ? -(float)w.im : (float)w.im;
     }
     const float v2[2] = {-v1[1], v1[0]};
     const long long o = row * 2LL * Kpad + 2LL * mu;
@@ -855,9 +856,9 @@ gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, s
   return tf32 ? launch_tc<true, 2, 1>(maps, p, st, err) : launch_tc<false, 2, 1>(maps, p, st, err);
 }
 
-void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st) {
+void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st, int conj) {
   const long long total = (long long)nw * N * Kpad;
-  ++::gw::g_launch_count, k_w_planes<<<std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, st>>>(N, nw, Kpad, Wc, P, tf32, 2);
+  ++::gw::g_launch_count, k_w_planes<<<std::min<long long>((total + 255) / 256, 152 * 64), 256, 0, st>>>(N, nw, Kpad, Wc, P, tf32, 2, conj);
 }
 
 void tc_herm_fill(int N, int nw, c128* chi0, cudaStream_t st) {

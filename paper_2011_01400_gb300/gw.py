@@ -21,7 +21,7 @@ GW_FP64, GW_3XTF32, GW_3XBF16, GW_3XFP16 = 0, 1, 2, 3
 PREC = {"fp64": GW_FP64, "3xtf32": GW_3XTF32, "3xbf16": GW_3XBF16, "3xfp16": GW_3XFP16}
 
 # every symbol include/gw.h declares
-EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_sigma_x", "gw_g0w0", "gw_g0w0_qset",
+EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigma", "gw_sigma_ext", "gw_sigma_x", "gw_g0w0", "gw_g0w0_qset",
            "gw_g0w0_batch",
            "gw_plan_n_sys", "gw_qp",
            "gw_qp_static", "gw_plan_freq", "gw_plan_mu", "gw_plan_last_chi0_stats", "gw_plan_chi0_terms", "gw_kernel_launches",
@@ -71,6 +71,8 @@ class gw_problem(ctypes.Structure):
         ("spin", ctypes.c_double),
         ("mu", ctypes.c_double),
         ("prec", ctypes.c_int32),
+        ("time_reversal", ctypes.c_int32),
+        ("k_offset", ctypes.c_double * 3),
     ]
 
 
@@ -91,6 +93,7 @@ def load():
     lib.gw_chi0.argtypes = [vp, i32, i32, vp]
     lib.gw_screen.argtypes = [vp, i32, i32, vp]
     lib.gw_sigma.argtypes = [vp, i32, i32, vp]
+    lib.gw_sigma_ext.argtypes = [vp, i32, i32, vp, i32, i32, vp]
     lib.gw_g0w0.argtypes = [vp, i32, vp]
     lib.gw_g0w0_qset.argtypes = [vp, i32, ctypes.POINTER(i32), i32, vp]
     lib.gw_sigma_x.argtypes = [vp, i32, vp]
@@ -183,6 +186,10 @@ def gw_screen(plan, sys, q, wc_out=None):
 
 def gw_sigma(plan, sys, q, sigma_acc=None):
     _check(load().gw_sigma(plan, sys, q, _ptr(sigma_acc)))
+
+
+def gw_sigma_ext(plan, sys, q, wc, k_lo, k_hi, sigma_acc=None):
+    _check(load().gw_sigma_ext(plan, sys, q, _ptr(wc), k_lo, k_hi, _ptr(sigma_acc)))
 
 
 def gw_sigma_x(plan, sys, sigx):
@@ -353,7 +360,7 @@ def gw_surrogate_fit_scale(model, x, y):
 class Problem:
     """Keeps the device tensors and host arrays that a gw_problem points to alive."""
 
-    def __init__(self, system, prec="3xbf16", device="cuda", host=False):
+    def __init__(self, system, prec="3xbf16", device="cuda", host=False, trs=None, mu=None):
         import torch
         s = system
         self.system = s
@@ -389,8 +396,11 @@ class Problem:
         p.omega0 = s.omega0
         p.sigma_lo, p.sigma_hi = s.sigma_lo, s.sigma_hi
         p.spin = s.spin
-        p.mu = math.nan
+        p.mu = math.nan if mu is None else float(mu)
         p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        # time-reversal symmetric inputs (the generator's default) let the q loop pair q with -q
+        p.time_reversal = int(bool(getattr(s, "trs", False) if trs is None else trs))
+        p.k_offset[:] = [float(x) for x in getattr(s, "k_offset", (0.0, 0.0, 0.0))]
         self.prob = p
 
     def upload(self):

@@ -18,7 +18,7 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-__all__ = ["System", "CONFIGS", "make_system", "kmesh_index", "minus_k", "add_k"]
+__all__ = ["System", "CONFIGS", "make_system", "shifted_system", "kmesh_index", "minus_k", "add_k"]
 
 
 @dataclasses.dataclass
@@ -46,6 +46,8 @@ class System:
     spin: float = 2.0
     head_wings: int = 1
     seed: int = 0
+    trs: bool = False       # drawn with time-reversal symmetry (then the library may pair q with -q)
+    k_offset: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros(3))  # shift of the k mesh
 
     @property
     def n_k(self):
@@ -219,7 +221,28 @@ def make_system(cfg="cfg0", seed=0, *, trs=True, n_freq=None, nk=None, n_bands=N
                   basis_atom=basis_atom, aux_atom=aux_atom, R=R, eps=eps, evec=evec,
                   ctil_R=ctil, V=V, pmom=pm, omega_cell=float(p["omega_cell"]),
                   qhat=np.array([1.0, 0.0, 0.0]), n_freq=int(p["n_freq"]), omega0=omega0,
-                  sigma_lo=int(lo), sigma_hi=int(hi), spin=2.0, head_wings=head_wings, seed=seed)
+                  sigma_lo=int(lo), sigma_hi=int(hi), spin=2.0, head_wings=head_wings, seed=seed, trs=bool(trs))
+
+
+def shifted_system(base, k_offset, seed, eps=None, evec=None, pmom=None):
+    """The system `base` on the k mesh shifted by k_offset (fractional): the same atoms, basis,
+    two-centre coefficients C~(R), Coulomb matrices V(q) (the q mesh is not shifted) and window,
+    with KS energies, eigenvectors and momentum matrices at the shifted points k0 + i/n, drawn
+    from `seed` by the recipe of make_system unless given. Sigma at an off-mesh point k0 is the
+    Sigma of point 0 of this mesh (its k - q run over the shifted mesh)."""
+    rng = np.random.default_rng(seed)
+    NK, nb, nbands, nocc = base.n_k, base.n_basis, base.n_bands, base.n_occ
+    if eps is None:
+        eps = np.stack([np.concatenate([np.sort(rng.uniform(-0.8, -0.2, nocc)),
+                                        np.sort(rng.uniform(0.05, 3.0, nbands - nocc))]) for _ in range(NK)])
+    if evec is None:
+        evec = np.stack([np.linalg.qr(_cgauss(rng, (nb, nb)))[0][:, :nbands] for _ in range(NK)])
+    if pmom is None:
+        g3 = _cgauss(rng, (NK, 3, nbands, nbands))
+        pmom = 0.5 * (g3 + np.conj(np.swapaxes(g3, -1, -2))) / np.sqrt(2.0)
+    return dataclasses.replace(base, eps=np.ascontiguousarray(eps), evec=np.ascontiguousarray(evec),
+                               pmom=np.ascontiguousarray(pmom), trs=False,
+                               k_offset=np.asarray(k_offset, dtype=np.float64), seed=seed)
 
 
 def surrogate_init(n_in, n_hidden, n_out, seed=0, out_gain=0.01):

@@ -39,6 +39,7 @@ def test_struct_layout_matches_header():
     assert p.basis_atom.offset == 32
     assert p.eps.offset % 8 == 0 and p.qhat.offset % 8 == 0
     assert p.prec.offset + 4 <= gw.ctypes.sizeof(p)
+    assert p.time_reversal.offset == p.prec.offset + 4
 
 
 def test_null_arguments_are_rejected_without_gpu():
