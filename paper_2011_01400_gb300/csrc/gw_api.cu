@@ -258,6 +258,12 @@ struct gw_plan_s {
   size_t ws_limit = 0;              // GW_WORKSPACE_LIMIT (bytes; 0 = no limit)
   int dev = -1;                     // CUDA device that was current at gw_plan_create
   bool trs = false;                 // time-reversal symmetric inputs (gw_problem.time_reversal)
+  // time reversal without a q -> 0 direction: Sigma_c(-k) = Sigma_c(k), so gw_g0w0 computes the
+  // target k with k <= -k only (d_ktab, n_krep) into d_sigtmp and fills the others from them
+  int* d_ktab = nullptr;
+  int* d_isrep = nullptr;
+  int n_krep = 0;
+  c128* d_sigtmp = nullptr;
   double *d_freq = nullptr, *d_fw = nullptr, *d_mu = nullptr;
   void* d_T1 = nullptr;     // c128 (FP64) or c64 (split)
   c128* d_Vh = nullptr;     // [NK][N][N] V(q)^1/2 (full, truncated at q=0)
@@ -854,6 +860,24 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
       return cleanup(fail(GW_ERR_ARG, "time_reversal is set but eps(-k) != eps(k) or V(-q) != conj(V(q)) (max "
                                       "differences " + std::to_string(v[0]) + ", " + std::to_string(v[2]) + ")"));
     P->trs = true;
+    if (prob->head_wings != 1) {
+      std::vector<int> rep, isrep(P->NK, 0);
+      for (int k = 0; k < P->NK; ++k) {
+        const int i3 = k % prob->nk[2], i2 = (k / prob->nk[2]) % prob->nk[1], i1 = k / (prob->nk[1] * prob->nk[2]);
+        const int mk = (((prob->nk[0] - i1) % prob->nk[0]) * prob->nk[1] + (prob->nk[1] - i2) % prob->nk[1]) *
+                           prob->nk[2] + (prob->nk[2] - i3) % prob->nk[2];
+        if (mk >= k) {
+          rep.push_back(k);
+          isrep[k] = 1;
+        }
+      }
+      P->n_krep = (int)rep.size();
+      if ((s = dalloc(P, &P->d_ktab, rep.size())) != GW_OK) return cleanup(s);
+      if ((s = dalloc(P, &P->d_isrep, isrep.size())) != GW_OK) return cleanup(s);
+      if ((s = dalloc(P, &P->d_sigtmp, (size_t)P->NK * P->nsig * nw)) != GW_OK) return cleanup(s);
+      CK(cudaMemcpy(P->d_ktab, rep.data(), sizeof(int) * rep.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(P->d_isrep, isrep.data(), sizeof(int) * isrep.size(), cudaMemcpyHostToDevice));
+    }
   }
   // V(q)^1/2; at q = 0 with head_wings split off the lambda = 1 eigenvector first
   const c128* V = reinterpret_cast<const c128*>(prob->V);
@@ -1232,7 +1256,9 @@ gw_status w_core(gw_plan_s* P, int q, const c128* X, c128* Wc) {
 
 // q term of Sigma_c from W^c(q), accumulated into sig ([N_k][n_sigma][nw])
 // target k in [k_lo, k_hi) (k_hi < 0: all)
-gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig, bool conjW = false, int k_lo = 0, int k_hi = -1) {
+// use_ktab: the target k of P->d_ktab (time reversal, Sigma_c(-k) = Sigma_c(k)) instead of a range
+gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig, bool conjW = false, int k_lo = 0, int k_hi = -1,
+                     bool use_ktab = false) {
   cudaStream_t st = P->st;
   const int N = P->N, nw = P->nw, NBd = P->NBd, nsig = P->nsig;
   const long long NN = (long long)N * N;
@@ -1240,14 +1266,17 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig, bool conjW 
   const double pref = -1.0 / (2.0 * M_PI * P->NK);
   const int tf32 = P->prec == GW_3XTF32;
   if (!P->fp64) tc_w_planes(N, nw, P->Kx, Wc, P->d_Wpl, tf32, st, conjW ? 1 : 0);
-  const int k_end = k_hi < 0 ? P->NK : k_hi;
-  for (int kk0 = k_lo; kk0 < k_end; kk0 += P->sig_nkk) {
+  const int k_end = use_ktab ? P->n_krep : (k_hi < 0 ? P->NK : k_hi);
+  LriGeom geom = P->geom;                 // the M kernels map row blocks to target k through ktab
+  geom.ktab = use_ktab ? P->d_ktab : nullptr;
+  const int* ktab = geom.ktab;
+  for (int kk0 = use_ktab ? 0 : k_lo; kk0 < k_end; kk0 += P->sig_nkk) {
     const int nkk = std::min(P->sig_nkk, k_end - kk0);
     const int R = nkk * nsig * NBd;
     if (P->fp64) {
       c128* A = static_cast<c128*>(P->d_A);
       c128* U = static_cast<c128*>(P->d_U);
-      launch_mgen<double>(P->geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk,
+      launch_mgen<double>(geom, static_cast<const c128*>(P->d_T1), nullptr, evec, q, kk0, nkk,
                           MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, N, 1, st);
       for (int j = 0; j < nw; ++j) {
         launch_zgemm<double>(R, N, N, c128{1, 0}, A, N, 0, OP_N, Wc + j * NN, N, 0, conjW ? OP_CONJ : OP_N,
@@ -1258,7 +1287,7 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig, bool conjW 
       // rows a_r as an fp32 plane [R][Kx] (zero beyond n_aux), then the tensor-core contraction
       c64* A = static_cast<c64*>(P->d_A);
       if (!P->mtune.run(0, nsig, NBd, st, [&](int v) {
-            launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk,
+            launch_mgen<float>(geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk,
                                MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, P->Kx, 1, st, v);
           }))
         return fail(GW_ERR_CUDA, "M kernel autotuner: CUDA error");
@@ -1283,7 +1312,7 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig, bool conjW 
       }
     }
     launch_sigma_conv_chunk(kk0, nkk, nsig, NBd, P->p.nk, q, P->p.eps, P->d_mu, P->d_S_f, P->d_S_d, P->d_freq,
-                            P->d_fw, nw, pref, sig, P->fp64, st);
+                            P->d_fw, nw, pref, sig, P->fp64, st, ktab);
     GW_TRY(check_launch(P, "Sigma_c"));
   }
   return GW_OK;
@@ -1312,7 +1341,9 @@ int minus_q(const gw_plan_s* P, int q) {
   return (((n[0] - i1) % n[0]) * n[1] + (n[1] - i2) % n[1]) * n[2] + (n[2] - i3) % n[2];
 }
 
-gw_status g0w0_qlist(gw_plan_s* P, const std::vector<int>& qs_in, c128* sig) {
+// full: the list is the whole q mesh (then, with time reversal and no q -> 0 direction, only the
+// target k <= -k are computed and the others copied: Sigma_c(-k) = Sigma_c(k))
+gw_status g0w0_qlist(gw_plan_s* P, const std::vector<int>& qs_in, c128* sig_out, bool full = false) {
   cudaStream_t st = P->st;
   const int N = P->N, nw = P->nw;
   const long long NN = (long long)N * N;
@@ -1330,6 +1361,12 @@ gw_status g0w0_qlist(gw_plan_s* P, const std::vector<int>& qs_in, c128* sig) {
       partner.push_back(mq != q && in[mq] ? mq : -1);
     }
   }
+  const bool halve_k = full && P->d_ktab;
+  c128* sig = sig_out;
+  if (halve_k) {
+    sig = P->d_sigtmp;
+    GW_CUDA(cudaMemsetAsync(sig, 0, sizeof(c128) * (size_t)P->NK * P->nsig * nw, st));
+  }
   P->reset_timing();
   for (size_t g0 = 0; g0 < qs.size(); g0 += P->qb) {
     const int nq = (int)std::min<size_t>(P->qb, qs.size() - g0);
@@ -1344,10 +1381,14 @@ gw_status g0w0_qlist(gw_plan_s* P, const std::vector<int>& qs_in, c128* sig) {
       if (q[j] == 0 && P->p.head_wings == 2) GW_TRY(q0_average(P, P->g_E + j * slot));
     for (int j = 0; j < nq; ++j) GW_TRY(w_core(P, q[j], P->g_E + j * slot, P->g_chi0 + j * slot));
     for (int j = 0; j < nq; ++j) {
-      GW_TRY(sigma_core(P, q[j], P->g_chi0 + j * slot, sig));
-      if (qp[j] >= 0) GW_TRY(sigma_core(P, qp[j], P->g_chi0 + j * slot, sig, true));
+      GW_TRY(sigma_core(P, q[j], P->g_chi0 + j * slot, sig, false, 0, -1, halve_k));
+      if (qp[j] >= 0) GW_TRY(sigma_core(P, qp[j], P->g_chi0 + j * slot, sig, true, 0, -1, halve_k));
     }
     GW_TRY(read_status(P, "gw_g0w0"));
+  }
+  if (halve_k) {
+    launch_sigma_trs_fill(P->NK, P->nsig, nw, P->p.nk, P->d_isrep, sig, sig_out, st);
+    GW_TRY(check_launch(P, "Sigma_c time-reversal fill"));
   }
   GW_TRY(P->collect_timing());
   P->chi0_q = P->wc_q = -1;
@@ -1438,7 +1479,7 @@ gw_status gw_g0w0(gw_plan P, int32_t sys, gw_complex* sigma_acc) {
   c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
   std::vector<int> qs(P->NK);
   for (int q = 0; q < P->NK; ++q) qs[q] = q;
-  return g0w0_qlist(P, qs, sig);
+  return g0w0_qlist(P, qs, sig, true);
 }
 
 gw_status gw_g0w0_qset(gw_plan P, int32_t sys, const int32_t* q_list, int32_t n_q, gw_complex* sigma_acc) {

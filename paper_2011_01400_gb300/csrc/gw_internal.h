@@ -55,6 +55,7 @@ struct LriGeom {
   int n_atoms, NK, NB, NBd, N, nR;
   int nk[3];
   double koff[3];              // shift of the k mesh (fractional); the q mesh is not shifted
+  const int* ktab;             // device: target k of row block kk0 + kk (NULL: k = kk0 + kk)
   int atom_b0[64], atom_nb[64], atom_x0[64], atom_nx[64];
   long long ctil_off[64];      // element offset of atom block in ctil_R
   long long t_off[64];         // element offset of atom block in T1/T2
@@ -133,7 +134,12 @@ void launch_rowdot(int R, int N, const cplx<T>* U, const cplx<T>* a, long long l
 // for the target k = kk0 + kk of one chunk of rows r = ((kk*nsig)+n)*NBd + m.
 void launch_sigma_conv_chunk(int kk0, int nkk, int nsig, int NBd, const int* nk, int q, const double* eps,
                              const double* mu, const float* S_f, const double* S_d, const double* freq,
-                             const double* gw, int nw, double pref, c128* sigma, bool fp64, cudaStream_t st);
+                             const double* gw, int nw, double pref, c128* sigma, bool fp64, cudaStream_t st,
+                             const int* ktab = nullptr);
+// sigma[k] += part[k] for the target k the pass computed, part[-k] for the others (time reversal:
+// Sigma_c(-k) = Sigma_c(k) when q -> 0 carries no direction); is_rep [NK]: 1 for computed k
+void launch_sigma_trs_fill(int NK, int nsig, int nw, const int* nk, const int* is_rep, const c128* part,
+                           c128* sigma, cudaStream_t st);
 void launch_qp(int NK, int nsig, int NBd, int sig_lo, int nw, const c128* sigma, const double* dxv,
                const double* eps, const double* mu, const double* freq, double* e_qp, int* conv,
                cudaStream_t st);

@@ -146,7 +146,7 @@ __device__ __forceinline__ void mgen_body(const LriGeom& g, const cplx<T>* __res
                                           const c128* __restrict__ evec, int q, int kk0, int mode, int a0, int na,
                                           int b0, int nb, Store store) {
   const int kk = blockIdx.x;
-  int ktgt = kk0 + kk;
+  int ktgt = g.ktab ? g.ktab[kk0 + kk] : kk0 + kk;
   int k3 = ktgt % g.nk[2], k2 = (ktgt / g.nk[2]) % g.nk[1], k1 = ktgt / (g.nk[1] * g.nk[2]);
   int q3 = q % g.nk[2], q2 = (q / g.nk[2]) % g.nk[1], q1 = q / (g.nk[1] * g.nk[2]);
   int kp;  // k' (b bands live here), k'+q (a bands live here)
@@ -230,7 +230,7 @@ __device__ __forceinline__ void mgen_smem_body(const LriGeom& g, const c64* __re
   const int kk = blockIdx.x;
   int A, mu0, cnt;
   if (!mgen_tile(g, blockIdx.y, A, mu0, cnt)) return;
-  int ktgt = kk0 + kk;
+  int ktgt = g.ktab ? g.ktab[kk0 + kk] : kk0 + kk;
   int k3 = ktgt % g.nk[2], k2 = (ktgt / g.nk[2]) % g.nk[1], k1 = ktgt / (g.nk[1] * g.nk[2]);
   int q3 = q % g.nk[2], q2 = (q / g.nk[2]) % g.nk[1], q1 = q / (g.nk[1] * g.nk[2]);
   int kp;

@@ -38,7 +38,7 @@ __global__ void k_sigma_conv(int nkk, int kk0, int nsig, int NBd, int n1, int n2
                              const double* __restrict__ eps, const double* __restrict__ mu_p,
                              const float* __restrict__ S_f, const double* __restrict__ S_d,
                              const double* __restrict__ freq, const double* __restrict__ gw, int nw, double pref,
-                             c128* __restrict__ sigma) {
+                             c128* __restrict__ sigma, const int* __restrict__ ktab) {
   extern __shared__ double sh[];
   double* fr = sh;
   double* gg = sh + nw;
@@ -51,7 +51,7 @@ __global__ void k_sigma_conv(int nkk, int kk0, int nsig, int NBd, int n1, int n2
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   const int w_i = t % nw, n = (t / nw) % nsig, kk = t / (nw * nsig);
-  const int k = kk0 + kk;
+  const int k = ktab ? ktab[kk0 + kk] : kk0 + kk;
   int k3 = k % n3, k2 = (k / n3) % n2, k1 = k / (n2 * n3);
   int q3 = q % n3, q2 = (q / n3) % n2, q1 = q / (n2 * n3);
   int kmq = (((k1 - q1 + n1) % n1) * n2 + ((k2 - q2 + n2) % n2)) * n3 + ((k3 - q3 + n3) % n3);
@@ -85,15 +85,39 @@ __global__ void k_sigma_conv(int nkk, int kk0, int nsig, int NBd, int n1, int n2
 
 void launch_sigma_conv_chunk(int kk0, int nkk, int nsig, int NBd, const int* nk, int q, const double* eps,
                              const double* mu, const float* S_f, const double* S_d, const double* freq,
-                             const double* gw, int nw, double pref, c128* sigma, bool fp64, cudaStream_t st) {
+                             const double* gw, int nw, double pref, c128* sigma, bool fp64, cudaStream_t st,
+                             const int* ktab) {
   int total = nkk * nsig * nw;
   size_t smem = 2 * nw * sizeof(double);
   if (fp64)
     ++::gw::g_launch_count, k_sigma_conv<double><<<(total + 127) / 128, 128, smem, st>>>(nkk, kk0, nsig, NBd, nk[0], nk[1], nk[2], q, eps,
-                                                                 mu, S_f, S_d, freq, gw, nw, pref, sigma);
+                                                                 mu, S_f, S_d, freq, gw, nw, pref, sigma, ktab);
   else
     ++::gw::g_launch_count, k_sigma_conv<float><<<(total + 127) / 128, 128, smem, st>>>(nkk, kk0, nsig, NBd, nk[0], nk[1], nk[2], q, eps,
-                                                                mu, S_f, S_d, freq, gw, nw, pref, sigma);
+                                                                mu, S_f, S_d, freq, gw, nw, pref, sigma, ktab);
+}
+
+__global__ void k_sigma_trs_fill(int NK, int nsig, int nw, int n1, int n2, int n3, const int* __restrict__ is_rep,
+                                 const c128* __restrict__ part, c128* __restrict__ sigma) {
+  const long long per_k = (long long)nsig * nw;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)NK * per_k;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e / per_k);
+    int src = k;
+    if (!is_rep[k]) {
+      const int k3 = k % n3, k2 = (k / n3) % n2, k1 = k / (n2 * n3);
+      src = (((n1 - k1) % n1) * n2 + (n2 - k2) % n2) * n3 + (n3 - k3) % n3;
+    }
+    const c128 v = part[(long long)src * per_k + e % per_k];
+    sigma[e].re += v.re;
+    sigma[e].im += v.im;
+  }
+}
+void launch_sigma_trs_fill(int NK, int nsig, int nw, const int* nk, const int* is_rep, const c128* part,
+                           c128* sigma, cudaStream_t st) {
+  const long long total = (long long)NK * nsig * nw;
+  ++::gw::g_launch_count, k_sigma_trs_fill<<<(int)std::min<long long>((total + 255) / 256, 152LL * 8), 256, 0, st>>>(
+      NK, nsig, nw, nk[0], nk[1], nk[2], is_rep, part, sigma);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -39,9 +39,13 @@ def pass_sigma(s, prec, trs, qs=None):
     return acc.cpu().numpy(), e, gap
 
 
+@pytest.mark.parametrize("hw", [1, 2])
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("3xfp16", 1e-6), ("3xtf32", 1e-6)])
-def test_pairs_give_the_full_pass(prec, tol):
-    s = make_system("cfg0", seed=31, nk=(3, 2, 1))          # q and -q differ for 4 of the 6 q
+def test_pairs_give_the_full_pass(prec, tol, hw):
+    """hw = 1: q -> 0 along one direction, which breaks k -> -k for Sigma_c, so only the q points are
+    paired; hw = 2 (direction average): Sigma_c(-k) = Sigma_c(k) too, and the pass computes the
+    target k <= -k only."""
+    s = make_system("cfg0", seed=31, nk=(3, 2, 1), head_wings=hw)   # q and -q differ for 4 of the 6 q
     assert s.trs
     sig_t, e_t, gap_t = pass_sigma(s, prec, True)
     sig_f, e_f, gap_f = pass_sigma(s, prec, False)
@@ -49,7 +53,7 @@ def test_pairs_give_the_full_pass(prec, tol):
     assert np.abs(sig_t - sig_f).max() <= tol * scale
     ref = O.g0w0(s)
     err = np.abs(sig_t - ref["sigma"]).max() * HA_MEV
-    print(f"{prec}: time reversal vs none {np.abs(sig_t - sig_f).max() / scale:.1e} rel, vs oracle {err:.2e} meV")
+    print(f"{prec} head_wings={hw}: time reversal vs none {np.abs(sig_t - sig_f).max() / scale:.1e} rel, vs oracle {err:.2e} meV")
     assert err <= (1e-6 if prec == "fp64" else 1.0)
     assert abs(gap_t - ref["gap"]) * HA_MEV <= (1e-6 if prec == "fp64" else 1.0)
 
