@@ -32,13 +32,13 @@
 // filled from the lower one afterwards. Work items (tile, K chunk, weight row) are assigned to the
 // persistent CTAs on the host, longest first to the least loaded CTA.
 //
-// Roles (480 threads):
+// Roles (736 threads):
 //   warp 0 (TMA):      B pieces, 128 rows x 128 B each per stage, SWIZZLE_128B
-//   warp 14 (TMA):     raw fp32 A rows, 64 rows x 128 B per ring slot, with the slot's 16 weights
+//   warp 22 (TMA):     raw fp32 A rows, 64 rows x 128 B per ring slot, with the slot's 16 weights
 //   warps 2-5:         transform: y = v x from the ring, split, write A1 / A2 pieces in the UMMA
 //                      K-major 128B-swizzled layout
 //   warp 1:            one elected thread issues tcgen05.mma (M = 128, N = tile columns)
-//   warps 6-13:        epilogue (two warps per TMEM lane quadrant, 64 columns each)
+//   warps 6-21:        epilogue (four warps per TMEM lane quadrant, 32 columns each)
 // All mbarrier waits are bounded; on expiry the kernel sets ST_TIMEOUT and unwinds.
 #include "gw_internal.h"
 #include "tc_ptx.cuh"
@@ -61,7 +61,7 @@ constexpr int BNU = 128;                 // nu columns per tile (at most)
 constexpr int TILE = 128 * ROWB;         // 16 KB: one piece of A ([A1; A2]) or B (128 rows)
 constexpr int SLOT = BMU * ROWB;         // 8 KB: raw ring slot, 64 rows x 32 floats (16 complex pairs)
 constexpr int WBYTES = 16 * 4;           // the weights of a slot's 16 pair rows
-constexpr int NTHREADS = 480;
+constexpr int NTHREADS = 736;           // 23 warps (roles below)
 constexpr uint32_t D1_COL = 0, D2_COL = 256, DBUF = 128;
 constexpr int LSH = 11;                  // F16: the low piece is scaled by 2^11
 
@@ -140,15 +140,16 @@ __device__ __forceinline__ void tld16(uint32_t taddr, uint32_t (&r)[16]) {
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
 }
-// acc[j] += f * D[t + j] for this thread's 64 columns
-__device__ __forceinline__ void drain(uint32_t t, float f, float (&acc)[64]) {
+// acc[j] += f * D[t + j] for this thread's 32 columns (both loads in flight, one wait)
+__device__ __forceinline__ void drain(uint32_t t, float f, float (&acc)[32]) {
+  uint32_t a[16], b[16];
+  tld16(t, a);
+  tld16(t + 16, b);
+  tmem_wait_ld();
 #pragma unroll
-  for (int c = 0; c < 64; c += 16) {
-    uint32_t a[16];
-    tld16(t + c, a);
-    tmem_wait_ld();
-#pragma unroll
-    for (int j = 0; j < 16; ++j) acc[c + j] = fmaf(f, __uint_as_float(a[j]), acc[c + j]);
+  for (int j = 0; j < 16; ++j) {
+    acc[j] = fmaf(f, __uint_as_float(a[j]), acc[j]);
+    acc[16 + j] = fmaf(f, __uint_as_float(b[j]), acc[16 + j]);
   }
 }
 
@@ -193,9 +194,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&t1full[b], 1);
-      mbar_init(&t1empty[b], 8);                // one per epilogue warp
+      mbar_init(&t1empty[b], 16);               // one per epilogue warp
       mbar_init(&t2full[b], 1);
-      mbar_init(&t2empty[b], 8);
+      mbar_init(&t2empty[b], 16);
     }
     for (int r = 0; r < RING; ++r) {
       mbar_init(&rfull[r], 1);
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
         }
       }
     }
-  } else if (warp == 14) {
+  } else if (warp == 22) {
     // ---------------- TMA producer: raw A rows and their weights into the ring ----------------
     if (lane == 0) {
       uint32_t gr = 0;
@@ -443,23 +444,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
         if (lane == 0) mbar_arrive(&full_a[s]);
       }
     }
-  } else if (warp >= 6 && warp <= 13) {
+  } else if (warp >= 6 && warp <= 21) {
     // ---------------- epilogue: drain D1 per stage, D2 per segment, FP64 flush ----------------
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
-    const int half = (warp - 6) >> 2;          // tile columns 64*half .. 64*half+63
+    const int cg = (warp - 6) >> 2;            // tile columns 32*cg .. 32*cg+31
     const int lrow = quad * 32 + lane;         // TMEM lane: Re (< 64) or Im (>= 64) of mu row lrow & 63
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     const float f2 = (KIND == K_F16) ? 1.0f / (float)(1 << LSH) : 1.0f;
     uint32_t gs = 0, gseg = 0;
     bool ok = true;
-    float acc[64];
+    float acc[32];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
     for (int it = it0; it < it1 && ok; ++it) {
       Tile tl;
       int t, s0, s1;
       decode(p, p.items[it], tl, t, s0, s1);
-      const int ncol = max(0, min(64, tl.ncols - 64 * half));
+      const int ncol = max(0, min(32, tl.ncols - 32 * cg));
       const int mu = tl.m0 + (lrow & 63);
       const int part = lrow >> 6;
       const double es = p.escale[t];
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
         if (!ok) break;
         tc_fence_after();
         // all 64 columns: the ones beyond the tile hold stale values that are never flushed
-        drain(tmem + lane_off + D1_COL + b * DBUF + 64 * half, 1.0f, acc);
+        drain(tmem + lane_off + D1_COL + b * DBUF + 32 * cg, 1.0f, acc);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&t1empty[b]);
@@ -478,21 +479,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
           ok = __all_sync(0xffffffffu, mbar_wait(&t2full[b2], (gseg >> 1) & 1, p.status));
           if (!ok) break;
           tc_fence_after();
-          drain(tmem + lane_off + D2_COL + b2 * DBUF + 64 * half, f2, acc);
+          drain(tmem + lane_off + D2_COL + b2 * DBUF + 32 * cg, f2, acc);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&t2empty[b2]);
           ++gseg;
           if (mu >= tl.m0 && mu < tl.mhi) {
-            const int c0 = tl.n0 + 64 * half;
+            const int c0 = tl.n0 + 32 * cg;
             double* o = p.out + 2 * (((long long)t * p.N + mu) * p.N + c0) + part;
             const int jmax = min(ncol, mu - c0 + 1);   // columns nu = c0 + j <= mu of the tile
 #pragma unroll
-            for (int j = 0; j < 64; ++j)
+            for (int j = 0; j < 32; ++j)
               if (j < jmax) atomicAdd(o + 2 * j, es * (double)acc[j]);
           }
 #pragma unroll
-          for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+          for (int j = 0; j < 32; ++j) acc[j] = 0.f;
         }
       }
     }

@@ -52,12 +52,14 @@ def rel_fro(a, b):
 @pytest.mark.parametrize("qcase", ["cfg1_q1", "cfg1_q0"])
 @pytest.mark.parametrize("prec,tol_chi,tol_w,tol_sig_mev",
                          [("3xbf16", 1e-6, 1e-4, 1.0), ("3xtf32", 1e-6, 1e-4, 1.0), ("3xfp16", 1e-6, 1e-4, 1.0),
-                          ("fp64", 1e-11, 1e-10, 1e-6)])
+                          ("fp64", 1e-11, 1e-9, 1e-6)])
 def test_cfg1_one_q_full_size(request, qcase, prec, tol_chi, tol_w, tol_sig_mev):
     """chi0 and Sigma_c hold their targets (1e-6 relative, 1 meV). W^c has none of its own: on the
     split path its screen products are FP32 (~1e-7 relative per term), and at the highest
     frequencies W^c = V^1/2 (eps~^-1 - 1) V^1/2 is a difference 1e-2..1e-3 of its terms, so its
-    relative error is bounded by 1e-4 (cfg1, q = 1: 1.2e-5)."""
+    relative error is bounded by 1e-4 (cfg1, q = 1: 1.2e-5). On the FP64 path the bound is 1e-9:
+    at q = 0 the Coulomb head eigenvalue (~40 here) enters W^c squared-root-wise on both sides and
+    the same difference of terms leaves 2e-10 (q = 1: 7.6e-11)."""
     from paper_2011_01400_gb300 import gw
     s, chi_ref, W_ref, sig_ref = request.getfixturevalue(qcase)
     Q = 0 if qcase == "cfg1_q0" else 1
