@@ -284,6 +284,27 @@ def timed_pass(gw, s, prec, torch, warm=1, qs=None):
     return out
 
 
+def fp64_gemm_peak(torch, n=4096, reps=5):
+    """Measured FP64 rate of this GPU: the best of `reps` CUDA-event-timed cuBLAS DGEMMs
+    (torch.matmul, n^3, 2 n^3 flops) after one warm-up. It is the denominator of the FP64
+    Cholesky-inverse's roofline fraction (that kernel runs on the same FP64 units)."""
+    a = torch.randn((n, n), dtype=torch.float64, device="cuda")
+    b = torch.randn((n, n), dtype=torch.float64, device="cuda")
+    c = torch.matmul(a, b)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    best = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        ev[0].record()
+        c = torch.matmul(a, b)
+        ev[1].record()
+        torch.cuda.synchronize()
+        t = ev[0].elapsed_time(ev[1]) / 1e3
+        best = t if best is None else min(best, t)
+    del a, b, c
+    return 2.0 * n ** 3 / best / 1e12
+
+
 def chi0_frac(prec, chi, s, T_rows, peak_bf16):
     """chi0 TFLOP/s (algorithmic), its fraction of the dense peak of the precision's operand type
     and the tensor-issued fraction (split products, compressed weight rows)."""
@@ -695,6 +716,14 @@ def run_device(args, system, world, rank):
             fp64_pass[p] = dict(step_s=tp, speedup=t64 / tp, max_abs_dE_qp_meV=float(abs(ep - e64).max() * ha),
                                 abs_dgap_meV=float(abs(gp - g64) * ha))
         line["fp64_pass"] = fp64_pass
+    if world == 1 and not args.no_extras:
+        # the FP64 Cholesky-inverse of eps~: its share of the step and its FP64 rate against a
+        # measured FP64 GEMM (4 N^3 flops per (q, w) matrix: N^3 / 2 complex multiply-adds)
+        peak64 = fp64_gemm_peak(torch)
+        nq = q_computed(s)
+        chol_flops = 4.0 * s.n_aux ** 3 * s.n_freq * nq
+        line["fp64_peak"] = dict(dgemm_tflops=peak64, method="cuBLAS DGEMM via torch.matmul, 4096^3, best of 5, "
+                                                           "CUDA events", cholesky_flops_per_step=chol_flops)
     if args.surrogate:
         line["surrogate"] = surrogate_bench(args, gw, torch)
     if args.batch:

@@ -310,7 +310,10 @@ struct gw_plan_s {
   unsigned* d_absmax = nullptr;  // largest |re|, |im| of the chi0 M plane (float bits)
   int* d_eB = nullptr;        // FP16: exponent of the B plane scale
   double* d_escale = nullptr; // [nw] factors of the drained chi0 sums
-  Chi0Plan* chi0plan = nullptr;   // work lists of the tcgen05 chi0 kernel
+  Chi0Plan* chi0plan = nullptr;   // work lists of the tcgen05 chi0 kernel (and the screen products)
+  float* d_hb[2] = {nullptr, nullptr};  // screen products: TF32 pieces of the Hermitian right operand
+  float* d_hones = nullptr;             // [Kpad] unit weights
+  double* d_hesc = nullptr;             // [nw]
   // frequency compression of the split-precision chi0 (k_compress.cu)
   // largest relative residual |W_j - sum_{t<T} E_jt v_t| / |W_j| over the frequencies j that the
   // compression may leave (computed in FP64 over all pair rows); 0 disables. 3e-8 is below the
@@ -771,6 +774,13 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
     ALLOC(P->d_Praw, (size_t)N * 2 * P->ldm);
     P->n_bpl = P->prec == GW_3XBF16 ? 3 : 2;
     ALLOC(P->d_absmax, 1);
+    {
+      const size_t kp = (size_t)(N + 31) / 32 * 32;
+      ALLOC(P->d_hb[0], (size_t)nw * N * 2 * kp);
+      ALLOC(P->d_hb[1], (size_t)nw * N * 2 * kp);
+      ALLOC(P->d_hones, kp);
+      ALLOC(P->d_hesc, (size_t)nw);
+    }
     ALLOC(P->d_eB, 1);
     ALLOC(P->d_escale, (size_t)nw);
     for (int i = 0; i < P->n_bpl; ++i) {
@@ -1174,6 +1184,31 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
   return GW_OK;
 }
 
+// C[b] = alpha A[b] H[b] on the tensor cores (split precision screen products; H Hermitian)
+gw_status herm_gemm(gw_plan_s* P, const c64* A, bool a_batch, const c128* H, bool h_batch, double alpha, c128* C) {
+  HermGemmArgs g{};
+  g.N = P->N;
+  g.nb = P->nw;
+  g.A = A;
+  g.a_batch = a_batch ? 1 : 0;
+  g.H64 = H;
+  g.h_batch = h_batch ? 1 : 0;
+  g.alpha = alpha;
+  g.C = C;
+  g.bpl[0] = P->d_hb[0];
+  g.bpl[1] = P->d_hb[1];
+  g.ones = P->d_hones;
+  g.escale = P->d_hesc;
+  g.status = P->d_status;
+  std::string err;
+  gw_status ts = herm_gemm_run(g, &P->chi0plan, P->st, err);
+  if (ts != GW_OK) {
+    P->err = 1;
+    return fail(ts, "screen product: " + err);
+  }
+  return GW_OK;
+}
+
 // eps~(q) = 1 - V^1/2 chi0 V^1/2 (head and wings at q = 0) into E ([nw][N][N], FP64)
 gw_status eps_core(gw_plan_s* P, int q, const c128* chi0, c128* E) {
   cudaStream_t st = P->st;
@@ -1191,12 +1226,18 @@ gw_status eps_core(gw_plan_s* P, int q, const c128* chi0, c128* E) {
     launch_zgemm<double>(N, N, N, one, chi0, N, NN, OP_N, Vin, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
     launch_zgemm<double>(N, N, N, mone, Vin, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, E, N, NN, nw, st);
   } else {
+    // V^1/2 chi0 V^1/2 as (V^1/2 chi0) V^1/2: both right operands are Hermitian, the form of the
+    // tensor-core kernel (TF32 two-piece products, FP64 accumulation)
     const c64* Vh32 = P->d_Vh32 + (long long)q * NN;
     const c64* Vin32 = hw ? P->d_Vb32 : Vh32;
-    launch_convert((int)(NN * nw), chi0, A32, st);
-    launch_zgemm<float>(N, N, N, one32, A32, N, NN, OP_N, Vin32, N, 0, OP_N, zero32, B32, N, NN, nw, st);
-    launch_zgemm<float>(N, N, N, mone32, Vin32, N, 0, OP_N, B32, N, NN, OP_N, zero32, C32, N, NN, nw, st);
-    launch_convert_back((int)(NN * nw), C32, E, st);
+    GW_TRY(herm_gemm(P, Vin32, false, chi0, true, 1.0, P->d_tmp));
+    launch_convert((int)(NN * nw), P->d_tmp, A32, st);
+    GW_TRY(herm_gemm(P, A32, true, Vin, false, -1.0, E));
+    (void)B32;
+    (void)C32;
+    (void)one32;
+    (void)zero32;
+    (void)mone32;
   }
   launch_axpby_identity<double>(N, E, NN, nw, 1.0, st);
   if (hw && P->p.head_wings == 1) {
@@ -1245,11 +1286,15 @@ gw_status w_core(gw_plan_s* P, int q, const c128* X, c128* Wc) {
     launch_zgemm<double>(N, N, N, one, X, N, NN, OP_N, Vh, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
     launch_zgemm<double>(N, N, N, one, Vh, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, Wc, N, NN, nw, st);
   } else {
+    // V^1/2 X V^1/2 as (V^1/2 X) V^1/2 (X = eps~^-1 - 1 and V^1/2 Hermitian)
     const c64* Vh32 = P->d_Vh32 + (long long)q * NN;
-    launch_convert((int)(NN * nw), X, A32, st);
-    launch_zgemm<float>(N, N, N, one32, A32, N, NN, OP_N, Vh32, N, 0, OP_N, zero32, B32, N, NN, nw, st);
-    launch_zgemm<float>(N, N, N, one32, Vh32, N, 0, OP_N, B32, N, NN, OP_N, zero32, C32, N, NN, nw, st);
-    launch_convert_back((int)(NN * nw), C32, Wc, st);
+    GW_TRY(herm_gemm(P, Vh32, false, X, true, 1.0, P->d_tmp));
+    launch_convert((int)(NN * nw), P->d_tmp, A32, st);
+    GW_TRY(herm_gemm(P, A32, true, Vh, false, 1.0, Wc));
+    (void)B32;
+    (void)C32;
+    (void)one32;
+    (void)zero32;
   }
   return check_launch(P, "W^c");
 }

@@ -214,6 +214,23 @@ struct Chi0Plan;
 void chi0_plan_free(Chi0Plan* p);
 gw_status chi0h_pieces(const Chi0hArgs& a, cudaStream_t st);
 gw_status chi0h_run(const Chi0hArgs& a, Chi0Plan** plan, cudaStream_t st, std::string& err);
+// C[b] = alpha A[b] H[b] (b < nb; complex N x N row-major, N even; H[b] Hermitian) on the same
+// tcgen05 kernel with unit weights, every element, TF32 two-piece operands, FP64 output (overwritten)
+struct HermGemmArgs {
+  int N, nb;
+  const c64* A;          // [a_batch ? nb : 1][N][N]
+  int a_batch;
+  const c128* H64;       // [h_batch ? nb : 1][N][N] FP64, or NULL and H32 given
+  const c64* H32;
+  int h_batch;
+  double alpha;
+  c128* C;               // [nb][N][N]
+  float* bpl[2];         // workspace: [(h_batch ? nb : 1) N][2 Kpad] fp32 each, Kpad = N rounded up to 32
+  float* ones;           // workspace [Kpad]
+  double* escale;        // workspace [nb]
+  int* status;
+};
+gw_status herm_gemm_run(const HermGemmArgs& a, Chi0Plan** plan, cudaStream_t st, std::string& err);
 // wtab[j][r] = 2 D_r / (w_j^2 + D_r^2) (0 for padding rows r >= K)
 void chi0h_weights(int K, int Kpad, int nw, const float* delta, const double* freq, float* wtab, cudaStream_t st);
 

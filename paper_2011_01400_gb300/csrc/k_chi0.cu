@@ -108,6 +108,9 @@ struct Chi0Params {
   const double* escale; // [T] factor applied to the drained sums (scale, and the F16 scales undone)
   double* out;          // [T][N][N] complex as (re, im) doubles, lower triangle accumulated
   int* status;
+  int lower;            // 1: lower triangle only (Hermitian result); 0: every element
+  int a_bstride;        // A rows of weight row / batch entry t start at t * a_bstride
+  int b_bstride;        // B rows of t start at t * b_bstride
 };
 
 struct Chi0Maps {
@@ -231,7 +234,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
           mbar_arrive_expect_tx(&full_b[s], NP * TILE);
           const int x = i * (ROWB / C::ESZ);
 #pragma unroll
-          for (int pc = 0; pc < NP; ++pc) tma_load_2d(st + pc * TILE, &maps.b[pc], &full_b[s], x, tl.n0);
+          for (int pc = 0; pc < NP; ++pc)
+            tma_load_2d(st + pc * TILE, &maps.b[pc], &full_b[s], x, t * p.b_bstride + tl.n0);
         }
       }
     }
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
           const int slot = gr % RING;
           if (!mbar_wait(&rempty[slot], ((gr / RING) & 1) ^ 1, p.status)) { ok = false; break; }
           mbar_arrive_expect_tx(&rfull[slot], SLOT + WBYTES);
-          tma_load_2d(ring + slot * SLOT, &maps.raw, &rfull[slot], i * 32, tl.m0);
+          tma_load_2d(ring + slot * SLOT, &maps.raw, &rfull[slot], i * 32, t * p.a_bstride + tl.m0);
           // pair rows 16 i .. 16 i + 15 (16-byte aligned: weight rows are a multiple of 32 floats apart)
           bulk_load(wbuf + slot * 16, wrow + 16 * i, WBYTES, &rfull[slot]);
         }
@@ -487,7 +491,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
           if (mu >= tl.m0 && mu < tl.mhi) {
             const int c0 = tl.n0 + 32 * cg;
             double* o = p.out + 2 * (((long long)t * p.N + mu) * p.N + c0) + part;
-            const int jmax = min(ncol, mu - c0 + 1);   // columns nu = c0 + j <= mu of the tile
+            // columns nu = c0 + j of the tile below N (and, for the lower triangle, <= mu)
+            const int jmax = min(ncol, (p.lower ? mu + 1 : p.N) - c0);
 #pragma unroll
             for (int j = 0; j < 32; ++j)
               if (j < jmax) atomicAdd(o + 2 * j, es * (double)acc[j]);
@@ -635,8 +640,16 @@ int sm_count() {
 
 // Tiles covering the lower triangle of an N x N matrix: mu blocks of 64 aligned to row N, nu
 // chunks of <= 128 columns up to the block's last row.
-std::vector<Tile> make_tiles(int N) {
+std::vector<Tile> make_tiles(int N, bool lower = true) {
   std::vector<Tile> v;
+  if (!lower) {
+    for (int m0 = 0; m0 < N; m0 += BMU)
+      for (int n0 = 0; n0 < N; n0 += BNU) {
+        const int w = std::min(BNU, N - n0);
+        v.push_back(Tile{m0, std::min(N, m0 + BMU), n0, (w + 15) / 16 * 16});
+      }
+    return v;
+  }
   for (int mhi = N; mhi > 0; mhi -= BMU) {
     const int m0 = std::max(0, mhi - BMU);
     for (int n0 = 0; n0 < mhi; n0 += BNU) {
@@ -680,7 +693,7 @@ void chi0_plan_free(Chi0Plan* p) { delete p; }
 // same-cost items of one tile and K chunk stay adjacent so that concurrent CTAs share their
 // operands in L2), each given to the least loaded CTA.
 static gw_status chi0_lists(Chi0Plan** pp, int N, int T, int nst, int seg, cudaStream_t st, Chi0Lists** out,
-                            std::string& err) {
+                            std::string& err, bool lower = true) {
   if (!*pp) {
     *pp = new (std::nothrow) Chi0Plan();
     if (!*pp) {
@@ -688,7 +701,7 @@ static gw_status chi0_lists(Chi0Plan** pp, int N, int T, int nst, int seg, cudaS
       return GW_ERR_NOMEM;
     }
   }
-  const std::array<int, 4> key{N, T, nst, seg};
+  const std::array<int, 4> key{lower ? N : -N, T, nst, seg};
   auto f = (*pp)->lists.find(key);
   if (f != (*pp)->lists.end()) {
     *out = f->second;
@@ -699,7 +712,7 @@ static gw_status chi0_lists(Chi0Plan** pp, int N, int T, int nst, int seg, cudaS
     err = "host allocation failed";
     return GW_ERR_NOMEM;
   }
-  const std::vector<Tile> tiles = make_tiles(N);
+  const std::vector<Tile> tiles = make_tiles(N, lower);
   const int nsm = sm_count();
   const int nseg = (nst + seg - 1) / seg;
   const long long base = (long long)tiles.size() * T;
@@ -814,6 +827,9 @@ gw_status chi0h_run(const Chi0hArgs& a, Chi0Plan** plan, cudaStream_t st, std::s
   prm.escale = a.escale;
   prm.out = reinterpret_cast<double*>(a.out);
   prm.status = a.status;
+  prm.lower = 1;
+  prm.a_bstride = 0;
+  prm.b_bstride = 0;
   if (a.events) cudaEventRecord(a.events[0], st);
   if (a.kind == 0) s = launch_chi0<K_F16>(maps, prm, P->grid, st, err);
   else if (a.kind == 1) s = launch_chi0<K_BF16>(maps, prm, P->grid, st, err);
@@ -821,6 +837,85 @@ gw_status chi0h_run(const Chi0hArgs& a, Chi0Plan** plan, cudaStream_t st, std::s
   if (s != GW_OK) return s;
   if (a.events) cudaEventRecord(a.events[1], st);
   return GW_OK;
+}
+
+// TF32 pieces of Hermitian matrices H (FP64 or FP32 complex, [rows][N]) as the B planes of the
+// product kernel: row r, K index 2k + {0: re, 1: im}, zero for k >= N (padding to Kpad)
+template <typename T>
+__global__ void k_h_pieces_tf32(long long rows, int N, int Kpad, const cplx<T>* __restrict__ H, float* __restrict__ p0,
+                                float* __restrict__ p1) {
+  const long long total = rows * Kpad;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / Kpad;
+    const int k = (int)(e % Kpad);
+    float xr = 0.f, xi = 0.f;
+    if (k < N) {
+      const cplx<T> v = H[r * N + k];
+      xr = (float)v.re;
+      xi = (float)v.im;
+    }
+    const float hr = tf32_rn(xr), hi = tf32_rn(xi);
+    reinterpret_cast<float2*>(p0)[e] = make_float2(hr, hi);
+    reinterpret_cast<float2*>(p1)[e] = make_float2(xr - hr, xi - hi);
+  }
+}
+
+__global__ void k_fill_d(double* p, int n, double v) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) p[e] = v;
+}
+__global__ void k_fill_f(float* p, int n, float v) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) p[e] = v;
+}
+
+gw_status herm_gemm_run(const HermGemmArgs& a, Chi0Plan** plan, cudaStream_t st, std::string& err) {
+  const int N = a.N, nb = a.nb;
+  if (N < 2 || N % 2 != 0 || nb < 1) {
+    err = "herm_gemm: N must be even and >= 2";
+    return GW_ERR_ARG;
+  }
+  const int Kpad = (N + 31) / 32 * 32;
+  const long long hrows = (long long)(a.h_batch ? nb : 1) * N;
+  const int grid = (int)std::min<long long>((hrows * Kpad + 255) / 256, 152LL * 16);
+  if (a.H64)
+    ++g_launch_count, k_h_pieces_tf32<double><<<grid, 256, 0, st>>>(hrows, N, Kpad, a.H64, a.bpl[0], a.bpl[1]);
+  else
+    ++g_launch_count, k_h_pieces_tf32<float><<<grid, 256, 0, st>>>(hrows, N, Kpad, a.H32, a.bpl[0], a.bpl[1]);
+  ++g_launch_count, k_fill_d<<<1, 256, 0, st>>>(a.escale, nb, a.alpha);
+  ++g_launch_count, k_fill_f<<<(Kpad + 255) / 256, 256, 0, st>>>(a.ones, Kpad, 1.0f);
+  if (cudaMemsetAsync(a.C, 0, sizeof(c128) * (size_t)nb * N * N, st) != cudaSuccess) {
+    err = "herm_gemm: memset failed";
+    return GW_ERR_CUDA;
+  }
+  const int RS = Kd<K_TF32>::RS;
+  const int nst = Kpad / RS;
+  Chi0Lists* L = nullptr;
+  gw_status s = chi0_lists(plan, N, nb, nst, nst, st, &L, err, false);
+  if (s != GW_OK) return s;
+  Chi0Maps maps;
+  for (int i = 0; i < 2; ++i)
+    if (!map2d(&maps.b[i], a.bpl[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * Kpad, hrows, BNU, err))
+      return GW_ERR_CUDA;
+  const long long arows = (long long)(a.a_batch ? nb : 1) * N;
+  if (!map2d(&maps.raw, a.A, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, 2LL * N, arows, BMU, err)) return GW_ERR_CUDA;
+  Chi0Params prm{};
+  prm.N = N;
+  prm.nst = nst;
+  prm.seg = nst;
+  prm.nchunk = L->nchunk;
+  prm.tiles = L->d_tiles;
+  prm.items = L->d_items;
+  prm.cta_off = L->d_off;
+  prm.T = nb;
+  prm.wtab = a.ones;
+  prm.wstride = 0;
+  prm.escale = a.escale;
+  prm.out = reinterpret_cast<double*>(a.C);
+  prm.status = a.status;
+  prm.lower = 0;
+  prm.a_bstride = a.a_batch ? N : 0;
+  prm.b_bstride = a.h_batch ? N : 0;
+  return launch_chi0<K_TF32>(maps, prm, L->grid, st, err);
 }
 
 void chi0h_weights(int K, int Kpad, int nw, const float* delta, const double* freq, float* wtab, cudaStream_t st) {
