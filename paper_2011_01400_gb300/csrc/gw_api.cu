@@ -1331,7 +1331,9 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig, bool conjW 
     } else {
       // rows a_r as an fp32 plane [R][Kx] (zero beyond n_aux), then the tensor-core contraction
       c64* A = static_cast<c64*>(P->d_A);
-      if (!P->mtune.run(0, nsig, NBd, st, [&](int v) {
+      if (!launch_mgen_sig(geom, static_cast<const c64*>(P->d_T1), evec, q, kk0, nkk, P->p.sigma_lo, nsig, NBd, A,
+                           P->Kx, 1, st) &&
+          !P->mtune.run(0, nsig, NBd, st, [&](int v) {
             launch_mgen<float>(geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk,
                                MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, P->Kx, 1, st, v);
           }))
@@ -1830,7 +1832,9 @@ gw_status sigma_core_sur(gw_plan_s* P, int q, const c128* Wc_c, const c128* U, c
       launch_sur_assemble<double>(R, nc, nw, k, S.d_jmap, S.d_Sc_d, Pm, coef, nf, Lmat, P->d_S_d, st);
     } else {
       c64* A = static_cast<c64*>(P->d_A);
-      if (!P->mtune.run(0, nsig, NBd, st, [&](int v) {
+      if (!launch_mgen_sig(P->geom, static_cast<const c64*>(P->d_T1), evec, q, kk0, nkk, P->p.sigma_lo, nsig, NBd,
+                           A, P->Kx, 1, st) &&
+          !P->mtune.run(0, nsig, NBd, st, [&](int v) {
             launch_mgen<float>(P->geom, static_cast<const c64*>(P->d_T1), nullptr, evec, q, kk0, nkk,
                                MAP_K_IS_KK_MINUS_Q, P->p.sigma_lo, nsig, 0, NBd, A, P->Kx, 1, st, v);
           }))

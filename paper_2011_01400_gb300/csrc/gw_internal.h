@@ -75,6 +75,10 @@ template <typename T>
 void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* T2, const c128* evec, int q,
                  int kk0, int nkk, MapMode mode, int a0, int na, int b0, int nb, cplx<T>* out, long long s_r,
                  long long s_mu, cudaStream_t st, int variant = 0);
+// Sigma_c rows of the split path, streamed (window of at most 8 bands, n_b(A) <= 48); returns
+// false when the shape is outside that range (the caller then uses launch_mgen<float>)
+bool launch_mgen_sig(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
+                     int nb, c64* out, long long s_r, long long s_mu, cudaStream_t st);
 // split planes for the tensor-core chi0 B operand: for row mu, K index 2r + {0: re, 1: im}
 // raw fp32 plane + B1/B2 split planes (3 BF16 pieces or 2 TF32 pieces each), see k_lri.cu
 // bplanes may be NULL (raw plane only); absmax (may be NULL) receives max |re|, |im| of the rows

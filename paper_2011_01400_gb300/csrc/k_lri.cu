@@ -383,6 +383,111 @@ void launch_mgen<float>(const LriGeom& g, const c64* T1, const c64* T2, const c1
   }
 }
 
+// Sigma_c rows, streamed (split-precision path). a_r(mu) = C^mu_{ab}(k, k - q) = M^mu_{ab}(k', q),
+// k' = k - q, a in the Sigma window (na <= SIG_NA, bands at k), b over the nb bands at k':
+//   M^mu_{ab} = sum_j c_{jb}(k') conj(T1^mu_{ja}(k)) + sum_i conj(c_{ia}(k)) T1^mu_{ib}(k'),
+// i, j over the n_b(A) basis functions of mu's atom A. The large operand is the slab
+// T1^mu(k')[i][b] (n_b(A) x nb per ABF): each thread owns one b and SIG_G ABFs of the block's
+// tile, reads the slabs once (coalesced along b) and the eigenvector c(k')[i][b] once for all of
+// them; the small pieces (T1^mu(k)[j][a] and c(k)[i][a] over the window) sit in shared memory.
+// The rows are HBM streams of arithmetic intensity ~4 flop/byte, so this is CUDA-core work.
+constexpr int SIG_NA = 8;   // largest Sigma window of this kernel
+constexpr int SIG_G = 4;    // ABFs per block
+
+__global__ void __launch_bounds__(128) k_mgen_sig(const __grid_constant__ LriGeom g, const c64* __restrict__ T1,
+                                                  const c128* __restrict__ evec, int q, int kk0, int a0, int na,
+                                                  int nb, c64* __restrict__ out, long long s_r, long long s_mu) {
+  __shared__ float2 sQ[SIG_G][48][SIG_NA];   // T1^mu(k)[j][a] (n_b(A) <= 48)
+  __shared__ float2 sC[48][SIG_NA];          // c(k)[i][a]
+  const int kk = blockIdx.x;
+  int t = blockIdx.y, A = 0;
+  for (; A < g.n_atoms; ++A) {
+    const int nt = (g.atom_nx[A] + SIG_G - 1) / SIG_G;
+    if (t < nt) break;
+    t -= nt;
+  }
+  if (A >= g.n_atoms) return;
+  const int mu0 = g.atom_x0[A] + t * SIG_G, cnt = min(SIG_G, g.atom_x0[A] + g.atom_nx[A] - mu0);
+  const int ktgt = g.ktab ? g.ktab[kk0 + kk] : kk0 + kk;
+  const int k3 = ktgt % g.nk[2], k2 = (ktgt / g.nk[2]) % g.nk[1], k1 = ktgt / (g.nk[1] * g.nk[2]);
+  const int q3 = q % g.nk[2], q2 = (q / g.nk[2]) % g.nk[1], q1 = q / (g.nk[1] * g.nk[2]);
+  const int kp = (((k1 - q1 + g.nk[0]) % g.nk[0]) * g.nk[1] + ((k2 - q2 + g.nk[1]) % g.nk[1])) * g.nk[2] +
+                 ((k3 - q3 + g.nk[2]) % g.nk[2]);
+  const int nbA = g.atom_nb[A], b0A = g.atom_b0[A], nxA = g.atom_nx[A];
+  const c128* ck = evec + (long long)kp * g.NB * g.NBd;     // c(k')
+  const c128* cq = evec + (long long)ktgt * g.NB * g.NBd;   // c(k)
+  for (int e = threadIdx.x; e < nbA * SIG_NA; e += blockDim.x) {
+    const int i = e / SIG_NA, a = e % SIG_NA;
+    float2 v = make_float2(0.f, 0.f);
+    if (a < na) {
+      const c128 c = cq[(long long)(b0A + i) * g.NBd + a0 + a];
+      v = make_float2((float)c.re, (float)c.im);
+    }
+    sC[i][a] = v;
+  }
+  for (int e = threadIdx.x; e < SIG_G * nbA * SIG_NA; e += blockDim.x) {
+    const int m = e / (nbA * SIG_NA), rest = e % (nbA * SIG_NA), j = rest / SIG_NA, a = rest % SIG_NA;
+    float2 v = make_float2(0.f, 0.f);
+    if (m < cnt && a < na) {
+      const c64 x = T1[g.t_off[A] + (((long long)ktgt * nxA + (mu0 - g.atom_x0[A] + m)) * nbA + j) * g.NBd + a0 + a];
+      v = make_float2(x.re, x.im);
+    }
+    sQ[m][j][a] = v;
+  }
+  __syncthreads();
+  const c64* U = T1 + g.t_off[A] + ((long long)kp * nxA + (mu0 - g.atom_x0[A])) * nbA * g.NBd;
+  const long long us = (long long)nbA * g.NBd;     // between the slabs of consecutive ABFs
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    float ar[SIG_G][SIG_NA], ai[SIG_G][SIG_NA];
+#pragma unroll
+    for (int m = 0; m < SIG_G; ++m)
+#pragma unroll
+      for (int a = 0; a < SIG_NA; ++a) ar[m][a] = ai[m][a] = 0.f;
+    for (int i = 0; i < nbA; ++i) {
+      const c128 cb = ck[(long long)(b0A + i) * g.NBd + b];
+      const float cr = (float)cb.re, ci = (float)cb.im;
+      float ur[SIG_G], ui[SIG_G];
+#pragma unroll
+      for (int m = 0; m < SIG_G; ++m) {
+        const c64 u = (m < cnt) ? U[m * us + (long long)i * g.NBd + b] : c64{0.f, 0.f};
+        ur[m] = u.re;
+        ui[m] = u.im;
+      }
+#pragma unroll
+      for (int a = 0; a < SIG_NA; ++a) {
+        const float2 d = sC[i][a];
+#pragma unroll
+        for (int m = 0; m < SIG_G; ++m) {
+          const float2 tq = sQ[m][i][a];
+          // c_{ib}(k') conj(T1^mu_{ia}(k)) + conj(c_{ia}(k)) T1^mu_{ib}(k')
+          ar[m][a] = fmaf(cr, tq.x, fmaf(ci, tq.y, fmaf(d.x, ur[m], fmaf(d.y, ui[m], ar[m][a]))));
+          ai[m][a] = fmaf(ci, tq.x, fmaf(-cr, tq.y, fmaf(d.x, ui[m], fmaf(-d.y, ur[m], ai[m][a]))));
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < SIG_NA; ++a) {
+      if (a >= na) continue;
+      const long long r = ((long long)kk * na + a) * nb + b;
+#pragma unroll
+      for (int m = 0; m < SIG_G; ++m)
+        if (m < cnt) out[r * s_r + (long long)(mu0 + m) * s_mu] = c64{ar[m][a], ai[m][a]};
+    }
+  }
+}
+
+bool launch_mgen_sig(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
+                     int nb, c64* out, long long s_r, long long s_mu, cudaStream_t st) {
+  if (na > SIG_NA) return false;
+  for (int A = 0; A < g.n_atoms; ++A)
+    if (g.atom_nb[A] > 48) return false;
+  int tiles = 0;
+  for (int A = 0; A < g.n_atoms; ++A) tiles += (g.atom_nx[A] + SIG_G - 1) / SIG_G;
+  dim3 grid(nkk, tiles);
+  ++::gw::g_launch_count, k_mgen_sig<<<grid, 128, 0, st>>>(g, T1, evec, q, kk0, a0, na, nb, out, s_r, s_mu);
+  return true;
+}
+
 // Operand planes for the tensor-core chi0 (row mu, K index kofs + 2r + {0, 1}):
 //   raw:  fp32 (re, im) of M^mu_r -- read by the transform warps that build the weighted A side;
 //   B1 pieces: split of (re, im);  B2 pieces: split of (-im, re)  (the complex product's second
