@@ -1126,7 +1126,9 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
         GW_CUDA(cudaMemsetAsync(P->d_delta_f + K, 0, sizeof(float) * (P->ldm - K), st));
       }
       GW_CUDA(cudaMemsetAsync(P->d_absmax, 0, sizeof(unsigned), st));
-      if (!P->mtune.run(1, na, nb, st, [&](int v) {
+      if (!launch_mgen_chi(P->geom, static_cast<const c64*>(P->d_T1), evec, q, kk0, nkk, P->nocc, na, 0, nb,
+                           P->d_Praw, 2 * P->ldm, 0, P->d_absmax, st) &&
+          !P->mtune.run(1, na, nb, st, [&](int v) {
             launch_mgen_planes(P->geom, static_cast<const c64*>(P->d_T1), evec, q, kk0, nkk, P->nocc, na, 0, nb,
                                P->d_Praw, nullptr, 2 * P->ldm, 0, 0, st, v, P->d_absmax);
           }))

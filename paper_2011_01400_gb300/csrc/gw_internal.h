@@ -79,6 +79,10 @@ void launch_mgen(const LriGeom& g, const cplx<T>* T1, const cplx<T>* T2, const c
 // false when the shape is outside that range (the caller then uses launch_mgen<float>)
 bool launch_mgen_sig(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
                      int nb, c64* out, long long s_r, long long s_mu, cudaStream_t st);
+// chi0 pair rows of the split path as the fp32 plane (streamed; at most 8 occupied bands,
+// n_b(A) <= 48), largest |re|, |im| into absmax; false outside that range
+bool launch_mgen_chi(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
+                     int b0, int nb, float* raw, long long ldk, long long kofs, unsigned* absmax, cudaStream_t st);
 // split planes for the tensor-core chi0 B operand: for row mu, K index 2r + {0: re, 1: im}
 // raw fp32 plane + B1/B2 split planes (3 BF16 pieces or 2 TF32 pieces each), see k_lri.cu
 // bplanes may be NULL (raw plane only); absmax (may be NULL) receives max |re|, |im| of the rows

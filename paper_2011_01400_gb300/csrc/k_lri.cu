@@ -488,6 +488,119 @@ bool launch_mgen_sig(const LriGeom& g, const c64* T1, const c128* evec, int q, i
   return true;
 }
 
+// chi0 pair rows, streamed (split-precision path): M^mu_{ab}(k, q) for a over na unoccupied bands
+// at k + q (the wide side) and b over nb <= CHI_NB occupied bands at k,
+//   M^mu_{ab} = sum_j c_{jb}(k) conj(T1^mu_{ja}(k + q)) + sum_i conj(c_{ia}(k + q)) T1^mu_{ib}(k),
+// written as the fp32 plane raw[mu][kofs + 2 r + {0, 1}], r = (kk * na + a) * nb + b, with the
+// largest |re|, |im| into absmax. Each thread owns one a and SIG_G ABFs: the slabs
+// T1^mu(k + q)[j][a] and c(k + q)[i][a] are read once along a; T1^mu(k)[i][b] and c(k)[j][b] sit
+// in shared memory.
+constexpr int CHI_NB = 8;
+
+__global__ void __launch_bounds__(128) k_mgen_chi(const __grid_constant__ LriGeom g, const c64* __restrict__ T1,
+                                                  const c128* __restrict__ evec, int q, int kk0, int a0, int na,
+                                                  int b0, int nb, float* __restrict__ raw, long long ldk,
+                                                  long long kofs, unsigned* __restrict__ absmax) {
+  __shared__ float2 sT[SIG_G][48][CHI_NB];   // T1^mu(k)[i][b]
+  __shared__ float2 sC[48][CHI_NB];          // c(k)[j][b]
+  const int kk = blockIdx.x;
+  int t = blockIdx.y, A = 0;
+  for (; A < g.n_atoms; ++A) {
+    const int nt = (g.atom_nx[A] + SIG_G - 1) / SIG_G;
+    if (t < nt) break;
+    t -= nt;
+  }
+  float amax = 0.f;
+  if (A < g.n_atoms) {
+    const int mu0 = g.atom_x0[A] + t * SIG_G, cnt = min(SIG_G, g.atom_x0[A] + g.atom_nx[A] - mu0);
+    const int k = g.ktab ? g.ktab[kk0 + kk] : kk0 + kk;
+    const int k3 = k % g.nk[2], k2 = (k / g.nk[2]) % g.nk[1], k1 = k / (g.nk[1] * g.nk[2]);
+    const int q3 = q % g.nk[2], q2 = (q / g.nk[2]) % g.nk[1], q1 = q / (g.nk[1] * g.nk[2]);
+    const int kq = (((k1 + q1) % g.nk[0]) * g.nk[1] + ((k2 + q2) % g.nk[1])) * g.nk[2] + ((k3 + q3) % g.nk[2]);
+    const int nbA = g.atom_nb[A], b0A = g.atom_b0[A], nxA = g.atom_nx[A];
+    const c128* ck = evec + (long long)k * g.NB * g.NBd;
+    const c128* ckq = evec + (long long)kq * g.NB * g.NBd;
+    for (int e = threadIdx.x; e < nbA * CHI_NB; e += blockDim.x) {
+      const int j = e / CHI_NB, b = e % CHI_NB;
+      float2 v = make_float2(0.f, 0.f);
+      if (b < nb) {
+        const c128 c = ck[(long long)(b0A + j) * g.NBd + b0 + b];
+        v = make_float2((float)c.re, (float)c.im);
+      }
+      sC[j][b] = v;
+    }
+    for (int e = threadIdx.x; e < SIG_G * nbA * CHI_NB; e += blockDim.x) {
+      const int m = e / (nbA * CHI_NB), rest = e % (nbA * CHI_NB), i = rest / CHI_NB, b = rest % CHI_NB;
+      float2 v = make_float2(0.f, 0.f);
+      if (m < cnt && b < nb) {
+        const c64 x = T1[g.t_off[A] + (((long long)k * nxA + (mu0 - g.atom_x0[A] + m)) * nbA + i) * g.NBd + b0 + b];
+        v = make_float2(x.re, x.im);
+      }
+      sT[m][i][b] = v;
+    }
+    __syncthreads();
+    const c64* U = T1 + g.t_off[A] + ((long long)kq * nxA + (mu0 - g.atom_x0[A])) * nbA * g.NBd;
+    const long long us = (long long)nbA * g.NBd;
+    for (int a = threadIdx.x; a < na; a += blockDim.x) {
+      float ar[SIG_G][CHI_NB], ai[SIG_G][CHI_NB];
+#pragma unroll
+      for (int m = 0; m < SIG_G; ++m)
+#pragma unroll
+        for (int b = 0; b < CHI_NB; ++b) ar[m][b] = ai[m][b] = 0.f;
+      for (int j = 0; j < nbA; ++j) {
+        const c128 ca = ckq[(long long)(b0A + j) * g.NBd + a0 + a];   // c_{ja}(k + q)
+        const float dr = (float)ca.re, di = (float)ca.im;
+        float ur[SIG_G], ui[SIG_G];
+#pragma unroll
+        for (int m = 0; m < SIG_G; ++m) {
+          const c64 u = (m < cnt) ? U[m * us + (long long)j * g.NBd + a0 + a] : c64{0.f, 0.f};   // T1^mu_{ja}(k+q)
+          ur[m] = u.re;
+          ui[m] = u.im;
+        }
+#pragma unroll
+        for (int b = 0; b < CHI_NB; ++b) {
+          const float2 c = sC[j][b];
+#pragma unroll
+          for (int m = 0; m < SIG_G; ++m) {
+            const float2 tk = sT[m][j][b];
+            // c_{jb}(k) conj(T1^mu_{ja}(k+q)) + conj(c_{ja}(k+q)) T1^mu_{jb}(k)
+            ar[m][b] = fmaf(c.x, ur[m], fmaf(c.y, ui[m], fmaf(dr, tk.x, fmaf(di, tk.y, ar[m][b]))));
+            ai[m][b] = fmaf(c.y, ur[m], fmaf(-c.x, ui[m], fmaf(dr, tk.y, fmaf(-di, tk.x, ai[m][b]))));
+          }
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < SIG_G; ++m) {
+        if (m >= cnt) continue;
+        float* row = raw + (long long)(mu0 + m) * ldk + kofs + 2 * (((long long)kk * na + a) * nb);
+#pragma unroll
+        for (int b = 0; b < CHI_NB; ++b) {
+          if (b >= nb) continue;
+          *reinterpret_cast<float2*>(row + 2 * b) = make_float2(ar[m][b], ai[m][b]);
+          amax = fmaxf(amax, fmaxf(fabsf(ar[m][b]), fabsf(ai[m][b])));
+        }
+      }
+    }
+  }
+  if (absmax) {
+    // every thread gets here (128 threads); non-negative floats order like their bit patterns
+    const unsigned mm = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+    if ((threadIdx.x & 31) == 0) atomicMax(absmax, mm);
+  }
+}
+
+bool launch_mgen_chi(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
+                     int b0, int nb, float* raw, long long ldk, long long kofs, unsigned* absmax, cudaStream_t st) {
+  if (nb > CHI_NB) return false;
+  for (int A = 0; A < g.n_atoms; ++A)
+    if (g.atom_nb[A] > 48) return false;
+  int tiles = 0;
+  for (int A = 0; A < g.n_atoms; ++A) tiles += (g.atom_nx[A] + SIG_G - 1) / SIG_G;
+  dim3 grid(nkk, tiles);
+  ++::gw::g_launch_count, k_mgen_chi<<<grid, 128, 0, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, raw, ldk, kofs, absmax);
+  return true;
+}
+
 // Operand planes for the tensor-core chi0 (row mu, K index kofs + 2r + {0, 1}):
 //   raw:  fp32 (re, im) of M^mu_r -- read by the transform warps that build the weighted A side;
 //   B1 pieces: split of (re, im);  B2 pieces: split of (-im, re)  (the complex product's second
