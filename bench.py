@@ -420,6 +420,24 @@ def surrogate_bench(args, gw, torch):
         sur_pass()  # warm-up (group buffers, module loading)
         (e_s, gap_s, _), t_sur = timed(sur_pass)
         (e_f, gap_f, _), t_full = timed(full_pass)
+        # the linear map alone: the network's output scale s (the last parameter) set to 0
+        nparam = gw.gw_surrogate_param_count(*dims)
+        theta = gw.gw_surrogate_get_params(model, torch.empty(nparam, device="cuda"))
+        th0 = theta.clone()
+        th0[-1] = 0.0
+        gw.gw_surrogate_set_params(model, th0)
+        e_l, gap_l, _ = sur_pass()
+        gw.gw_surrogate_set_params(model, theta)
+        # the plain method on the 12 coarse points alone (their own Gauss-Legendre grid: the
+        # chi0 / eps~ work of the surrogate pass without the reconstruction)
+        sys12 = make_system(args.config, seed=1000 * int(args.config[-1]) + 1, n_freq=nc)
+        pb12 = gw.Problem(sys12, args.prec)
+        plan12 = gw.gw_plan_create(pb12.prob)
+        try:
+            gw.gw_g0w0(plan12, 0)
+            e_12, gap_12, _ = gw.gw_qp(plan12, 0, sys12.n_k, nsig)
+        finally:
+            gw.gw_plan_destroy(plan12)
     finally:
         gw.gw_surrogate_destroy(model)
     ha = 27211.386
@@ -430,6 +448,10 @@ def surrogate_bench(args, gw, torch):
                 loss_last=float(hist[-1]) if len(hist) else None,
                 surrogate_step_s=t_sur, full_grid_step_s=t_full, speedup=t_full / t_sur,
                 max_abs_dE_qp_meV=float(abs(e_s - e_f).max() * ha), abs_dgap_meV=float(abs(gap_s - gap_f) * ha),
+                linear_only=dict(max_abs_dE_qp_meV=float(abs(e_l - e_f).max() * ha),
+                                 abs_dgap_meV=float(abs(gap_l - gap_f) * ha)),
+                plain_12_point_grid=dict(max_abs_dE_qp_meV=float(abs(e_12 - e_f).max() * ha),
+                                         abs_dgap_meV=float(abs(gap_12 - gap_f) * ha)),
                 error_reference="the plain method on the full 60-point grid, same precision, same system")
 
 
@@ -666,6 +688,8 @@ def run_device(args, system, world, rank):
                     q_loop="q-parallel (gw_g0w0_qset + Sigma_c sum over ranks)" if qshard else args.qloop,
                     global_batch=1 if qshard else world, seq_len=0, parallelism=mode if world > 1 else "single",
                     time_reversal=bool(getattr(s, "trs", False)),
+                    q0={0: "regular formula", 1: "head and wings along x", 2: "head and wings averaged over the "
+                        "direction of q -> 0 (128-point sphere rule)"}[s.head_wings],
                     q_chi0_computed=f"{q_computed(s)} of {s.n_k} (W^c(-q) = conj(W^c(q)) for the pairs)"
                     if getattr(s, "trs", False) else f"{s.n_k} of {s.n_k}",
                     l2="inputs larger than L2 (chi0 operand planes 0.8 GB per q)"),
@@ -706,7 +730,7 @@ def run_device(args, system, world, rank):
         # like for like at matched accuracy: the whole pass in FP64 and split precision on the
         # workload's band / ABF / frequency shape with a 3x3x3 k mesh
         from paper_2011_01400_gb300.synth import make_system
-        s3 = make_system(args.config, seed=replica_seed(args.config, 0), nk=(3, 3, 3))
+        s3 = make_system(args.config, seed=replica_seed(args.config, 0), nk=(3, 3, 3), head_wings=args.head_wings)
         t64, e64, g64, _ = timed_pass(gw, s3, "fp64", torch, warm=0)
         fp64_pass = dict(system=f"{args.config} shape on a 3x3x3 k mesh (27 k, 27 q), seed "
                                 f"{replica_seed(args.config, 0)}; plan + gw_g0w0 + gw_qp, CUDA events",
@@ -745,6 +769,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-slice", action="store_true")
     ap.add_argument("--qslice", type=int, default=2, help="cfg2: q points of the timed slice")
+    ap.add_argument("--head-wings", type=int, default=2, choices=[0, 1, 2],
+                    help="q -> 0: 2 = head and wings averaged over the direction of q (default), 1 = along x, "
+                         "0 = regular formula")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other split precisions and the FP64 pass on the 3x3x3 mesh")
     ap.add_argument("--qloop", default="g0w0", choices=["g0w0", "perq"],
@@ -769,6 +796,7 @@ def main():
     over = {}
     if args.nk:
         over["nk"] = tuple(int(x) for x in args.nk.split(","))
+    over["head_wings"] = args.head_wings
     system = make_system(args.config, seed=replica_seed(args.config, rank, args.parallel), **over)
     if args.impl == "reference":
         run_reference(args, system, world, rank)
