@@ -254,23 +254,25 @@ def g0w0_step(gw, plan_prob, s, torch, chi_ms, qloop="g0w0", qshard=False):
     return e, gap
 
 
-def timed_pass(gw, s, prec, torch, warm=1, qs=None):
+def timed_pass(gw, s, prec, torch, warm=1, qs=None, sigma=False):
     """One G0W0 pass of system s at precision prec (plan, the q loop, QP), CUDA-event timed on the
     current stream after `warm` untimed passes. qs: only these q points (gw_g0w0_qset, no QP).
-    Returns (seconds, e_qp, gap, (chi0 ms, chi0 flops))."""
+    Returns (seconds, e_qp, gap, (chi0 ms, chi0 flops)), and Sigma_c [N_k][n_sigma][n_freq] as a
+    fifth item when sigma is set (accumulated into a caller tensor, which the QP solve then reads)."""
     pb = gw.Problem(s, prec)
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     nsig = s.sigma_hi - s.sigma_lo
     out = None
     for i in range(warm + 1):
+        acc = torch.zeros((s.n_k, nsig, s.n_freq), dtype=torch.complex128, device="cuda") if sigma else None
         torch.cuda.synchronize()
         ev[0].record(stream)
         plan = gw.gw_plan_create(pb.prob)
         try:
             if qs is None:
-                gw.gw_g0w0(plan, 0)
-                e, gap, _ = gw.gw_qp(plan, 0, s.n_k, nsig)
+                gw.gw_g0w0(plan, 0, acc)
+                e, gap, _ = gw.gw_qp(plan, 0, s.n_k, nsig, sigma=acc)
             else:
                 acc = torch.zeros((s.n_k, nsig, s.n_freq), dtype=torch.complex128, device="cuda")
                 gw.gw_g0w0_qset(plan, 0, qs, acc)
@@ -281,7 +283,7 @@ def timed_pass(gw, s, prec, torch, warm=1, qs=None):
         ev[1].record(stream)
         torch.cuda.synchronize()
         out = (ev[0].elapsed_time(ev[1]) / 1e3, e, gap, chi)
-    return out
+    return out + (acc,) if sigma else out
 
 
 def fp64_gemm_peak(torch, n=4096, reps=5):
@@ -586,6 +588,7 @@ def run_slice(args, gw, torch, s, world, rank):
 
 
 def run_device(args, system, world, rank):
+    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -731,14 +734,18 @@ def run_device(args, system, world, rank):
         # workload's band / ABF / frequency shape with a 3x3x3 k mesh
         from paper_2011_01400_gb300.synth import make_system
         s3 = make_system(args.config, seed=replica_seed(args.config, 0), nk=(3, 3, 3), head_wings=args.head_wings)
-        t64, e64, g64, _ = timed_pass(gw, s3, "fp64", torch, warm=0)
+        t64, e64, g64, _, sig64 = timed_pass(gw, s3, "fp64", torch, warm=0, sigma=True)
         fp64_pass = dict(system=f"{args.config} shape on a 3x3x3 k mesh (27 k, 27 q), seed "
                                 f"{replica_seed(args.config, 0)}; plan + gw_g0w0 + gw_qp, CUDA events",
                          fp64_s=t64)
         for p in ("3xfp16", "3xbf16", "3xtf32"):
-            tp, ep, gp, _ = timed_pass(gw, s3, p, torch)
-            fp64_pass[p] = dict(step_s=tp, speedup=t64 / tp, max_abs_dE_qp_meV=float(abs(ep - e64).max() * ha),
-                                abs_dgap_meV=float(abs(gp - g64) * ha))
+            tp, ep, gp, _, sigp = timed_pass(gw, s3, p, torch, sigma=True)
+            de = abs(ep - e64)
+            kn = np.unravel_index(int(de.argmax()), de.shape)
+            fp64_pass[p] = dict(step_s=tp, speedup=t64 / tp, max_abs_dE_qp_meV=float(de.max() * ha),
+                                abs_dgap_meV=float(abs(gp - g64) * ha),
+                                max_abs_dsigma_c_meV=float((sigp - sig64).abs().max()) * ha,
+                                dE_qp_argmax_k_band=[int(kn[0]), int(kn[1]) + s3.sigma_lo])
         line["fp64_pass"] = fp64_pass
     if world == 1 and not args.no_extras:
         # the FP64 Cholesky-inverse of eps~: its share of the step and its FP64 rate against a
@@ -764,7 +771,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", default="cfg1", choices=list(WORKLOADS))
-    ap.add_argument("--prec", default="3xbf16", choices=["3xfp16", "3xbf16", "3xtf32", "fp64"])
+    ap.add_argument("--prec", default="3xfp16", choices=["3xfp16", "3xbf16", "3xtf32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-slice", action="store_true")

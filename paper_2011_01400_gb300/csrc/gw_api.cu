@@ -331,7 +331,6 @@ struct gw_plan_s {
   PlaneSet d_Wpl{};           // W^c split planes [nw*N][2*Kx]
   c64* d_Vh32 = nullptr;      // FP32 copies of V^1/2 for the split-precision screen
   c64* d_Vb32 = nullptr;
-  TcWorkspace tcws;
   // q-group buffers of gw_g0w0
   c128 *g_chi0 = nullptr, *g_E = nullptr, *g_work = nullptr;
   int qb = 0;
@@ -482,6 +481,56 @@ gw_status newton_schulz(gw_plan_s* P, const c128* V, c128* out, int batch, int i
   for (int i = 0; i < 5; ++i) {
     dfree_last(P);
   }
+  return GW_OK;
+}
+
+gw_status herm_gemm(gw_plan_s* P, const c64* A, bool a_batch, const c128* H64, const c64* H32, bool h_batch,
+                    double alpha, c128* C, int nb);
+
+// The same iteration on the tensor cores for the split path: its three products per step as TF32
+// two-piece products, FP64-accumulated, in chunks of n_freq matrices (the screen's product
+// workspace). The kernel multiplies by the conjugate transpose of the rows it is given, so every
+// right operand goes in as its conjugate transpose, written next to it when it is formed. (Y, Z and
+// T are Hermitian in exact arithmetic, but taking H^H for H, or projecting them on their Hermitian
+// parts, turns the rounding into a mode that grows after convergence; the plain products do not.)
+gw_status newton_schulz_tc(gw_plan_s* P, c128* Vio, int batch, int iters) {
+  const int N = P->N, nb = P->nw;
+  const long long s = (long long)N * N;
+  double* d_c;
+  c64 *Y, *Yh, *Z, *Zh, *Tm, *Th;
+  c128* C;
+  GW_TRY(dalloc(P, &d_c, batch));
+  GW_TRY(dalloc(P, &Y, s * nb));
+  GW_TRY(dalloc(P, &Yh, s * nb));
+  GW_TRY(dalloc(P, &Z, s * nb));
+  GW_TRY(dalloc(P, &Zh, s * nb));
+  GW_TRY(dalloc(P, &Tm, s * nb));
+  GW_TRY(dalloc(P, &Th, s * nb));
+  GW_TRY(dalloc(P, &C, s * nb));
+  ++::gw::g_launch_count, k_frob_scale<<<batch, 256, 0, P->st>>>(N, Vio, s, d_c);
+  for (int b0 = 0; b0 < batch; b0 += nb) {
+    const int n = std::min(nb, batch - b0);
+    dim3 g(std::min<long long>((s + 255) / 256, 1024), n);
+    ++::gw::g_launch_count, k_ns_init<float><<<g, 256, 0, P->st>>>(N, Vio + b0 * s, s, d_c + b0, Y, Z);
+    // Y0 = V / c is Hermitian and Z0 = I: their conjugate transposes are themselves
+    if (cudaMemcpyAsync(Yh, Y, sizeof(c64) * s * n, cudaMemcpyDeviceToDevice, P->st) != cudaSuccess ||
+        cudaMemcpyAsync(Zh, Z, sizeof(c64) * s * n, cudaMemcpyDeviceToDevice, P->st) != cudaSuccess)
+      return fail(GW_ERR_CUDA, "newton_schulz: copy failed");
+    for (int it = 0; it < iters; ++it) {
+      // T = 1.5 I - 0.5 Z Y;  Y <- Y T;  Z <- T Z
+      GW_TRY(herm_gemm(P, Z, true, nullptr, Yh, true, -0.5, C, n));
+      launch_take_both(N, C, s, n, 1.5f, Tm, Th, P->st);
+      GW_TRY(herm_gemm(P, Y, true, nullptr, Th, true, 1.0, C, n));
+      launch_take_both(N, C, s, n, 0.0f, Y, Yh, P->st);
+      GW_TRY(herm_gemm(P, Tm, true, nullptr, Zh, true, 1.0, C, n));
+      launch_take_both(N, C, s, n, 0.0f, Z, Zh, P->st);
+    }
+    ++::gw::g_launch_count, k_ns_final<float><<<g, 256, 0, P->st>>>(N, Y, s, d_c + b0, Vio + b0 * s);
+  }
+  GW_TRY(check_launch(P, "newton_schulz"));
+  cudaError_t e = cudaStreamSynchronize(P->st);
+  if (e != cudaSuccess) return fail(GW_ERR_CUDA, std::string("newton_schulz: ") + cudaGetErrorString(e));
+  for (int i = 0; i < 8; ++i) dfree_last(P);
   return GW_OK;
 }
 
@@ -908,6 +957,8 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
   }
   if (P->fp64)
     s = newton_schulz<double>(P, P->d_Vh, P->d_Vh, P->NK, 24);
+  else if (N % 2 == 0)
+    s = newton_schulz_tc(P, P->d_Vh, P->NK, 24);
   else
     s = newton_schulz<float>(P, P->d_Vh, P->d_Vh, P->NK, 24);
   if (s != GW_OK) return cleanup(s);
@@ -1186,14 +1237,17 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
   return GW_OK;
 }
 
-// C[b] = alpha A[b] H[b] on the tensor cores (split precision screen products; H Hermitian)
-gw_status herm_gemm(gw_plan_s* P, const c64* A, bool a_batch, const c128* H, bool h_batch, double alpha, c128* C) {
+// C[b] = alpha A[b] H[b] for b < nb on the tensor cores (split precision screen products; H
+// Hermitian, FP64 or FP32)
+gw_status herm_gemm(gw_plan_s* P, const c64* A, bool a_batch, const c128* H64, const c64* H32, bool h_batch,
+                    double alpha, c128* C, int nb) {
   HermGemmArgs g{};
   g.N = P->N;
-  g.nb = P->nw;
+  g.nb = nb;
   g.A = A;
   g.a_batch = a_batch ? 1 : 0;
-  g.H64 = H;
+  g.H64 = H64;
+  g.H32 = H32;
   g.h_batch = h_batch ? 1 : 0;
   g.alpha = alpha;
   g.C = C;
@@ -1209,6 +1263,9 @@ gw_status herm_gemm(gw_plan_s* P, const c64* A, bool a_batch, const c128* H, boo
     return fail(ts, "screen product: " + err);
   }
   return GW_OK;
+}
+gw_status herm_gemm(gw_plan_s* P, const c64* A, bool a_batch, const c128* H, bool h_batch, double alpha, c128* C) {
+  return herm_gemm(P, A, a_batch, H, nullptr, h_batch, alpha, C, P->nw);
 }
 
 // eps~(q) = 1 - V^1/2 chi0 V^1/2 (head and wings at q = 0) into E ([nw][N][N], FP64)
@@ -1354,7 +1411,7 @@ gw_status sigma_core(gw_plan_s* P, int q, const c128* Wc, c128* sig, bool conjW 
       a.tf32 = tf32;
       a.status = P->d_status;
       std::string err;
-      gw_status ts = tc_sigma_run(a, P->tcws, st, err);
+      gw_status ts = tc_sigma_run(a, st, err);
       if (ts != GW_OK) {
         P->err = 1;
         return fail(ts, err);
@@ -1855,7 +1912,7 @@ gw_status sigma_core_sur(gw_plan_s* P, int q, const c128* Wc_c, const c128* U, c
       a.tf32 = tf32;
       a.status = P->d_status;
       std::string err;
-      gw_status ts = tc_sigma_run(a, P->tcws, st, err);
+      gw_status ts = tc_sigma_run(a, st, err);
       if (ts != GW_OK) {
         P->err = 1;
         return fail(ts, err);

@@ -104,6 +104,7 @@ void launch_chi0_simt(int N, int K, const cplx<T>* Mt, long long ldm, const floa
 void launch_chol_inv_minus_I(int N, c128* A, int batch, long long stride, c128* work, int* status,
                              cudaStream_t st);
 template <typename T> void launch_axpby_identity(int N, cplx<T>* A, long long s, int batch, T diag, cudaStream_t st);
+void launch_take_both(int N, const c128* C, long long s, int batch, float d, c64* X, c64* XH, cudaStream_t st);
 void launch_convert(int n, const c128* in, c64* out, cudaStream_t st);
 void launch_convert_back(int n, const c64* in, c128* out, cudaStream_t st);
 // dominant eigenpair of a Hermitian matrix by power iteration (FP64)
@@ -152,35 +153,9 @@ void launch_qp(int NK, int nsig, int NBd, int sig_lo, int nw, const c128* sigma,
                const double* eps, const double* mu, const double* freq, double* e_qp, int* conv,
                cudaStream_t st);
 
-// k_tc.cu -- tcgen05 split-precision kernels
-struct TcChi0Args {
-  int N;            // n_aux
-  int Kpad;         // padded number of pair rows (multiple of the K chunk)
-  int K;            // valid rows
-  const float* raw;       // [N][2*Kpad] fp32 (re, im) of M, read by the A-side transform
-  const void* bpl[6];     // B1 pieces then B2 pieces, [N][2*Kpad] each (bf16 x3 or tf32 x2)
-  const float* delta;   // [Kpad] transition energies (0 for padding)
-  const double* freq;   // [nw]
-  int nw;
-  double scale;     // -(s / N_k)
-  c128* chi0;       // [nw][N][N]
-  int tf32;
-  int* status;
-  int seg_rows;     // pair rows per FP64 promotion segment
-  float* wtab;      // workspace [nw][Kpad] for the Lorentzian weights
-  int wtab_ready;   // 1: wtab already holds the nw weight rows (frequency compression), 0: fill it
-};
+// k_tc.cu -- tcgen05 split-precision Sigma_c contraction (and the chi0 / W^c plane helpers)
 struct PlaneSet {
   void* b[6];       // B1 pieces then B2 pieces
-};
-// device tables owned by a plan for the tensor-core launches
-struct TcWorkspace {
-  short2* tiles = nullptr;
-  int tile_cap = 0;
-  float* ones = nullptr;
-  int ones_cap = 0;
-  ~TcWorkspace();
-  gw_status ensure(int ntiles, int nones, cudaStream_t st, std::string& err);
 };
 struct TcSigmaArgs {
   int R;            // rows a_r = C^mu_{nm}(k, k-q) of this chunk
@@ -189,14 +164,12 @@ struct TcSigmaArgs {
   int nw;
   const float* raw; // [R][2*Kpad] fp32 (re, im) of a_r (zero beyond n_aux)
   const void* bpl[6];  // W^c planes [nw*N][2*Kpad] (B1 pieces then B2 pieces)
-  void* apl[2];     // A pieces [R][2*Kpad] (bf16 or tf32), written by tc_sigma_run from raw before the
-                    // launch; NULL: the kernel splits the rows itself
+  void* apl[2];     // workspace: A pieces [R][2*Kpad] (bf16 or tf32), written by tc_sigma_run from raw
   float* S;         // [R][nw] accumulated (zeroed by the caller)
   int tf32;
   int* status;
 };
-gw_status tc_chi0_run(const TcChi0Args& a, TcWorkspace& ws, cudaStream_t st, std::string& err);
-gw_status tc_sigma_run(const TcSigmaArgs& a, TcWorkspace& ws, cudaStream_t st, std::string& err);
+gw_status tc_sigma_run(const TcSigmaArgs& a, cudaStream_t st, std::string& err);
 // conj != 0: the planes of conj(W^c) (time reversal: W^c(-q) = conj(W^c(q)))
 void tc_w_planes(int N, int nw, int Kpad, const c128* Wc, const PlaneSet& P, int tf32, cudaStream_t st, int conj = 0);
 bool tc_available();

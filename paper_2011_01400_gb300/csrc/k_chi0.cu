@@ -60,34 +60,42 @@ constexpr int BMU = 64;                  // mu rows per tile
 constexpr int BNU = 128;                 // nu columns per tile (at most)
 constexpr int TILE = 128 * ROWB;         // 16 KB: one piece of A ([A1; A2]) or B (128 rows)
 constexpr int SLOT = BMU * ROWB;         // 8 KB: raw ring slot, 64 rows x 32 floats (16 complex pairs)
-constexpr int WBYTES = 16 * 4;           // the weights of a slot's 16 pair rows
+constexpr int WBYTES = 16 * 4;           // the weights of a slot's 16 pair rows (one weight row)
 constexpr int NTHREADS = 736;           // 23 warps (roles below)
 constexpr uint32_t D1_COL = 0, D2_COL = 256, DBUF = 128;
 constexpr int LSH = 11;                  // F16: the low piece is scaled by 2^11
+constexpr int TP_F16 = 1, TP_TF32 = 1;   // weight rows per work item (measured: 2 is slower)
 
 enum { K_F16 = 0, K_BF16 = 1, K_TF32 = 2 };
 
 // Shared memory: a ring of SB B stages (TMA runs up to SB - 1 stages ahead of the MMAs, which
 // covers the L2 / HBM latency), SA buffers of split A pieces (written by the transform just in
 // time), and the raw-row ring of RING slots with their weights.
-template <int KIND> struct Kd {
+// TP weight rows per work item share the loaded operands: the raw A rows and the B rows of a
+// stage are loaded once and feed TP weighted A operands (each its own NT = 128 / TP accumulator
+// columns), so with TP = 2 a stage of the same MMA work loads 32 KB instead of 48 KB (F16: B
+// rows 2 x 64 instead of 2 x 128, raw rows unchanged). The kernel streams its operands from L2
+// and is bound by that stream; the price is twice the transform work per loaded raw row.
+template <int KIND, int TP> struct Kd {
   static constexpr int NP = (KIND == K_BF16) ? 3 : 2;       // pieces per operand
   static constexpr int ESZ = (KIND == K_TF32) ? 4 : 2;      // bytes per element
   static constexpr int RPS = (KIND == K_TF32) ? 1 : 2;      // ring slots per stage
   static constexpr int RS = 16 * RPS;                       // complex pair rows per stage
-  static constexpr int BST = NP * TILE;                     // one B stage (or one A buffer)
+  static constexpr int NT = BNU / TP;                       // nu columns per weight row
+  static constexpr int BST = NP * NT * ROWB;                // one B stage (NT rows per piece)
+  static constexpr int AST = TP * NP * TILE;                // one A buffer (TP weighted operands)
   static constexpr int SB = (KIND == K_BF16) ? 2 : 4;       // B stages
   static constexpr int SA = 2;                              // A buffers
   static constexpr int RING = (KIND == K_BF16) ? 2 : 4;     // raw ring slots
   static constexpr int A_OFF = SB * BST;
-  static constexpr int RING_OFF = A_OFF + SA * BST;
+  static constexpr int RING_OFF = A_OFF + SA * AST;
   static constexpr int WB_OFF = RING_OFF + RING * SLOT;
-  static constexpr int BAR_OFF = WB_OFF + RING * WBYTES;
+  static constexpr int BAR_OFF = WB_OFF + RING * TP * WBYTES;
   static constexpr int SMEM = BAR_OFF + 256 + 1024;
 };
-static_assert(Kd<K_F16>::SMEM <= 232448, "shared memory budget");
-static_assert(Kd<K_BF16>::SMEM <= 232448, "shared memory budget");
-static_assert(Kd<K_TF32>::SMEM <= 232448, "shared memory budget");
+static_assert(Kd<K_F16, 1>::SMEM <= 232448 && Kd<K_F16, 2>::SMEM <= 232448, "shared memory budget");
+static_assert(Kd<K_BF16, 1>::SMEM <= 232448, "shared memory budget");
+static_assert(Kd<K_TF32, 1>::SMEM <= 232448 && Kd<K_TF32, 2>::SMEM <= 232448, "shared memory budget");
 
 struct Tile {
   int m0, mhi;     // mu rows [m0, m0 + 64) loaded; rows [m0, mhi) owned by this tile
@@ -100,9 +108,10 @@ struct Chi0Params {
   int seg;              // stages per promotion segment
   int nchunk;           // K chunks (runs of whole segments) per tile
   const Tile* tiles;
-  const int* items;     // item = (tile * nchunk + chunk) * T + t, grouped per CTA
+  const int* items;     // item = (tile * nchunk + chunk) * TG + g (weight rows g TP ..), grouped per CTA
   const int* cta_off;   // [gridDim.x + 1] range of each CTA in items
-  int T;
+  int T;                // weight rows (or batch entries)
+  int TG;               // groups of TP consecutive weight rows: ceil(T / TP)
   const float* wtab;    // [T][wstride] weights (F16: already multiplied by the row's scale)
   long long wstride;
   const double* escale; // [T] factor applied to the drained sums (scale, and the F16 scales undone)
@@ -118,9 +127,11 @@ struct Chi0Maps {
   CUtensorMap raw;      // fp32 plane, 32 floats x 64 rows per box
 };
 
+// t: the first weight row of the item's group (TP consecutive rows, those >= T are not computed)
+template <int TP>
 __device__ __forceinline__ void decode(const Chi0Params& p, int item, Tile& tl, int& t, int& s0, int& s1) {
-  t = item % p.T;
-  const int tc = item / p.T;
+  t = (item % p.TG) * TP;
+  const int tc = item / p.TG;
   tl = p.tiles[tc / p.nchunk];
   const int c = tc % p.nchunk;
   const int nseg = (p.nst + p.seg - 1) / p.seg;
@@ -161,14 +172,15 @@ __device__ __forceinline__ void mma_k(uint32_t d, uint64_t a, uint64_t b, uint32
   mma<KIND == K_TF32>(d, a, b, idesc, acc);
 }
 
-template <int KIND>
+template <int KIND, int TP>
 __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Chi0Maps maps, Chi0Params p) {
-  using C = Kd<KIND>;
-  constexpr int NP = C::NP, SB = C::SB, SA = C::SA, BST = C::BST, RPS = C::RPS, RING = C::RING;
+  using C = Kd<KIND, TP>;
+  constexpr int NP = C::NP, SB = C::SB, SA = C::SA, BST = C::BST, AST = C::AST, RPS = C::RPS, RING = C::RING;
+  constexpr int NT = C::NT;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = smem + C::RING_OFF;
-  float* wbuf = reinterpret_cast<float*>(smem + C::WB_OFF);   // [RING][16]
+  float* wbuf = reinterpret_cast<float*>(smem + C::WB_OFF);   // [RING][TP][16]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
   uint64_t* full_b = bars;                        // [SB] B stage landed
   uint64_t* empty_b = bars + SB;                  // [SB] B stage consumed by the MMAs
@@ -226,16 +238,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
       for (int it = it0; it < it1 && ok; ++it) {
         Tile tl;
         int t, s0, s1;
-        decode(p, p.items[it], tl, t, s0, s1);
+        decode<TP>(p, p.items[it], tl, t, s0, s1);
         for (int i = s0; i < s1; ++i, ++gs) {
           const int s = gs % SB;
           if (!mbar_wait(&empty_b[s], ((gs / SB) & 1) ^ 1, p.status)) { ok = false; break; }
           uint8_t* st = smem + s * BST;
-          mbar_arrive_expect_tx(&full_b[s], NP * TILE);
+          mbar_arrive_expect_tx(&full_b[s], BST);
           const int x = i * (ROWB / C::ESZ);
 #pragma unroll
           for (int pc = 0; pc < NP; ++pc)
-            tma_load_2d(st + pc * TILE, &maps.b[pc], &full_b[s], x, t * p.b_bstride + tl.n0);
+            tma_load_2d(st + pc * NT * ROWB, &maps.b[pc], &full_b[s], x, t * p.b_bstride + tl.n0);
         }
       }
     }
@@ -247,15 +259,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
       for (int it = it0; it < it1 && ok; ++it) {
         Tile tl;
         int t, s0, s1;
-        decode(p, p.items[it], tl, t, s0, s1);
-        const float* wrow = p.wtab + (long long)t * p.wstride;
+        decode<TP>(p, p.items[it], tl, t, s0, s1);
         for (int i = s0 * RPS; i < s1 * RPS; ++i, ++gr) {
           const int slot = gr % RING;
           if (!mbar_wait(&rempty[slot], ((gr / RING) & 1) ^ 1, p.status)) { ok = false; break; }
-          mbar_arrive_expect_tx(&rfull[slot], SLOT + WBYTES);
+          mbar_arrive_expect_tx(&rfull[slot], SLOT + TP * WBYTES);
           tma_load_2d(ring + slot * SLOT, &maps.raw, &rfull[slot], i * 32, t * p.a_bstride + tl.m0);
-          // pair rows 16 i .. 16 i + 15 (16-byte aligned: weight rows are a multiple of 32 floats apart)
-          bulk_load(wbuf + slot * 16, wrow + 16 * i, WBYTES, &rfull[slot]);
+          // pair rows 16 i .. 16 i + 15 of each weight row of the group (16-byte aligned: weight rows
+          // are a multiple of 32 floats apart); rows past T repeat the last one (not computed)
+#pragma unroll
+          for (int u = 0; u < TP; ++u)
+            bulk_load(wbuf + (slot * TP + u) * 16, p.wtab + (long long)min(t + u, p.T - 1) * p.wstride + 16 * i,
+                      WBYTES, &rfull[slot]);
         }
       }
     }
@@ -268,9 +283,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
       for (int it = it0; it < it1 && ok; ++it) {
         Tile tl;
         int t, s0, s1;
-        decode(p, p.items[it], tl, t, s0, s1);
+        decode<TP>(p, p.items[it], tl, t, s0, s1);
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(tl.ncols >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
+        const int nt_valid = min(TP, p.T - t);   // weight rows of the group that exist
         for (int i = s0; i < s1; ++i, ++gs) {
           const int sb = gs % SB, sa = gs % SA;
           const int b = gs & 1, b2 = gseg & 1;
@@ -285,24 +301,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
           if (!mbar_wait(&full_a[sa], (gs / SA) & 1, p.status)) { ok = false; break; }
           tc_fence_after();
           const uint32_t bbase = smem_u32(smem + sb * BST);
-          const uint32_t abase = smem_u32(smem + C::A_OFF + sa * BST);
-          const uint32_t d1 = tmem + D1_COL + b * DBUF;
-          const uint32_t d2 = tmem + D2_COL + b2 * DBUF;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint32_t ko = kk * 32;
-            const uint32_t acc2 = (seg_first && kk == 0) ? 0u : 1u;
-            const uint64_t A0 = sdesc(abase + ko), B0 = sdesc(bbase + ko);
-            const uint64_t A1 = sdesc(abase + TILE + ko), B1 = sdesc(bbase + TILE + ko);
-            mma_k<KIND>(d2, A0, B1, idesc, acc2);
-            mma_k<KIND>(d2, A1, B0, idesc, 1u);
-            if constexpr (NP == 3) {
-              const uint64_t A2 = sdesc(abase + 2 * TILE + ko), B2 = sdesc(bbase + 2 * TILE + ko);
-              mma_k<KIND>(d2, A0, B2, idesc, 1u);
-              mma_k<KIND>(d2, A2, B0, idesc, 1u);
-              mma_k<KIND>(d2, A1, B1, idesc, 1u);
+          for (int u = 0; u < TP; ++u) {
+            if (u >= nt_valid) break;
+            const uint32_t abase = smem_u32(smem + C::A_OFF + sa * AST + u * NP * TILE);
+            const uint32_t d1 = tmem + D1_COL + b * DBUF + u * NT;
+            const uint32_t d2 = tmem + D2_COL + b2 * DBUF + u * NT;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint32_t ko = kk * 32;
+              const uint32_t acc2 = (seg_first && kk == 0) ? 0u : 1u;
+              const uint64_t A0 = sdesc(abase + ko), B0 = sdesc(bbase + ko);
+              const uint64_t A1 = sdesc(abase + TILE + ko), B1 = sdesc(bbase + NT * ROWB + ko);
+              mma_k<KIND>(d2, A0, B1, idesc, acc2);
+              mma_k<KIND>(d2, A1, B0, idesc, 1u);
+              if constexpr (NP == 3) {
+                const uint64_t A2 = sdesc(abase + 2 * TILE + ko), B2 = sdesc(bbase + 2 * NT * ROWB + ko);
+                mma_k<KIND>(d2, A0, B2, idesc, 1u);
+                mma_k<KIND>(d2, A2, B0, idesc, 1u);
+                mma_k<KIND>(d2, A1, B1, idesc, 1u);
+              }
+              mma_k<KIND>(d1, A0, B0, idesc, kk == 0 ? 0u : 1u);
             }
-            mma_k<KIND>(d1, A0, B0, idesc, kk == 0 ? 0u : 1u);
           }
           mma_commit(&empty_b[sb]);
           mma_commit(&empty_a[sa]);
@@ -326,20 +346,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
     for (int it = it0; it < it1 && ok; ++it) {
       Tile tl;
       int t, s0, s1;
-      decode(p, p.items[it], tl, t, s0, s1);
+      decode<TP>(p, p.items[it], tl, t, s0, s1);
       for (int i = s0; i < s1; ++i, ++gs, gr += RPS) {
         const int s = gs % SA;
         // warp-uniform waits: the arrivals below are elected per warp
         if (!__all_sync(0xffffffffu, mbar_wait(&empty_a[s], ((gs / SA) & 1) ^ 1, p.status))) { ok = false; break; }
-        uint8_t* at = smem + C::A_OFF + s * BST;
+        uint8_t* at = smem + C::A_OFF + s * AST;
         const uint32_t g = gr + (RPS == 2 ? h : 0);
         const int slot = g % RING;
         if (!__all_sync(0xffffffffu, mbar_wait(&rfull[slot], (g / RING) & 1, p.status))) { ok = false; break; }
         const uint8_t* rs = ring + slot * SLOT;
-        const float* wslot = wbuf + slot * 16;
+        const float* wslot = wbuf + slot * TP * 16;
         if constexpr (KIND == K_TF32) {
           // 8 pairs [8h, 8h + 8) of the slot: raw chunks 4h .. 4h + 3, A chunks 4h .. 4h + 3 (2 pairs each)
-          float x[16], wv[8];
+          float x[16], wv[TP][8];
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const float4 v = *reinterpret_cast<const float4*>(rs + swz(row, 4 * h + c));
@@ -349,22 +369,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
             x[4 * c + 3] = v.w;
           }
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const float4 v = reinterpret_cast<const float4*>(wslot + 8 * h)[c];
-            wv[4 * c] = v.x;
-            wv[4 * c + 1] = v.y;
-            wv[4 * c + 2] = v.z;
-            wv[4 * c + 3] = v.w;
-          }
+          for (int u = 0; u < TP; ++u)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const float4 v = reinterpret_cast<const float4*>(wslot + 16 * u + 8 * h)[c];
+              wv[u][4 * c] = v.x;
+              wv[u][4 * c + 1] = v.y;
+              wv[u][4 * c + 2] = v.z;
+              wv[u][4 * c + 3] = v.w;
+            }
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) mbar_arrive(&rempty[slot]);
 #pragma unroll
+          for (int u = 0; u < TP; ++u)
+#pragma unroll
           for (int c = 0; c < 4; ++c) {
+            uint8_t* au = at + u * NP * TILE;
             uint32_t h1[4], l1[4], h2[4], l2[4];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-              const float wt = wv[2 * c + q];
+              const float wt = wv[u][2 * c + q];
               const float yr = wt * x[4 * c + 2 * q], yi = wt * x[4 * c + 2 * q + 1];
               const float hr = tf32_rn(yr), hi = tf32_rn(yi);
               const float lr = yr - hr, li = yi - hi;
@@ -378,14 +403,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
               l2[2 * q + 1] = __float_as_uint(-lr);
             }
             const uint32_t o1 = swz(row, 4 * h + c), o2 = swz(row + 64, 4 * h + c);
-            *reinterpret_cast<uint4*>(at + o1) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
-            *reinterpret_cast<uint4*>(at + o2) = make_uint4(h2[0], h2[1], h2[2], h2[3]);
-            *reinterpret_cast<uint4*>(at + TILE + o1) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
-            *reinterpret_cast<uint4*>(at + TILE + o2) = make_uint4(l2[0], l2[1], l2[2], l2[3]);
+            *reinterpret_cast<uint4*>(au + o1) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
+            *reinterpret_cast<uint4*>(au + o2) = make_uint4(h2[0], h2[1], h2[2], h2[3]);
+            *reinterpret_cast<uint4*>(au + TILE + o1) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
+            *reinterpret_cast<uint4*>(au + TILE + o2) = make_uint4(l2[0], l2[1], l2[2], l2[3]);
           }
         } else {
           // the slot's 16 pairs of this row: raw chunks 0..7; A chunks 4h .. 4h + 3 (4 pairs each)
-          float x[32], wv[16];
+          float x[32], wv[TP][16];
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             const float4 v = *reinterpret_cast<const float4*>(rs + swz(row, c));
@@ -395,24 +420,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
             x[4 * c + 3] = v.w;
           }
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const float4 v = reinterpret_cast<const float4*>(wslot)[c];
-            wv[4 * c] = v.x;
-            wv[4 * c + 1] = v.y;
-            wv[4 * c + 2] = v.z;
-            wv[4 * c + 3] = v.w;
-          }
+          for (int u = 0; u < TP; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const float4 v = reinterpret_cast<const float4*>(wslot + 16 * u)[c];
+              wv[u][4 * c] = v.x;
+              wv[u][4 * c + 1] = v.y;
+              wv[u][4 * c + 2] = v.z;
+              wv[u][4 * c + 3] = v.w;
+            }
           // order these generic-proxy reads before the TMA (async-proxy) refill of the slot
           fence_proxy_async();
           __syncwarp();
           if (lane == 0) mbar_arrive(&rempty[slot]);
 #pragma unroll
+          for (int u = 0; u < TP; ++u)
+#pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
+            uint8_t* au = at + u * NP * TILE;
             uint32_t o[NP][4], o2[NP][4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
               const int pr = 4 * cc + q;
-              const float wt = wv[pr];
+              const float wt = wv[u][pr];
               const float yr = wt * x[2 * pr], yi = wt * x[2 * pr + 1];
               if constexpr (KIND == K_F16) {
                 const __half2 hh = __floats2half2_rn(yr, yi);
@@ -437,8 +467,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
             const uint32_t off1 = swz(row, 4 * h + cc), off2 = swz(row + 64, 4 * h + cc);
 #pragma unroll
             for (int pc = 0; pc < NP; ++pc) {
-              *reinterpret_cast<uint4*>(at + pc * TILE + off1) = make_uint4(o[pc][0], o[pc][1], o[pc][2], o[pc][3]);
-              *reinterpret_cast<uint4*>(at + pc * TILE + off2) =
+              *reinterpret_cast<uint4*>(au + pc * TILE + off1) = make_uint4(o[pc][0], o[pc][1], o[pc][2], o[pc][3]);
+              *reinterpret_cast<uint4*>(au + pc * TILE + off2) =
                   make_uint4(o2[pc][0], o2[pc][1], o2[pc][2], o2[pc][3]);
             }
           }
@@ -451,7 +481,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
   } else if (warp >= 6 && warp <= 21) {
     // ---------------- epilogue: drain D1 per stage, D2 per segment, FP64 flush ----------------
     const int quad = warp & 3;                 // TMEM lanes 32*quad .. 32*quad+31
-    const int cg = (warp - 6) >> 2;            // tile columns 32*cg .. 32*cg+31
+    const int cg = (warp - 6) >> 2;            // TMEM columns 32*cg .. 32*cg+31 of a buffer
+    constexpr int CPT = 4 / TP;                // column groups per weight row
+    const int u = cg / CPT;                    // weight row t + u of the item's group
+    const int cw = 32 * (cg % CPT);            // first tile column of the group
     const int lrow = quad * 32 + lane;         // TMEM lane: Re (< 64) or Im (>= 64) of mu row lrow & 63
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     const float f2 = (KIND == K_F16) ? 1.0f / (float)(1 << LSH) : 1.0f;
@@ -463,11 +496,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
     for (int it = it0; it < it1 && ok; ++it) {
       Tile tl;
       int t, s0, s1;
-      decode(p, p.items[it], tl, t, s0, s1);
-      const int ncol = max(0, min(32, tl.ncols - 32 * cg));
+      decode<TP>(p, p.items[it], tl, t, s0, s1);
+      const int ncol = (t + u < p.T) ? max(0, min(32, tl.ncols - cw)) : 0;
       const int mu = tl.m0 + (lrow & 63);
       const int part = lrow >> 6;
-      const double es = p.escale[t];
+      const double es = p.escale[min(t + u, p.T - 1)];
       for (int i = s0; i < s1; ++i, ++gs) {
         const int b = gs & 1;
         ok = __all_sync(0xffffffffu, mbar_wait(&t1full[b], (gs >> 1) & 1, p.status));
@@ -489,8 +522,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
           if (lane == 0) mbar_arrive(&t2empty[b2]);
           ++gseg;
           if (mu >= tl.m0 && mu < tl.mhi) {
-            const int c0 = tl.n0 + 32 * cg;
-            double* o = p.out + 2 * (((long long)t * p.N + mu) * p.N + c0) + part;
+            const int c0 = tl.n0 + cw;
+            double* o = p.out + 2 * (((long long)(t + u) * p.N + mu) * p.N + c0) + part;
             // columns nu = c0 + j of the tile below N (and, for the lower triangle, <= mu)
             const int jmax = min(ncol, (p.lower ? mu + 1 : p.N) - c0);
 #pragma unroll
@@ -639,30 +672,30 @@ int sm_count() {
 }
 
 // Tiles covering the lower triangle of an N x N matrix: mu blocks of 64 aligned to row N, nu
-// chunks of <= 128 columns up to the block's last row.
-std::vector<Tile> make_tiles(int N, bool lower = true) {
+// chunks of <= nt columns up to the block's last row.
+std::vector<Tile> make_tiles(int N, bool lower, int nt) {
   std::vector<Tile> v;
   if (!lower) {
     for (int m0 = 0; m0 < N; m0 += BMU)
-      for (int n0 = 0; n0 < N; n0 += BNU) {
-        const int w = std::min(BNU, N - n0);
+      for (int n0 = 0; n0 < N; n0 += nt) {
+        const int w = std::min(nt, N - n0);
         v.push_back(Tile{m0, std::min(N, m0 + BMU), n0, (w + 15) / 16 * 16});
       }
     return v;
   }
   for (int mhi = N; mhi > 0; mhi -= BMU) {
     const int m0 = std::max(0, mhi - BMU);
-    for (int n0 = 0; n0 < mhi; n0 += BNU) {
-      const int w = std::min(BNU, mhi - n0);
+    for (int n0 = 0; n0 < mhi; n0 += nt) {
+      const int w = std::min(nt, mhi - n0);
       v.push_back(Tile{m0, mhi, n0, (w + 15) / 16 * 16});
     }
   }
   return v;
 }
 
-// relative cost of one stage of a tile: the MMAs scale with the columns, the transform and the
-// operand loads do not
-double tile_cost(const Tile& t) { return std::max((double)t.ncols, 48.0); }
+// relative cost of one stage of a tile for nvalid weight rows: the MMAs scale with the columns
+// computed, the operand loads do not
+double tile_cost(const Tile& t, int nvalid) { return std::max((double)(t.ncols * nvalid), 48.0); }
 
 }  // namespace
 
@@ -681,7 +714,7 @@ struct Chi0Lists {
 
 // the launch shapes a plan has met (the weight-row count T may differ from one q to the next)
 struct Chi0Plan {
-  std::map<std::array<int, 4>, Chi0Lists*> lists;
+  std::map<std::array<int, 5>, Chi0Lists*> lists;
   ~Chi0Plan() {
     for (auto& kv : lists) delete kv.second;
   }
@@ -689,10 +722,10 @@ struct Chi0Plan {
 
 void chi0_plan_free(Chi0Plan* p) { delete p; }
 
-// Work lists for (N, T, nst, seg), built once per shape: items sorted by cost (longest first;
-// same-cost items of one tile and K chunk stay adjacent so that concurrent CTAs share their
-// operands in L2), each given to the least loaded CTA.
-static gw_status chi0_lists(Chi0Plan** pp, int N, int T, int nst, int seg, cudaStream_t st, Chi0Lists** out,
+// Work lists for (N, T, nst, seg, TP), built once per shape: items (a tile, a K chunk and a group
+// of TP weight rows) sorted by cost (longest first; same-cost items of one tile and K chunk stay
+// adjacent so that concurrent CTAs share their operands in L2), each given to the least loaded CTA.
+static gw_status chi0_lists(Chi0Plan** pp, int N, int T, int nst, int seg, int tp, cudaStream_t st, Chi0Lists** out,
                             std::string& err, bool lower = true) {
   if (!*pp) {
     *pp = new (std::nothrow) Chi0Plan();
@@ -701,7 +734,7 @@ static gw_status chi0_lists(Chi0Plan** pp, int N, int T, int nst, int seg, cudaS
       return GW_ERR_NOMEM;
     }
   }
-  const std::array<int, 4> key{lower ? N : -N, T, nst, seg};
+  const std::array<int, 5> key{lower ? N : -N, T, nst, seg, tp};
   auto f = (*pp)->lists.find(key);
   if (f != (*pp)->lists.end()) {
     *out = f->second;
@@ -712,10 +745,11 @@ static gw_status chi0_lists(Chi0Plan** pp, int N, int T, int nst, int seg, cudaS
     err = "host allocation failed";
     return GW_ERR_NOMEM;
   }
-  const std::vector<Tile> tiles = make_tiles(N, lower);
+  const std::vector<Tile> tiles = make_tiles(N, lower, BNU / tp);
   const int nsm = sm_count();
   const int nseg = (nst + seg - 1) / seg;
-  const long long base = (long long)tiles.size() * T;
+  const int TG = (T + tp - 1) / tp;
+  const long long base = (long long)tiles.size() * TG;
   int nchunk = 1;
   while (base * nchunk < 2LL * nsm && nchunk * 2 <= nseg) nchunk *= 2;
   std::vector<std::pair<double, int>> items;
@@ -723,7 +757,8 @@ static gw_status chi0_lists(Chi0Plan** pp, int N, int T, int nst, int seg, cudaS
     for (int c = 0; c < nchunk; ++c) {
       const int s0 = (int)((long long)c * nseg / nchunk) * seg;
       const int s1 = std::min(nst, (int)((long long)(c + 1) * nseg / nchunk) * seg);
-      for (int t = 0; t < T; ++t) items.push_back({tile_cost(tiles[ti]) * (s1 - s0), (ti * nchunk + c) * T + t});
+      for (int g = 0; g < TG; ++g)
+        items.push_back({tile_cost(tiles[ti], std::min(tp, T - g * tp)) * (s1 - s0), (ti * nchunk + c) * TG + g});
     }
   std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
   const int grid = (int)std::min<long long>((long long)items.size(), nsm);
@@ -764,11 +799,11 @@ static gw_status chi0_lists(Chi0Plan** pp, int N, int T, int nst, int seg, cudaS
   return GW_OK;
 }
 
-template <int KIND>
+template <int KIND, int TP>
 static gw_status launch_chi0(const Chi0Maps& maps, const Chi0Params& prm, int grid, cudaStream_t st, std::string& err) {
-  const int smem = Kd<KIND>::SMEM;
-  cudaFuncSetAttribute(k_chi0<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  ++g_launch_count, k_chi0<KIND><<<grid, NTHREADS, smem, st>>>(maps, prm);
+  const int smem = Kd<KIND, TP>::SMEM;
+  cudaFuncSetAttribute(k_chi0<KIND, TP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  ++g_launch_count, k_chi0<KIND, TP><<<grid, NTHREADS, smem, st>>>(maps, prm);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("k_chi0 launch: ") + cudaGetErrorString(e);
@@ -794,11 +829,12 @@ gw_status chi0h_run(const Chi0hArgs& a, Chi0Plan** plan, cudaStream_t st, std::s
     err = "chi0: Kpad must be a multiple of 32";
     return GW_ERR_ARG;
   }
-  const int RS = (a.kind == 2) ? Kd<K_TF32>::RS : Kd<K_F16>::RS;
+  const int RS = (a.kind == 2) ? Kd<K_TF32, 1>::RS : Kd<K_F16, 1>::RS;
   const int nst = a.Kpad / RS;
   const int seg = std::max(1, a.seg_rows / RS);
+  const int tp = a.kind == 0 ? TP_F16 : a.kind == 1 ? 1 : TP_TF32;
   Chi0Lists* P = nullptr;
-  gw_status s = chi0_lists(plan, a.N, a.T, nst, seg, st, &P, err);
+  gw_status s = chi0_lists(plan, a.N, a.T, nst, seg, tp, st, &P, err);
   if (s != GW_OK) return s;
   // weight-row scales (F16) and the factors of the drained sums
   ++g_launch_count, k_wscale<<<a.T, 256, 0, st>>>(a.Kpad, a.T, a.wtab, a.absmax, a.eB, a.scale, a.kind == 0 ? 1 : 0,
@@ -811,7 +847,7 @@ gw_status chi0h_run(const Chi0hArgs& a, Chi0Plan** plan, cudaStream_t st, std::s
   const int esz = a.kind == 2 ? 4 : 2;
   const int np = a.kind == 1 ? 3 : 2;
   for (int i = 0; i < np; ++i)
-    if (!map2d(&maps.b[i], a.bpl[i], dt, esz, ldk, a.N, BNU, err)) return GW_ERR_CUDA;
+    if (!map2d(&maps.b[i], a.bpl[i], dt, esz, ldk, a.N, BNU / tp, err)) return GW_ERR_CUDA;
   if (!map2d(&maps.raw, a.raw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, ldk, a.N, BMU, err)) return GW_ERR_CUDA;
   Chi0Params prm{};
   prm.N = a.N;
@@ -822,6 +858,7 @@ gw_status chi0h_run(const Chi0hArgs& a, Chi0Plan** plan, cudaStream_t st, std::s
   prm.items = P->d_items;
   prm.cta_off = P->d_off;
   prm.T = a.T;
+  prm.TG = (a.T + tp - 1) / tp;
   prm.wtab = a.wtab;
   prm.wstride = a.Kpad;
   prm.escale = a.escale;
@@ -831,9 +868,9 @@ gw_status chi0h_run(const Chi0hArgs& a, Chi0Plan** plan, cudaStream_t st, std::s
   prm.a_bstride = 0;
   prm.b_bstride = 0;
   if (a.events) cudaEventRecord(a.events[0], st);
-  if (a.kind == 0) s = launch_chi0<K_F16>(maps, prm, P->grid, st, err);
-  else if (a.kind == 1) s = launch_chi0<K_BF16>(maps, prm, P->grid, st, err);
-  else s = launch_chi0<K_TF32>(maps, prm, P->grid, st, err);
+  if (a.kind == 0) s = launch_chi0<K_F16, TP_F16>(maps, prm, P->grid, st, err);
+  else if (a.kind == 1) s = launch_chi0<K_BF16, 1>(maps, prm, P->grid, st, err);
+  else s = launch_chi0<K_TF32, TP_TF32>(maps, prm, P->grid, st, err);
   if (s != GW_OK) return s;
   if (a.events) cudaEventRecord(a.events[1], st);
   return GW_OK;
@@ -887,10 +924,10 @@ gw_status herm_gemm_run(const HermGemmArgs& a, Chi0Plan** plan, cudaStream_t st,
     err = "herm_gemm: memset failed";
     return GW_ERR_CUDA;
   }
-  const int RS = Kd<K_TF32>::RS;
+  const int RS = Kd<K_TF32, 1>::RS;
   const int nst = Kpad / RS;
   Chi0Lists* L = nullptr;
-  gw_status s = chi0_lists(plan, N, nb, nst, nst, st, &L, err, false);
+  gw_status s = chi0_lists(plan, N, nb, nst, nst, 1, st, &L, err, false);
   if (s != GW_OK) return s;
   Chi0Maps maps;
   for (int i = 0; i < 2; ++i)
@@ -907,6 +944,7 @@ gw_status herm_gemm_run(const HermGemmArgs& a, Chi0Plan** plan, cudaStream_t st,
   prm.items = L->d_items;
   prm.cta_off = L->d_off;
   prm.T = nb;
+  prm.TG = nb;
   prm.wtab = a.ones;
   prm.wstride = 0;
   prm.escale = a.escale;
@@ -915,7 +953,7 @@ gw_status herm_gemm_run(const HermGemmArgs& a, Chi0Plan** plan, cudaStream_t st,
   prm.lower = 0;
   prm.a_bstride = a.a_batch ? N : 0;
   prm.b_bstride = a.h_batch ? N : 0;
-  return launch_chi0<K_TF32>(maps, prm, L->grid, st, err);
+  return launch_chi0<K_TF32, 1>(maps, prm, L->grid, st, err);
 }
 
 void chi0h_weights(int K, int Kpad, int nw, const float* delta, const double* freq, float* wtab, cudaStream_t st) {

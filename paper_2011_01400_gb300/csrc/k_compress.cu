@@ -158,24 +158,37 @@ __global__ void k_wtab_compressed(int K, int Kpad, int nw, int T, const double* 
 }
 
 // chi0[j][e] += sum_t E[j][t] C[t][e]  for every frequency j and element e < NN
+// chi0[j] += sum_t E_jt C_t, 16 frequencies per pass (register accumulators; the C rows are
+// re-read once per pass, from L2)
 __global__ void k_expand(int nw, int T, long long NN, const double* __restrict__ E, const c128* __restrict__ C,
                          c128* __restrict__ chi0) {
+  constexpr int JB = 16;
   __shared__ double u[64 * 64];
   for (int e = threadIdx.x; e < nw * T; e += blockDim.x) u[e] = E[(e / T) * nw + (e % T)];
   __syncthreads();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < NN; e += (long long)gridDim.x * blockDim.x) {
-    c128 c[64];
-    for (int t = 0; t < T; ++t) c[t] = C[(long long)t * NN + e];
-    for (int j = 0; j < nw; ++j) {
-      double re = 0.0, im = 0.0;
+    for (int j0 = 0; j0 < nw; j0 += JB) {
+      double re[JB], im[JB];
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) re[jj] = im[jj] = 0.0;
       for (int t = 0; t < T; ++t) {
-        re += u[j * T + t] * c[t].re;
-        im += u[j * T + t] * c[t].im;
+        const c128 c = C[(long long)t * NN + e];
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+          const double w = (j0 + jj < nw) ? u[(j0 + jj) * T + t] : 0.0;
+          re[jj] = fma(w, c.re, re[jj]);
+          im[jj] = fma(w, c.im, im[jj]);
+        }
       }
-      c128 o = chi0[(long long)j * NN + e];
-      o.re += re;
-      o.im += im;
-      chi0[(long long)j * NN + e] = o;
+#pragma unroll
+      for (int jj = 0; jj < JB; ++jj) {
+        if (j0 + jj < nw) {
+          c128 o = chi0[(long long)(j0 + jj) * NN + e];
+          o.re += re[jj];
+          o.im += im[jj];
+          chi0[(long long)(j0 + jj) * NN + e] = o;
+        }
+      }
     }
   }
 }

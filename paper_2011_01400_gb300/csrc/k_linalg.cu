@@ -493,6 +493,38 @@ template <typename T> void launch_axpby_identity(int N, cplx<T>* A, long long s,
 template void launch_axpby_identity<double>(int, c128*, long long, int, double, cudaStream_t);
 template void launch_axpby_identity<float>(int, c64*, long long, int, float, cudaStream_t);
 
+// X[b] = C[b] + d I and XH[b] = X[b]^H, rounded to FP32 (a product and its conjugate transpose,
+// the latter the right operand of a later product on the tensor-core kernel, which multiplies by
+// the conjugate transpose of the rows it is given); 32 x 32 tiles, the transposed tile through
+// shared memory
+__global__ void k_take_both(int N, const c128* __restrict__ C, long long s, float d, c64* __restrict__ X,
+                            c64* __restrict__ XH) {
+  __shared__ c128 tt[32][33];
+  const c128* Cb = C + blockIdx.z * s;
+  c64* xb = X + blockIdx.z * s;
+  c64* hb = XH + blockIdx.z * s;
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int row = j0 + r, col = i0 + threadIdx.x;
+    if (row < N && col < N) tt[r][threadIdx.x] = Cb[(long long)row * N + col];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    if (i < N && j < N) {
+      const float dd = (i == j) ? d : 0.0f;
+      const c128 a = Cb[(long long)i * N + j];
+      const c128 t = tt[threadIdx.x][r];   // C[j][i]
+      xb[(long long)i * N + j] = c64{(float)a.re + dd, (float)a.im};
+      hb[(long long)i * N + j] = c64{(float)t.re + dd, -(float)t.im};
+    }
+  }
+}
+void launch_take_both(int N, const c128* C, long long s, int batch, float d, c64* X, c64* XH, cudaStream_t st) {
+  dim3 grid((N + 31) / 32, (N + 31) / 32, batch);
+  ++::gw::g_launch_count, k_take_both<<<grid, dim3(32, 8), 0, st>>>(N, C, s, d, X, XH);
+}
+
 __global__ void k_convert(int n, const c128* in, c64* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     out[i] = c64{(float)in[i].re, (float)in[i].im};
@@ -508,23 +540,31 @@ void launch_convert_back(int n, const c64* in, c128* out, cudaStream_t st) {
   ++::gw::g_launch_count, k_convert_back<<<std::min((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, in, out);
 }
 
-// Dominant eigenpair by power iteration with a Rayleigh quotient (one block, FP64).
-__global__ void k_power_iter(int N, const c128* __restrict__ A, c128* __restrict__ x, double* lam, int iters) {
+// Dominant eigenpair by power iteration with a Rayleigh quotient (one block, FP64). Each warp
+// takes whole rows of A (coalesced along the row), the iterate stays in shared memory.
+__global__ void __launch_bounds__(1024) k_power_iter(int N, const c128* __restrict__ A, c128* __restrict__ x,
+                                                     double* lam, int iters) {
   extern __shared__ c128 v[];   // [2N]
   __shared__ double red[32];
   c128* y = v + N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
   for (int i = threadIdx.x; i < N; i += blockDim.x) v[i] = c128{1.0 + 0.001 * (i % 7), 0.0};
   __syncthreads();
   double rq = 0;
   for (int it = 0; it < iters; ++it) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    for (int i = warp; i < N; i += nwarp) {
+      const c128* a = A + (long long)i * N;
       double sr = 0, si = 0;
-      for (int j = 0; j < N; ++j) {
-        c128 a = A[(long long)i * N + j], b = v[j];
-        sr += a.re * b.re - a.im * b.im;
-        si += a.re * b.im + a.im * b.re;
+      for (int j = lane; j < N; j += 32) {
+        const c128 aa = a[j], b = v[j];
+        sr = fma(aa.re, b.re, fma(-aa.im, b.im, sr));
+        si = fma(aa.re, b.im, fma(aa.im, b.re, si));
       }
-      y[i] = c128{sr, si};
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      if (lane == 0) y[i] = c128{sr, si};
     }
     __syncthreads();
     double p = 0, d = 0;
@@ -558,7 +598,7 @@ __global__ void k_power_iter(int N, const c128* __restrict__ A, c128* __restrict
 void launch_power_iter(int N, const c128* A, c128* x, double* lam, int iters, cudaStream_t st) {
   const int smem = 2 * N * (int)sizeof(c128);   // above 48 KB from N = 1536 on: opt in
   if (smem > 48 * 1024) cudaFuncSetAttribute(k_power_iter, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  ++::gw::g_launch_count, k_power_iter<<<1, 512, smem, st>>>(N, A, x, lam, iters);
+  ++::gw::g_launch_count, k_power_iter<<<1, 1024, smem, st>>>(N, A, x, lam, iters);
 }
 
 __global__ void k_rank1(int N, c128* A, const c128* x, double alpha) {
