@@ -507,6 +507,8 @@ gw_status newton_schulz_tc(gw_plan_s* P, c128* Vio, int batch, int iters) {
   GW_TRY(dalloc(P, &Tm, s * nb));
   GW_TRY(dalloc(P, &Th, s * nb));
   GW_TRY(dalloc(P, &C, s * nb));
+  unsigned* d_dev;
+  GW_TRY(dalloc(P, &d_dev, 1));
   ++::gw::g_launch_count, k_frob_scale<<<batch, 256, 0, P->st>>>(N, Vio, s, d_c);
   for (int b0 = 0; b0 < batch; b0 += nb) {
     const int n = std::min(nb, batch - b0);
@@ -520,8 +522,23 @@ gw_status newton_schulz_tc(gw_plan_s* P, c128* Vio, int batch, int iters) {
       // T = 1.5 I - 0.5 Z Y;  Y <- Y T;  Z <- T Z
       GW_TRY(herm_gemm(P, Z, true, nullptr, Yh, true, -0.5, C, n));
       launch_take_both(N, C, s, n, 1.5f, Tm, Th, P->st);
+      // converged chunk: once max |T - I| < 1e-4 the step below leaves it ~1e-8 from I (the
+      // iteration converges quadratically), below the FP32 rounding of the products
+      bool last = false;
+      if (it >= 6 && it % 2 == 0) {
+        unsigned hdev = 0;
+        if (cudaMemsetAsync(d_dev, 0, sizeof(unsigned), P->st) != cudaSuccess) return fail(GW_ERR_CUDA, "newton_schulz");
+        launch_dev_identity(N, Tm, s * n, d_dev, P->st);
+        if (cudaMemcpyAsync(&hdev, d_dev, sizeof(unsigned), cudaMemcpyDeviceToHost, P->st) != cudaSuccess ||
+            cudaStreamSynchronize(P->st) != cudaSuccess)
+          return fail(GW_ERR_CUDA, "newton_schulz: convergence check failed");
+        float dev;
+        std::memcpy(&dev, &hdev, sizeof(float));
+        last = dev < 1e-4f;
+      }
       GW_TRY(herm_gemm(P, Y, true, nullptr, Th, true, 1.0, C, n));
       launch_take_both(N, C, s, n, 0.0f, Y, Yh, P->st);
+      if (last) break;
       GW_TRY(herm_gemm(P, Tm, true, nullptr, Zh, true, 1.0, C, n));
       launch_take_both(N, C, s, n, 0.0f, Z, Zh, P->st);
     }
@@ -530,7 +547,7 @@ gw_status newton_schulz_tc(gw_plan_s* P, c128* Vio, int batch, int iters) {
   GW_TRY(check_launch(P, "newton_schulz"));
   cudaError_t e = cudaStreamSynchronize(P->st);
   if (e != cudaSuccess) return fail(GW_ERR_CUDA, std::string("newton_schulz: ") + cudaGetErrorString(e));
-  for (int i = 0; i < 8; ++i) dfree_last(P);
+  for (int i = 0; i < 9; ++i) dfree_last(P);
   return GW_OK;
 }
 

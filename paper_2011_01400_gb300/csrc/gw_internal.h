@@ -105,6 +105,7 @@ void launch_chol_inv_minus_I(int N, c128* A, int batch, long long stride, c128* 
                              cudaStream_t st);
 template <typename T> void launch_axpby_identity(int N, cplx<T>* A, long long s, int batch, T diag, cudaStream_t st);
 void launch_take_both(int N, const c128* C, long long s, int batch, float d, c64* X, c64* XH, cudaStream_t st);
+void launch_dev_identity(int N, const c64* T, long long total, unsigned* dev, cudaStream_t st);
 void launch_convert(int n, const c128* in, c64* out, cudaStream_t st);
 void launch_convert_back(int n, const c64* in, c128* out, cudaStream_t st);
 // dominant eigenpair of a Hermitian matrix by power iteration (FP64)

@@ -62,7 +62,7 @@ constexpr int TILE = 128 * ROWB;         // 16 KB: one piece of A ([A1; A2]) or 
 constexpr int SLOT = BMU * ROWB;         // 8 KB: raw ring slot, 64 rows x 32 floats (16 complex pairs)
 constexpr int WBYTES = 16 * 4;           // the weights of a slot's 16 pair rows (one weight row)
 constexpr int NTHREADS = 736;           // 23 warps (roles below)
-constexpr uint32_t D1_COL = 0, D2_COL = 256, DBUF = 128;
+constexpr uint32_t DBUF = 128;           // TMEM columns of one accumulator buffer
 constexpr int LSH = 11;                  // F16: the low piece is scaled by 2^11
 constexpr int TP_F16 = 1, TP_TF32 = 1;   // weight rows per work item (measured: 2 is slower)
 
@@ -84,18 +84,21 @@ template <int KIND, int TP> struct Kd {
   static constexpr int NT = BNU / TP;                       // nu columns per weight row
   static constexpr int BST = NP * NT * ROWB;                // one B stage (NT rows per piece)
   static constexpr int AST = TP * NP * TILE;                // one A buffer (TP weighted operands)
-  static constexpr int SB = (KIND == K_BF16) ? 2 : 4;       // B stages
-  static constexpr int SA = 2;                              // A buffers
+  // Stage s of the pipeline owns B buffer s, A buffer s and D1 accumulator s (DEPTH of each): one
+  // commit per stage tells the B producer, the transform and the epilogue that the stage's MMAs
+  // are done. D2 (per segment) takes the rest of TMEM.
+  static constexpr int DEPTH = (KIND == K_BF16) ? 2 : 3;
+  static constexpr int SB = DEPTH, SA = DEPTH, NB1 = DEPTH;  // B stages, A buffers, D1 buffers
+  static constexpr int NB2 = 4 - DEPTH;                      // D2 buffers (TMEM: 4 x 128 columns)
+  static constexpr uint32_t D1_COL = 0, D2_COL = NB1 * DBUF;
   static constexpr int RING = (KIND == K_BF16) ? 2 : 4;     // raw ring slots
   static constexpr int A_OFF = SB * BST;
   static constexpr int RING_OFF = A_OFF + SA * AST;
   static constexpr int WB_OFF = RING_OFF + RING * SLOT;
   static constexpr int BAR_OFF = WB_OFF + RING * TP * WBYTES;
-  static constexpr int SMEM = BAR_OFF + 256 + 1024;
+  static constexpr int BARS = 8 * (4 * DEPTH + 2 * NB2 + 1 + 2 * RING) + 16;   // + TMEM address
+  static constexpr int SMEM = BAR_OFF + BARS + 1024;
 };
-static_assert(Kd<K_F16, 1>::SMEM <= 232448 && Kd<K_F16, 2>::SMEM <= 232448, "shared memory budget");
-static_assert(Kd<K_BF16, 1>::SMEM <= 232448, "shared memory budget");
-static_assert(Kd<K_TF32, 1>::SMEM <= 232448 && Kd<K_TF32, 2>::SMEM <= 232448, "shared memory budget");
 
 struct Tile {
   int m0, mhi;     // mu rows [m0, m0 + 64) loaded; rows [m0, mhi) owned by this tile
@@ -118,6 +121,8 @@ struct Chi0Params {
   double* out;          // [T][N][N] complex as (re, im) doubles, lower triangle accumulated
   int* status;
   int lower;            // 1: lower triangle only (Hermitian result); 0: every element
+  int store;            // 1: one K chunk of one segment per output, written with plain stores (no
+                        //    zeroing, no atomics); 0: FP64 atomic accumulation
   int a_bstride;        // A rows of weight row / batch entry t start at t * a_bstride
   int b_bstride;        // B rows of t start at t * b_bstride
 };
@@ -175,41 +180,39 @@ __device__ __forceinline__ void mma_k(uint32_t d, uint64_t a, uint64_t b, uint32
 template <int KIND, int TP>
 __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Chi0Maps maps, Chi0Params p) {
   using C = Kd<KIND, TP>;
+  static_assert(C::SMEM <= 232448, "shared memory budget");
+  static_assert((C::NB1 + C::NB2) * DBUF <= 512, "TMEM budget");
   constexpr int NP = C::NP, SB = C::SB, SA = C::SA, BST = C::BST, AST = C::AST, RPS = C::RPS, RING = C::RING;
-  constexpr int NT = C::NT;
+  constexpr int NT = C::NT, NB1 = C::NB1, NB2 = C::NB2, DEPTH = C::DEPTH;
+  constexpr uint32_t D1_COL = C::D1_COL, D2_COL = C::D2_COL;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = smem + C::RING_OFF;
   float* wbuf = reinterpret_cast<float*>(smem + C::WB_OFF);   // [RING][TP][16]
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
-  uint64_t* full_b = bars;                        // [SB] B stage landed
-  uint64_t* empty_b = bars + SB;                  // [SB] B stage consumed by the MMAs
-  uint64_t* full_a = bars + 2 * SB;               // [SA] A buffer written by the transform
-  uint64_t* empty_a = bars + 2 * SB + SA;         // [SA] A buffer consumed by the MMAs
-  uint64_t* t1full = bars + 2 * SB + 2 * SA;      // [2] D1 of a stage ready
-  uint64_t* t1empty = t1full + 2;                 // [2] D1 drained
-  uint64_t* t2full = t1full + 4;                  // [2] D2 of a segment ready
-  uint64_t* t2empty = t1full + 6;                 // [2] D2 drained
-  uint64_t* done = t1full + 8;
-  uint64_t* rfull = t1full + 9;                   // [RING]
-  uint64_t* rempty = t1full + 9 + RING;           // [RING]
-  uint32_t* tmem_base_p = reinterpret_cast<uint32_t*>(t1full + 9 + 2 * RING);
+  uint64_t* full_b = bars;                        // [DEPTH] B stage landed
+  uint64_t* full_a = bars + DEPTH;                // [DEPTH] A buffer written by the transform
+  uint64_t* sdone = bars + 2 * DEPTH;             // [DEPTH] the stage's MMAs done: B and A buffers
+                                                  // free, D1 of the stage ready
+  uint64_t* t1empty = bars + 3 * DEPTH;           // [DEPTH] D1 drained
+  uint64_t* t2full = bars + 4 * DEPTH;            // [NB2] D2 of a segment ready
+  uint64_t* t2empty = t2full + NB2;               // [NB2] D2 drained
+  uint64_t* done = t2full + 2 * NB2;
+  uint64_t* rfull = done + 1;                     // [RING]
+  uint64_t* rempty = rfull + RING;                // [RING]
+  uint32_t* tmem_base_p = reinterpret_cast<uint32_t*>(rempty + RING);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int it0 = p.cta_off[blockIdx.x], it1 = p.cta_off[blockIdx.x + 1];
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < SB; ++s) {
+    for (int s = 0; s < DEPTH; ++s) {
       mbar_init(&full_b[s], 1);
-      mbar_init(&empty_b[s], 1);
-    }
-    for (int s = 0; s < SA; ++s) {
       mbar_init(&full_a[s], 4);                 // one elected arrival per transform warp
-      mbar_init(&empty_a[s], 1);
+      mbar_init(&sdone[s], 1);
+      mbar_init(&t1empty[s], 16);               // one per epilogue warp
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&t1full[b], 1);
-      mbar_init(&t1empty[b], 16);               // one per epilogue warp
+    for (int b = 0; b < NB2; ++b) {
       mbar_init(&t2full[b], 1);
       mbar_init(&t2empty[b], 16);
     }
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
         decode<TP>(p, p.items[it], tl, t, s0, s1);
         for (int i = s0; i < s1; ++i, ++gs) {
           const int s = gs % SB;
-          if (!mbar_wait(&empty_b[s], ((gs / SB) & 1) ^ 1, p.status)) { ok = false; break; }
+          if (!mbar_wait(&sdone[s], ((gs / SB) & 1) ^ 1, p.status)) { ok = false; break; }
           uint8_t* st = smem + s * BST;
           mbar_arrive_expect_tx(&full_b[s], BST);
           const int x = i * (ROWB / C::ESZ);
@@ -278,7 +281,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t fmt = (KIND == K_TF32) ? 2u : (KIND == K_BF16 ? 1u : 0u);
-      uint32_t gs = 0, gseg = 0;
+      const uint32_t sbase = smem_u32(smem);
+      // ring positions, their phase parities and the accumulator rounds, stepped per stage (no
+      // divisions in the issue loop)
+      int sb = 0, b2 = 0;                        // stage buffer (B, A and D1), D2 buffer
+      uint32_t pb = 0, r2 = 0;                   // stage-round parity, D2 rounds
       bool ok = true;
       for (int it = it0; it < it1 && ok; ++it) {
         Tile tl;
@@ -287,36 +294,34 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
         const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(tl.ncols >> 3) << 17) |
                                ((uint32_t)(128 >> 4) << 24);
         const int nt_valid = min(TP, p.T - t);   // weight rows of the group that exist
-        for (int i = s0; i < s1; ++i, ++gs) {
-          const int sb = gs % SB, sa = gs % SA;
-          const int b = gs & 1, b2 = gseg & 1;
-          const bool seg_first = ((i - s0) % F) == 0;
-          const bool seg_end = ((i - s0) % F) == F - 1 || i == s1 - 1;
-          if (gs >= 2 && !mbar_wait(&t1empty[b], ((gs >> 1) - 1) & 1, p.status)) { ok = false; break; }
-          if (seg_first && gseg >= 2 && !mbar_wait(&t2empty[b2], ((gseg >> 1) - 1) & 1, p.status)) {
-            ok = false;
-            break;
-          }
-          if (!mbar_wait(&full_b[sb], (gs / SB) & 1, p.status)) { ok = false; break; }
-          if (!mbar_wait(&full_a[sa], (gs / SA) & 1, p.status)) { ok = false; break; }
+        int spos = 0;                            // stage within the promotion segment
+        for (int i = s0; i < s1; ++i) {
+          const bool seg_first = spos == 0;
+          const bool seg_end = spos == F - 1 || i == s1 - 1;
+          // D1 buffer sb drained one round ago (the first round finds it free)
+          if (!mbar_wait(&t1empty[sb], pb ^ 1u, p.status)) { ok = false; break; }
+          if (seg_first && r2 > 0 && !mbar_wait(&t2empty[b2], (r2 - 1) & 1, p.status)) { ok = false; break; }
+          if (!mbar_wait(&full_b[sb], pb, p.status)) { ok = false; break; }
+          if (!mbar_wait(&full_a[sb], pb, p.status)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t bbase = smem_u32(smem + sb * BST);
+          // K-major SWIZZLE_128B descriptors; a 32-byte K step adds 2 to the address field
+          const uint64_t dB0 = sdesc(sbase + sb * BST), dB1 = sdesc(sbase + sb * BST + NT * ROWB);
 #pragma unroll
           for (int u = 0; u < TP; ++u) {
             if (u >= nt_valid) break;
-            const uint32_t abase = smem_u32(smem + C::A_OFF + sa * AST + u * NP * TILE);
-            const uint32_t d1 = tmem + D1_COL + b * DBUF + u * NT;
+            const uint32_t abase = sbase + C::A_OFF + sb * AST + u * NP * TILE;
+            const uint64_t dA0 = sdesc(abase), dA1 = sdesc(abase + TILE);
+            const uint32_t d1 = tmem + D1_COL + sb * DBUF + u * NT;
             const uint32_t d2 = tmem + D2_COL + b2 * DBUF + u * NT;
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t ko = kk * 32;
+              const uint64_t ko = (uint64_t)(2 * kk);
               const uint32_t acc2 = (seg_first && kk == 0) ? 0u : 1u;
-              const uint64_t A0 = sdesc(abase + ko), B0 = sdesc(bbase + ko);
-              const uint64_t A1 = sdesc(abase + TILE + ko), B1 = sdesc(bbase + NT * ROWB + ko);
+              const uint64_t A0 = dA0 + ko, B0 = dB0 + ko, A1 = dA1 + ko, B1 = dB1 + ko;
               mma_k<KIND>(d2, A0, B1, idesc, acc2);
               mma_k<KIND>(d2, A1, B0, idesc, 1u);
               if constexpr (NP == 3) {
-                const uint64_t A2 = sdesc(abase + 2 * TILE + ko), B2 = sdesc(bbase + 2 * NT * ROWB + ko);
+                const uint64_t A2 = sdesc(abase + 2 * TILE) + ko, B2 = sdesc(sbase + sb * BST + 2 * NT * ROWB) + ko;
                 mma_k<KIND>(d2, A0, B2, idesc, 1u);
                 mma_k<KIND>(d2, A2, B0, idesc, 1u);
                 mma_k<KIND>(d2, A1, B1, idesc, 1u);
@@ -324,13 +329,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
               mma_k<KIND>(d1, A0, B0, idesc, kk == 0 ? 0u : 1u);
             }
           }
-          mma_commit(&empty_b[sb]);
-          mma_commit(&empty_a[sa]);
-          mma_commit(&t1full[b]);
+          mma_commit(&sdone[sb]);
           if (seg_end) {
             mma_commit(&t2full[b2]);
-            ++gseg;
+            if (++b2 == NB2) { b2 = 0; ++r2; }
           }
+          if (++sb == DEPTH) { sb = 0; pb ^= 1u; }
+          spos = seg_end ? 0 : spos + 1;
         }
       }
       mma_commit(done);
@@ -350,7 +355,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
       for (int i = s0; i < s1; ++i, ++gs, gr += RPS) {
         const int s = gs % SA;
         // warp-uniform waits: the arrivals below are elected per warp
-        if (!__all_sync(0xffffffffu, mbar_wait(&empty_a[s], ((gs / SA) & 1) ^ 1, p.status))) { ok = false; break; }
+        if (!__all_sync(0xffffffffu, mbar_wait(&sdone[s], ((gs / SA) & 1) ^ 1, p.status))) { ok = false; break; }
         uint8_t* at = smem + C::A_OFF + s * AST;
         const uint32_t g = gr + (RPS == 2 ? h : 0);
         const int slot = g % RING;
@@ -488,7 +493,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
     const int lrow = quad * 32 + lane;         // TMEM lane: Re (< 64) or Im (>= 64) of mu row lrow & 63
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     const float f2 = (KIND == K_F16) ? 1.0f / (float)(1 << LSH) : 1.0f;
-    uint32_t gs = 0, gseg = 0;
+    int b = 0, b2 = 0;
+    uint32_t r1 = 0, r2 = 0;                   // stage / D2 rounds (phase parities)
     bool ok = true;
     float acc[32];
 #pragma unroll
@@ -501,9 +507,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
       const int mu = tl.m0 + (lrow & 63);
       const int part = lrow >> 6;
       const double es = p.escale[min(t + u, p.T - 1)];
-      for (int i = s0; i < s1; ++i, ++gs) {
-        const int b = gs & 1;
-        ok = __all_sync(0xffffffffu, mbar_wait(&t1full[b], (gs >> 1) & 1, p.status));
+      int spos = 0;
+      for (int i = s0; i < s1; ++i) {
+        const bool seg_end = spos == F - 1 || i == s1 - 1;
+        spos = seg_end ? 0 : spos + 1;
+        ok = __all_sync(0xffffffffu, mbar_wait(&sdone[b], r1 & 1, p.status));
         if (!ok) break;
         tc_fence_after();
         // all 64 columns: the ones beyond the tile hold stale values that are never flushed
@@ -511,24 +519,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) k_chi0(const __grid_constant__ Ch
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&t1empty[b]);
-        if (((i - s0) % F) == F - 1 || i == s1 - 1) {
-          const int b2 = gseg & 1;
-          ok = __all_sync(0xffffffffu, mbar_wait(&t2full[b2], (gseg >> 1) & 1, p.status));
+        if (++b == NB1) { b = 0; ++r1; }
+        if (seg_end) {
+          ok = __all_sync(0xffffffffu, mbar_wait(&t2full[b2], r2 & 1, p.status));
           if (!ok) break;
           tc_fence_after();
           drain(tmem + lane_off + D2_COL + b2 * DBUF + 32 * cg, f2, acc);
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(&t2empty[b2]);
-          ++gseg;
+          if (++b2 == NB2) { b2 = 0; ++r2; }
           if (mu >= tl.m0 && mu < tl.mhi) {
             const int c0 = tl.n0 + cw;
             double* o = p.out + 2 * (((long long)(t + u) * p.N + mu) * p.N + c0) + part;
             // columns nu = c0 + j of the tile below N (and, for the lower triangle, <= mu)
             const int jmax = min(ncol, (p.lower ? mu + 1 : p.N) - c0);
+            if (p.store) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (j < jmax) atomicAdd(o + 2 * j, es * (double)acc[j]);
+              for (int j = 0; j < 32; ++j)
+                if (j < jmax) o[2 * j] = es * (double)acc[j];
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (j < jmax) atomicAdd(o + 2 * j, es * (double)acc[j]);
+            }
           }
 #pragma unroll
           for (int j = 0; j < 32; ++j) acc[j] = 0.f;
@@ -694,8 +708,9 @@ std::vector<Tile> make_tiles(int N, bool lower, int nt) {
 }
 
 // relative cost of one stage of a tile for nvalid weight rows: the MMAs scale with the columns
-// computed, the operand loads do not
-double tile_cost(const Tile& t, int nvalid) { return std::max((double)(t.ncols * nvalid), 48.0); }
+// computed; the stage's fixed part (waits, transform, drain, commits) does not (measured: about
+// 1.5x the MMA time of a full 128-column stage)
+double tile_cost(const Tile& t, int nvalid) { return 192.0 + (double)(t.ncols * nvalid); }
 
 }  // namespace
 
@@ -920,10 +935,6 @@ gw_status herm_gemm_run(const HermGemmArgs& a, Chi0Plan** plan, cudaStream_t st,
     ++g_launch_count, k_h_pieces_tf32<float><<<grid, 256, 0, st>>>(hrows, N, Kpad, a.H32, a.bpl[0], a.bpl[1]);
   ++g_launch_count, k_fill_d<<<1, 256, 0, st>>>(a.escale, nb, a.alpha);
   ++g_launch_count, k_fill_f<<<(Kpad + 255) / 256, 256, 0, st>>>(a.ones, Kpad, 1.0f);
-  if (cudaMemsetAsync(a.C, 0, sizeof(c128) * (size_t)nb * N * N, st) != cudaSuccess) {
-    err = "herm_gemm: memset failed";
-    return GW_ERR_CUDA;
-  }
   const int RS = Kd<K_TF32, 1>::RS;
   const int nst = Kpad / RS;
   Chi0Lists* L = nullptr;
@@ -951,6 +962,11 @@ gw_status herm_gemm_run(const HermGemmArgs& a, Chi0Plan** plan, cudaStream_t st,
   prm.out = reinterpret_cast<double*>(a.C);
   prm.status = a.status;
   prm.lower = 0;
+  prm.store = 1;   // one K chunk (nchunk = 1) and one segment per item: every element written once
+  if (L->nchunk != 1) {
+    err = "herm_gemm: the product needs one K chunk per output tile";
+    return GW_ERR_STATE;
+  }
   prm.a_bstride = a.a_batch ? N : 0;
   prm.b_bstride = a.h_batch ? N : 0;
   return launch_chi0<K_TF32, 1>(maps, prm, L->grid, st, err);

@@ -520,6 +520,24 @@ __global__ void k_take_both(int N, const c128* __restrict__ C, long long s, floa
     }
   }
 }
+// dev = max over the batch of max(|Re T_ij - delta_ij|, |Im T_ij|) (as the bits of a non-negative
+// float; *dev must hold 0 on entry)
+__global__ void k_dev_identity(int N, const c64* __restrict__ T, long long total, unsigned* __restrict__ dev) {
+  float m = 0.f;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % ((long long)N * N);
+    const int i = (int)(r / N), j = (int)(r % N);
+    const c64 v = T[e];
+    m = fmaxf(m, fmaxf(fabsf(v.re - (i == j ? 1.0f : 0.0f)), fabsf(v.im)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(dev, __float_as_uint(m));
+}
+void launch_dev_identity(int N, const c64* T, long long total, unsigned* dev, cudaStream_t st) {
+  ++::gw::g_launch_count, k_dev_identity<<<(int)std::min<long long>((total + 255) / 256, 152LL * 8), 256, 0, st>>>(
+      N, T, total, dev);
+}
+
 void launch_take_both(int N, const c128* C, long long s, int batch, float d, c64* X, c64* XH, cudaStream_t st) {
   dim3 grid((N + 31) / 32, (N + 31) / 32, batch);
   ++::gw::g_launch_count, k_take_both<<<grid, dim3(32, 8), 0, st>>>(N, C, s, d, X, XH);
