@@ -28,7 +28,7 @@
  *   - No call uses more than the one current CUDA device.
  *   - Environment (read at gw_plan_create, split precision only):
  *     GW_CHI0_SEG_ROWS      pair rows per FP64 promotion segment of the tensor-core
- *                           chi0 (default 2048; at least 32);
+ *                           chi0 (default 8192; at least 32);
  *     GW_CHI0_COMPRESS_TOL  per-frequency residual bound of the chi0 weight-matrix
  *                           compression (default 3e-8; 0 keeps all frequencies).
  *   - Environment (read at gw_plan_create, all precisions):
