@@ -27,10 +27,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "G0W0 Σc time-to-solution & χ0 TFLOP/s: split-prec vs FP64 on 1 GB300 @ ≤1 meV"
 # DRAM bytes of one chi0 contraction launch (dram__bytes_read.sum, dram__bytes_write.sum), from an
-# ncu capture of the cfg1 shape on a 4x4x4 k mesh (q = 1, 3xBF16; the k_tc capture under profiles/).
-# The reads stream the operand planes of every k and grow with the k count; the writes are the
-# compressed output rows, independent of it.
-CHI0_DRAM_CAPTURE = dict(prec="3xbf16", n_k=64, n_aux=400, read=436.279552e6, write=25.975808e6)
+# ncu capture of k_chi0 (3xFP16) on the cfg1 shape with a 4x4x4 k mesh (the third chi0 launch of a
+# pass; its summary is kept with the other profiles). The reads stream the operand planes of every
+# k and grow with the k count; the writes are the FP64 output rows, independent of it.
+CHI0_DRAM_CAPTURE = dict(prec="3xfp16", n_k=64, n_aux=400, read=271.424512e6, write=39.426304e6)
 WORKLOADS = {
     "cfg0": "tiny synthetic insulator: 2x2x2 k, 2 atoms, 32 NAO, 32 bands (4 occ), 96 ABF, 16 imaginary frequencies",
     "cfg1": "Si-like 2-atom fcc cell: 6x6x6 k (216 k, 216 q), 78 NAO, 78 bands (4 occ), 400 ABF, 32 imaginary "
@@ -695,7 +695,7 @@ def run_device(args, system, world, rank):
                         "direction of q -> 0 (128-point sphere rule)"}[s.head_wings],
                     q_chi0_computed=f"{q_computed(s)} of {s.n_k} (W^c(-q) = conj(W^c(q)) for the pairs)"
                     if getattr(s, "trs", False) else f"{s.n_k} of {s.n_k}",
-                    l2="inputs larger than L2 (chi0 operand planes 0.8 GB per q)"),
+                    l2="inputs larger than L2 (chi0 operand planes 0.4-0.6 GB per q, by split)"),
         chi0_tflops=achieved,
         step_useful_tflops=fl["total"] / (ms * 1e-3) / 1e12,
         roofline=dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,

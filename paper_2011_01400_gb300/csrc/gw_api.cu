@@ -1175,7 +1175,8 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
       GW_CUDA(cudaEventRecord(e0, st));
       launch_chi0_simt<double>(N, K, M, P->ldm, nullptr, P->d_delta, P->d_freq, nw, scale, chi0, st);
       GW_CUDA(cudaEventRecord(e1, st));
-      if (hw)
+      // one direction (head_wings = 1) or the three Cartesian components for the average
+      if (hw && !hw_avg)
         launch_head_wings<double>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw, hw_pref, P->d_head, P->d_h,
                                   st);
       if (hw_avg) {
@@ -1238,9 +1239,10 @@ gw_status chi0_core(gw_plan_s* P, int q, c128* chi0) {
                                  P->nocc, na, 0, nb, M, 1, P->ldm, st, v);
             }))
           return fail(GW_ERR_CUDA, "M kernel autotuner: CUDA error");
-        launch_head_wings<float>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw, hw_pref, P->d_head, P->d_h,
-                                 st);
-        if (hw_avg) {
+        if (!hw_avg)
+          launch_head_wings<float>(N, K, M, P->ldm, P->d_delta, P->d_pq, P->d_freq, nw, hw_pref, P->d_head, P->d_h,
+                                   st);
+        else {
           pairs3(kk0, nkk);
           launch_head_wings3<float>(N, K, M, P->ldm, P->d_delta, P->d_pq3, P->ldm, P->d_freq, nw, hw_pref, P->d_A6,
                                     P->d_h3, st);

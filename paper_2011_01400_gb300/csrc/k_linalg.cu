@@ -569,6 +569,7 @@ __global__ void __launch_bounds__(1024) k_power_iter(int N, const c128* __restri
   for (int i = threadIdx.x; i < N; i += blockDim.x) v[i] = c128{1.0 + 0.001 * (i % 7), 0.0};
   __syncthreads();
   double rq = 0;
+  int extra = 10;
   for (int it = 0; it < iters; ++it) {
     for (int i = warp; i < N; i += nwarp) {
       const c128* a = A + (long long)i * N;
@@ -593,8 +594,19 @@ __global__ void __launch_bounds__(1024) k_power_iter(int N, const c128* __restri
     double nrm2 = block_sum(p, red);
     rq = block_sum(d, red);
     double inv = 1.0 / sqrt(nrm2);
-    for (int i = threadIdx.x; i < N; i += blockDim.x) v[i] = c128{y[i].re * inv, y[i].im * inv};
-    __syncthreads();
+    double dv = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const c128 nv = c128{y[i].re * inv, y[i].im * inv};
+      dv += (nv.re - v[i].re) * (nv.re - v[i].re) + (nv.im - v[i].im) * (nv.im - v[i].im);
+      v[i] = nv;
+    }
+    // converged: the step has shrunk geometrically below 1e-12; ten more steps (the dominant
+    // eigenvalue is positive, so the iterate does not flip) take it to the rounding level
+    const double step = sqrt(block_sum(dv, red));
+    if (step < 1e-12) {
+      if (extra == 0) break;
+      --extra;
+    }
   }
   // fix the phase: largest-magnitude component real positive
   if (threadIdx.x == 0) {

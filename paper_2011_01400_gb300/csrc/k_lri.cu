@@ -484,7 +484,9 @@ bool launch_mgen_sig(const LriGeom& g, const c64* T1, const c128* evec, int q, i
   int tiles = 0;
   for (int A = 0; A < g.n_atoms; ++A) tiles += (g.atom_nx[A] + SIG_G - 1) / SIG_G;
   dim3 grid(nkk, tiles);
-  ++::gw::g_launch_count, k_mgen_sig<<<grid, 128, 0, st>>>(g, T1, evec, q, kk0, a0, na, nb, out, s_r, s_mu);
+  // one thread per band b (whole warps, at most 128)
+  const int nt = std::min(128, (nb + 31) / 32 * 32);
+  ++::gw::g_launch_count, k_mgen_sig<<<grid, nt, 0, st>>>(g, T1, evec, q, kk0, a0, na, nb, out, s_r, s_mu);
   return true;
 }
 
@@ -494,9 +496,9 @@ bool launch_mgen_sig(const LriGeom& g, const c64* T1, const c128* evec, int q, i
 // written as the fp32 plane raw[mu][kofs + 2 r + {0, 1}], r = (kk * na + a) * nb + b, with the
 // largest |re|, |im| into absmax. Each thread owns one a and SIG_G ABFs: the slabs
 // T1^mu(k + q)[j][a] and c(k + q)[i][a] are read once along a; T1^mu(k)[i][b] and c(k)[j][b] sit
-// in shared memory.
-constexpr int CHI_NB = 8;
-
+// in shared memory. CHI_NB (4 or 8) bounds the occupied bands of one launch; the FMA work and the
+// accumulator registers scale with it.
+template <int CHI_NB>
 __global__ void __launch_bounds__(128) k_mgen_chi(const __grid_constant__ LriGeom g, const c64* __restrict__ T1,
                                                   const c128* __restrict__ evec, int q, int kk0, int a0, int na,
                                                   int b0, int nb, float* __restrict__ raw, long long ldk,
@@ -583,7 +585,7 @@ __global__ void __launch_bounds__(128) k_mgen_chi(const __grid_constant__ LriGeo
     }
   }
   if (absmax) {
-    // every thread gets here (128 threads); non-negative floats order like their bit patterns
+    // every thread gets here (whole warps); non-negative floats order like their bit patterns
     const unsigned mm = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
     if ((threadIdx.x & 31) == 0) atomicMax(absmax, mm);
   }
@@ -591,13 +593,18 @@ __global__ void __launch_bounds__(128) k_mgen_chi(const __grid_constant__ LriGeo
 
 bool launch_mgen_chi(const LriGeom& g, const c64* T1, const c128* evec, int q, int kk0, int nkk, int a0, int na,
                      int b0, int nb, float* raw, long long ldk, long long kofs, unsigned* absmax, cudaStream_t st) {
-  if (nb > CHI_NB) return false;
+  if (nb > 8) return false;
   for (int A = 0; A < g.n_atoms; ++A)
     if (g.atom_nb[A] > 48) return false;
   int tiles = 0;
   for (int A = 0; A < g.n_atoms; ++A) tiles += (g.atom_nx[A] + SIG_G - 1) / SIG_G;
   dim3 grid(nkk, tiles);
-  ++::gw::g_launch_count, k_mgen_chi<<<grid, 128, 0, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, raw, ldk, kofs, absmax);
+  // one thread per unoccupied band (whole warps, at most 128)
+  const int nt = std::min(128, (na + 31) / 32 * 32);
+  if (nb <= 4)
+    ++::gw::g_launch_count, k_mgen_chi<4><<<grid, nt, 0, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, raw, ldk, kofs, absmax);
+  else
+    ++::gw::g_launch_count, k_mgen_chi<8><<<grid, nt, 0, st>>>(g, T1, evec, q, kk0, a0, na, b0, nb, raw, ldk, kofs, absmax);
   return true;
 }
 
