@@ -755,9 +755,12 @@ def run_device(args, system, world, rank):
         chol_flops = 4.0 * s.n_aux ** 3 * s.n_freq * nq
         line["fp64_peak"] = dict(dgemm_tflops=peak64, method="cuBLAS DGEMM via torch.matmul, 4096^3, best of 5, "
                                                            "CUDA events", cholesky_flops_per_step=chol_flops)
-    if args.surrogate:
+    # the learned surrogate and the batch of uneven systems: part of the default N = 1 line
+    if args.surrogate or (world == 1 and not args.no_extras):
         line["surrogate"] = surrogate_bench(args, gw, torch)
-    if args.batch:
+    if args.batch or (world == 1 and not args.no_extras):
+        if not args.batch:
+            args.batch = 64
         line["batch"] = batch_bench(args, gw, torch)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(s)
@@ -780,19 +783,21 @@ def main():
                     help="q -> 0: 2 = head and wings averaged over the direction of q (default), 1 = along x, "
                          "0 = regular formula")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the other split precisions and the FP64 pass on the 3x3x3 mesh")
+                    help="skip the other split precisions, the FP64 pass on the 3x3x3 mesh, the surrogate "
+                         "and the batch (the last two can be asked for again with --surrogate / --batch)")
     ap.add_argument("--qloop", default="g0w0", choices=["g0w0", "perq"],
                     help="q loop in one gw_g0w0 call (default) or as per-q gw_chi0/gw_screen/gw_sigma calls")
     ap.add_argument("--nk", default=None, help="override the k mesh, e.g. 4,4,4 (profiling captures)")
     ap.add_argument("--surrogate", action="store_true",
-                    help="also train the frequency surrogate and time it against the full 60-point grid")
+                    help="train the frequency surrogate and time it against the full 60-point grid (part of the "
+                         "default N = 1 line; this flag asks for it with --no-extras too)")
     ap.add_argument("--sur-systems", type=int, default=64, help="training systems of the surrogate")
     ap.add_argument("--sur-epochs", type=int, default=40, help="training epochs of the surrogate")
     ap.add_argument("--parallel", default="qshard", choices=["qshard", "replicas"],
                     help="N > 1: split the q mesh of one system over the ranks and sum Sigma_c (default), or "
                          "run one independent system per rank")
     ap.add_argument("--batch", type=int, default=0,
-                    help="also run a batch of this many seeded systems of uneven size (e.g. 64)")
+                    help="run a batch of this many seeded systems of uneven size (64 in the default N = 1 line)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -1297,10 +1297,7 @@ gw_status eps_core(gw_plan_s* P, int q, const c128* chi0, c128* E) {
   const c128* Vh = P->d_Vh + (long long)q * NN;
   const c128* Vin = hw ? P->d_Vb0 : Vh;     // V^1/2 entering eps~ (body only at q = 0)
   const c128 one{1, 0}, zero{0, 0}, mone{-1, 0};
-  const c64 one32{1, 0}, zero32{0, 0}, mone32{-1, 0};
   c64* A32 = reinterpret_cast<c64*>(P->d_work);
-  c64* B32 = A32 + NN * nw;
-  c64* C32 = reinterpret_cast<c64*>(P->d_tmp);
   if (P->fp64) {
     launch_zgemm<double>(N, N, N, one, chi0, N, NN, OP_N, Vin, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
     launch_zgemm<double>(N, N, N, mone, Vin, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, E, N, NN, nw, st);
@@ -1312,11 +1309,6 @@ gw_status eps_core(gw_plan_s* P, int q, const c128* chi0, c128* E) {
     GW_TRY(herm_gemm(P, Vin32, false, chi0, true, 1.0, P->d_tmp));
     launch_convert((int)(NN * nw), P->d_tmp, A32, st);
     GW_TRY(herm_gemm(P, A32, true, Vin, false, -1.0, E));
-    (void)B32;
-    (void)C32;
-    (void)one32;
-    (void)zero32;
-    (void)mone32;
   }
   launch_axpby_identity<double>(N, E, NN, nw, 1.0, st);
   if (hw && P->p.head_wings == 1) {
@@ -1357,10 +1349,7 @@ gw_status w_core(gw_plan_s* P, int q, const c128* X, c128* Wc) {
   const long long NN = (long long)N * N;
   const c128* Vh = P->d_Vh + (long long)q * NN;
   const c128 one{1, 0}, zero{0, 0};
-  const c64 one32{1, 0}, zero32{0, 0};
   c64* A32 = reinterpret_cast<c64*>(P->d_work);
-  c64* B32 = A32 + NN * nw;
-  c64* C32 = reinterpret_cast<c64*>(P->d_tmp);
   if (P->fp64) {
     launch_zgemm<double>(N, N, N, one, X, N, NN, OP_N, Vh, N, 0, OP_N, zero, P->d_tmp, N, NN, nw, st);
     launch_zgemm<double>(N, N, N, one, Vh, N, 0, OP_N, P->d_tmp, N, NN, OP_N, zero, Wc, N, NN, nw, st);
@@ -1370,10 +1359,6 @@ gw_status w_core(gw_plan_s* P, int q, const c128* X, c128* Wc) {
     GW_TRY(herm_gemm(P, Vh32, false, X, true, 1.0, P->d_tmp));
     launch_convert((int)(NN * nw), P->d_tmp, A32, st);
     GW_TRY(herm_gemm(P, A32, true, Vh, false, 1.0, Wc));
-    (void)B32;
-    (void)C32;
-    (void)one32;
-    (void)zero32;
   }
   return check_launch(P, "W^c");
 }
@@ -1597,10 +1582,6 @@ gw_status gw_g0w0(gw_plan P, int32_t sys, gw_complex* sigma_acc) {
   if (!plan_ok(P, sys, &s)) return s;
   if (P->sur.on && P->sur.model)
     return g0w0_sur(P, sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma);
-  cudaStream_t st = P->st;
-  const int N = P->N, nw = P->nw;
-  const long long NN = (long long)N * N;
-  const long long slot = NN * nw;
   GW_TRY(ensure_groups(P));
   c128* sig = sigma_acc ? reinterpret_cast<c128*>(sigma_acc) : P->d_sigma;
   std::vector<int> qs(P->NK);

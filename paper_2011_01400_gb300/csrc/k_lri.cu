@@ -393,8 +393,9 @@ void launch_mgen<float>(const LriGeom& g, const c64* T1, const c64* T2, const c1
 // The rows are HBM streams of arithmetic intensity ~4 flop/byte, so this is CUDA-core work.
 constexpr int SIG_NA = 8;   // largest Sigma window of this kernel
 constexpr int SIG_G = 4;    // ABFs per block
+constexpr int SIG_AT = 4;   // window bands per thread: the block's threads split the window in halves
 
-__global__ void __launch_bounds__(128) k_mgen_sig(const __grid_constant__ LriGeom g, const c64* __restrict__ T1,
+__global__ void __launch_bounds__(256, 3) k_mgen_sig(const __grid_constant__ LriGeom g, const c64* __restrict__ T1,
                                                   const c128* __restrict__ evec, int q, int kk0, int a0, int na,
                                                   int nb, c64* __restrict__ out, long long s_r, long long s_mu) {
   __shared__ float2 sQ[SIG_G][48][SIG_NA];   // T1^mu(k)[j][a] (n_b(A) <= 48)
@@ -437,12 +438,16 @@ __global__ void __launch_bounds__(128) k_mgen_sig(const __grid_constant__ LriGeo
   __syncthreads();
   const c64* U = T1 + g.t_off[A] + ((long long)kp * nxA + (mu0 - g.atom_x0[A])) * nbA * g.NBd;
   const long long us = (long long)nbA * g.NBd;     // between the slabs of consecutive ABFs
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    float ar[SIG_G][SIG_NA], ai[SIG_G][SIG_NA];
+  // thread = (window half, band b): each warp covers 32 consecutive b of one half
+  const int nhalf = (na + SIG_AT - 1) / SIG_AT;
+  const int nbt = blockDim.x / nhalf;
+  const int ah = threadIdx.x / nbt, ab0 = SIG_AT * ah;
+  for (int b = threadIdx.x % nbt; b < nb && ah < nhalf; b += nbt) {
+    float ar[SIG_G][SIG_AT], ai[SIG_G][SIG_AT];
 #pragma unroll
     for (int m = 0; m < SIG_G; ++m)
 #pragma unroll
-      for (int a = 0; a < SIG_NA; ++a) ar[m][a] = ai[m][a] = 0.f;
+      for (int a = 0; a < SIG_AT; ++a) ar[m][a] = ai[m][a] = 0.f;
     for (int i = 0; i < nbA; ++i) {
       const c128 cb = ck[(long long)(b0A + i) * g.NBd + b];
       const float cr = (float)cb.re, ci = (float)cb.im;
@@ -454,11 +459,11 @@ __global__ void __launch_bounds__(128) k_mgen_sig(const __grid_constant__ LriGeo
         ui[m] = u.im;
       }
 #pragma unroll
-      for (int a = 0; a < SIG_NA; ++a) {
-        const float2 d = sC[i][a];
+      for (int a = 0; a < SIG_AT; ++a) {
+        const float2 d = sC[i][ab0 + a];
 #pragma unroll
         for (int m = 0; m < SIG_G; ++m) {
-          const float2 tq = sQ[m][i][a];
+          const float2 tq = sQ[m][i][ab0 + a];
           // c_{ib}(k') conj(T1^mu_{ia}(k)) + conj(c_{ia}(k)) T1^mu_{ib}(k')
           ar[m][a] = fmaf(cr, tq.x, fmaf(ci, tq.y, fmaf(d.x, ur[m], fmaf(d.y, ui[m], ar[m][a]))));
           ai[m][a] = fmaf(ci, tq.x, fmaf(-cr, tq.y, fmaf(d.x, ui[m], fmaf(-d.y, ur[m], ai[m][a]))));
@@ -466,9 +471,9 @@ __global__ void __launch_bounds__(128) k_mgen_sig(const __grid_constant__ LriGeo
       }
     }
 #pragma unroll
-    for (int a = 0; a < SIG_NA; ++a) {
-      if (a >= na) continue;
-      const long long r = ((long long)kk * na + a) * nb + b;
+    for (int a = 0; a < SIG_AT; ++a) {
+      if (ab0 + a >= na) continue;
+      const long long r = ((long long)kk * na + ab0 + a) * nb + b;
 #pragma unroll
       for (int m = 0; m < SIG_G; ++m)
         if (m < cnt) out[r * s_r + (long long)(mu0 + m) * s_mu] = c64{ar[m][a], ai[m][a]};
@@ -484,8 +489,9 @@ bool launch_mgen_sig(const LriGeom& g, const c64* T1, const c128* evec, int q, i
   int tiles = 0;
   for (int A = 0; A < g.n_atoms; ++A) tiles += (g.atom_nx[A] + SIG_G - 1) / SIG_G;
   dim3 grid(nkk, tiles);
-  // one thread per band b (whole warps, at most 128)
-  const int nt = std::min(128, (nb + 31) / 32 * 32);
+  // one thread per (window half, band b); whole warps per half, at most 128 threads per half
+  const int nhalf = (na + SIG_AT - 1) / SIG_AT;
+  const int nt = nhalf * std::min(128, (nb + 31) / 32 * 32);
   ++::gw::g_launch_count, k_mgen_sig<<<grid, nt, 0, st>>>(g, T1, evec, q, kk0, a0, na, nb, out, s_r, s_mu);
   return true;
 }
