@@ -74,8 +74,9 @@ enum { K_F16 = 0, K_BF16 = 1, K_TF32 = 2 };
 // TP weight rows per work item share the loaded operands: the raw A rows and the B rows of a
 // stage are loaded once and feed TP weighted A operands (each its own NT = 128 / TP accumulator
 // columns), so with TP = 2 a stage of the same MMA work loads 32 KB instead of 48 KB (F16: B
-// rows 2 x 64 instead of 2 x 128, raw rows unchanged). The kernel streams its operands from L2
-// and is bound by that stream; the price is twice the transform work per loaded raw row.
+// rows 2 x 64 instead of 2 x 128, raw rows unchanged), for twice the transform work per raw row
+// and twice the MMA instructions. Measured, TP = 2 is slower: the kernel is paced by its issue
+// loop (MMA issue, waits and commit per stage), not by the operand stream.
 template <int KIND, int TP> struct Kd {
   static constexpr int NP = (KIND == K_BF16) ? 3 : 2;       // pieces per operand
   static constexpr int ESZ = (KIND == K_TF32) ? 4 : 2;      // bytes per element
