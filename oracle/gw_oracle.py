@@ -495,9 +495,15 @@ def qp(sys, sigma, omegas, mu, dxv=None):
 # ----------------------------------------------------------------------------
 
 
-def g0w0(sys, qs=None, keep=False, dxv=None):
-    """chi0 -> eps~ -> W^c -> Sigma_c (summed over q) -> QP energies and gap."""
-    om, g = freq_grid(sys.n_freq, sys.omega0)
+def g0w0(sys, qs=None, keep=False, dxv=None, grid=None):
+    """chi0 -> eps~ -> W^c -> Sigma_c (summed over q) -> QP energies and gap.
+
+    grid: (frequencies, weights) of the imaginary axis; None is the modified
+    Gauss-Legendre grid of scale sys.omega0."""
+    if grid is None:
+        om, g = freq_grid(sys.n_freq, sys.omega0)
+    else:
+        om, g = np.asarray(grid[0], dtype=np.float64), np.asarray(grid[1], dtype=np.float64)
     mu = mu_midgap(sys)
     qs = range(sys.n_k) if qs is None else qs
     nsig = sys.sigma_hi - sys.sigma_lo

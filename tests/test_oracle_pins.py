@@ -418,3 +418,52 @@ def test_shifted_mesh_by_a_mesh_vector_relabels_the_points():
         sig_s += O.sigma_q(s, q, W, om, g, mu)
         sig_t += O.sigma_q(t, q, W, om, g, mu)
     assert np.abs(sig_t - sig_s[perm]).max() <= 1e-13 * np.abs(sig_s).max()
+
+
+def _tan_midpoint(n, w0):
+    """Midpoint rule on w = w0 tan(t), t in (0, pi/2): nodes and weights for an integral over (0, inf)."""
+    t = (np.arange(n) + 0.5) * np.pi / (2 * n)
+    return w0 * np.tan(t), w0 * (np.pi / (2 * n)) / np.cos(t) ** 2
+
+
+def test_caller_grid_single_pole_sigma_analytic():
+    """A caller grid (tangent-mapped midpoint rule, not the default Gauss-Legendre one) carried through
+    the whole pipeline reproduces the single-pole Sigma_c of the two-band system at its own nodes:
+    the mapped integrand is smooth and periodic in t, so the rule converges spectrally."""
+    s = _twoband(32)
+    om, g = _tan_midpoint(32, 1.0)
+    r = O.g0w0(s, grid=(om, g))
+    assert np.array_equal(r["omega"], om) and np.array_equal(r["g"], g)
+    mu = r["mu"]
+    D = s.eps[0, 1] - s.eps[0, 0]
+    m = O.mo_triple(s, 0, 0, [1], [0])[:, 0, 0]
+    Vh = scipy.linalg.sqrtm(s.V[0])
+    y = Vh @ (Vh @ m)
+    Wp = math.sqrt(D * D + 2 * s.spin * D * np.vdot(Vh @ m, Vh @ m).real)
+    Mall = O.mo_triple(s, 0, 0, [0, 1], [0, 1])
+    ref = np.zeros_like(r["sigma"])
+    for n in range(2):
+        for mm in range(2):
+            a = (s.spin * D / Wp) * abs(np.sum(Mall[:, n, mm] * y)) ** 2
+            em = s.eps[0, mm]
+            ref[0, n] += a / (1j * om + mu - em - np.sign(em - mu) * Wp)
+    sel = om < 1.0
+    assert np.abs(r["sigma"] - ref)[..., sel].max() < 1e-12 * np.abs(ref).max()
+
+
+def test_caller_grid_order_and_weight_scaling():
+    """Reversing the nodes permutes Sigma_c and leaves the QP energies (a least-squares fit over all
+    nodes) unchanged; Sigma_c is linear in the weights; the default grid passed explicitly is the
+    default."""
+    s = make_system("cfg0", seed=0)
+    om, g = _tan_midpoint(s.n_freq, 2.0)
+    r = O.g0w0(s, grid=(om, g))
+    rv = O.g0w0(s, grid=(om[::-1], g[::-1]))
+    assert np.abs(rv["sigma"][..., ::-1] - r["sigma"]).max() < 1e-12 * np.abs(r["sigma"]).max()
+    assert np.abs(rv["e_qp"] - r["e_qp"]).max() < 1e-9
+    r2 = O.g0w0(s, qs=[0, 1], grid=(om, 2.0 * g))
+    r1 = O.g0w0(s, qs=[0, 1], grid=(om, g))
+    assert np.abs(r2["sigma"] - 2.0 * r1["sigma"]).max() < 1e-13 * np.abs(r1["sigma"]).max()
+    d = O.g0w0(s, qs=[0, 1])
+    e = O.g0w0(s, qs=[0, 1], grid=O.freq_grid(s.n_freq, s.omega0))
+    assert np.array_equal(d["sigma"], e["sigma"])
