@@ -99,8 +99,10 @@ typedef struct {
                                     of q -> 0 (128-point product rule on the sphere: 8 Gauss-
                                     Legendre nodes in cos(theta) x 16 equally spaced phi,
                                     offset by half a step; qhat unused); 0: regular formula */
-  int32_t n_freq;                /* imaginary frequencies, modified Gauss-Legendre, 1..256   */
-  double omega0;                 /* grid scale: w_j = omega0 (1+x_j)/(1-x_j) (Ha), > 0       */
+  int32_t n_freq;                /* imaginary frequencies, 1..256                            */
+  double omega0;                 /* scale of the default grid (freq NULL): modified Gauss-
+                                    Legendre w_j = omega0 (1+x_j)/(1-x_j), g_j = 2 omega0 v_j /
+                                    (1-x_j)^2 (x_j, v_j Gauss-Legendre on (-1, 1)); Ha, > 0     */
   int32_t sigma_lo, sigma_hi;    /* self-energy bands [sigma_lo, sigma_hi), 0-based          */
   double spin;                   /* spin factor in chi0 (2 for doubly occupied bands)        */
   double mu;                     /* chemical potential; NaN selects midgap                   */
@@ -121,7 +123,16 @@ typedef struct {
                                     on the shifted mesh. All zero: the Gamma-centred mesh. A
                                     shifted plan gives Sigma_c at off-mesh k (its point 0 is k0)
                                     through gw_sigma_ext with the W^c of an unshifted plan.    */
+  const double* freq;            /* host [n_freq]: the caller's imaginary frequencies w_j > 0
+                                    (Ha, distinct), the grid of chi0 / eps~ / W^c and of the
+                                    Sigma_c output; NULL: the default grid above (copied)      */
+  const double* freq_w;          /* host [n_freq]: their weights g_j > 0 for the folded w'
+                                    integral over (0, inf) of Eq. GW_selfe_element; NULL with
+                                    freq NULL (both or neither)                                */
 } gw_problem;
+
+/* sizeof(gw_problem) as compiled into the library (a binding checks its own layout against it). */
+size_t gw_problem_bytes(void);
 
 /* Build a plan: validates `prob`, copies the host arrays, allocates the
  * library's own workspace, and on `stream` precomputes the half-transformed

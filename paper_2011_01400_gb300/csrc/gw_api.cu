@@ -572,7 +572,17 @@ gw_status validate(const gw_problem* p, int n_sys) {
   if (p->head_wings && (!p->pmom || !(p->omega_cell > 0.0)))
     return fail(GW_ERR_ARG, "head_wings needs pmom and omega_cell > 0");
   if (p->n_freq < 1 || p->n_freq > 256) return fail(GW_ERR_ARG, "n_freq out of range [1, 256]");
-  if (!(p->omega0 > 0.0)) return fail(GW_ERR_ARG, "omega0 must be > 0");
+  if ((p->freq == nullptr) != (p->freq_w == nullptr)) return fail(GW_ERR_ARG, "freq and freq_w: both or neither");
+  if (p->freq) {
+    for (int j = 0; j < p->n_freq; ++j) {
+      if (!(p->freq[j] > 0.0) || !std::isfinite(p->freq[j]) || !(p->freq_w[j] > 0.0) || !std::isfinite(p->freq_w[j]))
+        return fail(GW_ERR_ARG, "freq and freq_w must be positive and finite");
+      for (int i = 0; i < j; ++i)
+        if (p->freq[i] == p->freq[j]) return fail(GW_ERR_ARG, "freq must be distinct");
+    }
+  } else if (!(p->omega0 > 0.0)) {
+    return fail(GW_ERR_ARG, "omega0 must be > 0");
+  }
   if (p->sigma_lo < 0 || p->sigma_hi > p->n_bands || p->sigma_lo >= p->sigma_hi)
     return fail(GW_ERR_ARG, "sigma window must satisfy 0 <= lo < hi <= n_bands");
   if (!(p->spin > 0.0)) return fail(GW_ERR_ARG, "spin must be > 0");
@@ -633,6 +643,8 @@ bool plan_ok(gw_plan P, int32_t sys, gw_status* s) {
 extern "C" {
 
 const char* gw_last_error(void) { return g_last_error.c_str(); }
+
+size_t gw_problem_bytes(void) { return sizeof(gw_problem); }
 
 gw_status gw_device_allocations(uint64_t* count) {
   if (!count) return fail(GW_ERR_ARG, "count is NULL");
@@ -699,6 +711,8 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
   P->p.basis_atom = P->basis_atom.data();
   P->p.aux_atom = P->aux_atom.data();
   P->p.R = P->R.data();
+  P->p.freq = nullptr;   // the grid itself lives in P->freq / P->fweight
+  P->p.freq_w = nullptr;
   if (const char* v = std::getenv("GW_WORKSPACE_LIMIT")) {
     const double lim = std::atof(v);
     if (lim > 0) P->ws_limit = (size_t)lim;
@@ -747,14 +761,21 @@ gw_status gw_plan_create(const gw_problem* prob, int32_t n_sys, void* stream, gw
   }
   for (int r = 0; r < prob->n_R; ++r)
     for (int d = 0; d < 3; ++d) g.R[r][d] = P->R[3 * r + d];
-  // frequency grid
-  std::vector<double> x, w;
-  gauss_legendre(P->nw, x, w);
+  // frequency grid: the caller's, or the modified Gauss-Legendre grid of scale omega0
   P->freq.resize(P->nw);
   P->fweight.resize(P->nw);
-  for (int j = 0; j < P->nw; ++j) {
-    P->freq[j] = prob->omega0 * (1.0 + x[j]) / (1.0 - x[j]);
-    P->fweight[j] = 2.0 * prob->omega0 * w[j] / ((1.0 - x[j]) * (1.0 - x[j]));
+  if (prob->freq) {
+    for (int j = 0; j < P->nw; ++j) {
+      P->freq[j] = prob->freq[j];
+      P->fweight[j] = prob->freq_w[j];
+    }
+  } else {
+    std::vector<double> x, w;
+    gauss_legendre(P->nw, x, w);
+    for (int j = 0; j < P->nw; ++j) {
+      P->freq[j] = prob->omega0 * (1.0 + x[j]) / (1.0 - x[j]);
+      P->fweight[j] = 2.0 * prob->omega0 * w[j] / ((1.0 - x[j]) * (1.0 - x[j]));
+    }
   }
   const int N = P->N, nw = P->nw;
   const size_t NN = (size_t)N * N;

@@ -29,7 +29,7 @@ EXPORTS = ("gw_plan_create", "gw_plan_destroy", "gw_chi0", "gw_screen", "gw_sigm
            "gw_surrogate_param_count", "gw_surrogate_create", "gw_surrogate_destroy", "gw_surrogate_get_params",
            "gw_surrogate_set_params", "gw_surrogate_forward", "gw_surrogate_loss_grad", "gw_surrogate_fit_linear",
            "gw_surrogate_train", "gw_surrogate_enable", "gw_surrogate_modes", "gw_surrogate_data", "gw_surrogate_fit_moments",
-           "gw_surrogate_fit_scale", "gw_last_error")
+           "gw_surrogate_fit_scale", "gw_problem_bytes", "gw_last_error")
 
 
 class GwError(RuntimeError):
@@ -73,6 +73,8 @@ class gw_problem(ctypes.Structure):
         ("prec", ctypes.c_int32),
         ("time_reversal", ctypes.c_int32),
         ("k_offset", ctypes.c_double * 3),
+        ("freq", ctypes.POINTER(ctypes.c_double)),
+        ("freq_w", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -124,8 +126,10 @@ def load():
     lib.gw_surrogate_fit_moments.argtypes = [vp, vp, ctypes.c_double]
     lib.gw_surrogate_fit_scale.argtypes = [vp, vp, vp, i64, dpp]
     lib.gw_last_error.restype = ctypes.c_char_p
+    lib.gw_problem_bytes.argtypes = []
+    lib.gw_problem_bytes.restype = ctypes.c_size_t
     for name in EXPORTS:
-        if name != "gw_last_error":
+        if name not in ("gw_last_error", "gw_problem_bytes"):
             getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -360,7 +364,7 @@ def gw_surrogate_fit_scale(model, x, y):
 class Problem:
     """Keeps the device tensors and host arrays that a gw_problem points to alive."""
 
-    def __init__(self, system, prec="3xbf16", device="cuda", host=False, trs=None, mu=None):
+    def __init__(self, system, prec="3xbf16", device="cuda", host=False, trs=None, mu=None, grid=None):
         import torch
         s = system
         self.system = s
@@ -401,6 +405,14 @@ class Problem:
         # time-reversal symmetric inputs (the generator's default) let the q loop pair q with -q
         p.time_reversal = int(bool(getattr(s, "trs", False) if trs is None else trs))
         p.k_offset[:] = [float(x) for x in getattr(s, "k_offset", (0.0, 0.0, 0.0))]
+        # a caller's imaginary-frequency grid (freq, weights); None keeps the default grid of omega0
+        if grid is not None:
+            self.freq = np.ascontiguousarray(grid[0], dtype=np.float64)
+            self.freq_w = np.ascontiguousarray(grid[1], dtype=np.float64)
+            if self.freq.shape != (s.n_freq,) or self.freq_w.shape != (s.n_freq,):
+                raise ValueError("grid: freq and weights need n_freq entries each")
+            p.freq = self.freq.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            p.freq_w = self.freq_w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.prob = p
 
     def upload(self):

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "gw.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:gw_status|const char\*)\s+(gw_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:gw_status|const char\*|size_t)\s+(gw_\w+)\s*\(", src, re.M)))
 
 
 def test_header_declares_the_boundary():
@@ -30,6 +30,7 @@ def test_library_builds_loads_and_exports():
     for n in declared_symbols():
         assert hasattr(lib, n), n
     assert lib.gw_last_error() is not None
+    assert lib.gw_problem_bytes() == gw.ctypes.sizeof(gw.gw_problem)
 
 
 def test_struct_layout_matches_header():
@@ -40,6 +41,8 @@ def test_struct_layout_matches_header():
     assert p.eps.offset % 8 == 0 and p.qhat.offset % 8 == 0
     assert p.prec.offset + 4 <= gw.ctypes.sizeof(p)
     assert p.time_reversal.offset == p.prec.offset + 4
+    assert p.freq.offset == p.k_offset.offset + 24 and p.freq_w.offset == p.freq.offset + 8
+    assert gw.ctypes.sizeof(p) == p.freq_w.offset + 8
 
 
 def test_null_arguments_are_rejected_without_gpu():

@@ -128,3 +128,46 @@ def test_surrogate_dims_are_checked(lib, dims):
     d = gw.gw_surrogate_dims(*dims)
     assert lib.gw_surrogate_create(ctypes.byref(d), None, None, ctypes.byref(h)) == gw.GW_ERR_ARG
     assert not h.value
+
+
+GRID_CASES = [
+    ("freq without weights", [1.0, 2.0], None, "both or neither"),
+    ("weights without freq", None, [1.0, 2.0], "both or neither"),
+    ("zero frequency", [0.0, 2.0], [1.0, 1.0], "positive and finite"),
+    ("negative weight", [1.0, 2.0], [1.0, -1.0], "positive and finite"),
+    ("infinite frequency", [1.0, float("inf")], [1.0, 1.0], "positive and finite"),
+    ("nan weight", [1.0, 2.0], [float("nan"), 1.0], "positive and finite"),
+    ("repeated frequency", [2.0, 2.0], [1.0, 1.0], "freq must be distinct"),
+]
+
+
+@pytest.mark.parametrize("name,freq,wts,expect", GRID_CASES, ids=[c[0] for c in GRID_CASES])
+def test_caller_grid_is_checked(lib, name, freq, wts, expect):
+    p, keep = base()
+    p.n_freq = 2
+
+    def darr(vals):
+        a = (ctypes.c_double * len(vals))(*vals)
+        keep.append(a)
+        return ctypes.cast(a, ctypes.POINTER(ctypes.c_double))
+
+    if freq is not None:
+        p.freq = darr(freq)
+    if wts is not None:
+        p.freq_w = darr(wts)
+    st, msg = create(lib, p)
+    assert st == gw.GW_ERR_ARG, (name, st, msg)
+    assert expect in msg, (name, msg)
+
+
+def test_caller_grid_replaces_omega0(lib):
+    """With a grid given, omega0 is not read: a zero omega0 passes to the next check (the guard)."""
+    p, keep = base()
+    p.n_freq, p.omega0 = 2, 0.0
+    f = (ctypes.c_double * 2)(0.5, 3.0)
+    w = (ctypes.c_double * 2)(1.0, 4.0)
+    keep += [f, w]
+    p.freq = ctypes.cast(f, ctypes.POINTER(ctypes.c_double))
+    p.freq_w = ctypes.cast(w, ctypes.POINTER(ctypes.c_double))
+    st, msg = create(lib, p)
+    assert st == gw.GW_ERR_ARG and "aux_atom must be non-decreasing" in msg
