@@ -107,7 +107,6 @@ template <typename T> void launch_axpby_identity(int N, cplx<T>* A, long long s,
 void launch_take_both(int N, const c128* C, long long s, int batch, float d, c64* X, c64* XH, cudaStream_t st);
 void launch_dev_identity(int N, const c64* T, long long total, unsigned* dev, cudaStream_t st);
 void launch_convert(int n, const c128* in, c64* out, cudaStream_t st);
-void launch_convert_back(int n, const c64* in, c128* out, cudaStream_t st);
 // dominant eigenpair of a Hermitian matrix by power iteration (FP64)
 void launch_power_iter(int N, const c128* A, c128* x, double* lam, int iters, cudaStream_t st);
 // A += alpha * x x^H

@@ -845,7 +845,7 @@ gw_status chi0h_run(const Chi0hArgs& a, Chi0Plan** plan, cudaStream_t st, std::s
     err = "chi0: Kpad must be a multiple of 32";
     return GW_ERR_ARG;
   }
-  const int RS = (a.kind == 2) ? Kd<K_TF32, 1>::RS : Kd<K_F16, 1>::RS;
+  const int RS = (a.kind == 2) ? Kd<K_TF32, 1>::RS : (a.kind == 1 ? Kd<K_BF16, 1>::RS : Kd<K_F16, 1>::RS);
   const int nst = a.Kpad / RS;
   const int seg = std::max(1, a.seg_rows / RS);
   const int tp = a.kind == 0 ? TP_F16 : a.kind == 1 ? 1 : TP_TF32;

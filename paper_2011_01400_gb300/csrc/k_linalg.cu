@@ -547,15 +547,8 @@ __global__ void k_convert(int n, const c128* in, c64* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     out[i] = c64{(float)in[i].re, (float)in[i].im};
 }
-__global__ void k_convert_back(int n, const c64* in, c128* out) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    out[i] = c128{(double)in[i].re, (double)in[i].im};
-}
 void launch_convert(int n, const c128* in, c64* out, cudaStream_t st) {
   ++::gw::g_launch_count, k_convert<<<std::min((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, in, out);
-}
-void launch_convert_back(int n, const c64* in, c128* out, cudaStream_t st) {
-  ++::gw::g_launch_count, k_convert_back<<<std::min((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, in, out);
 }
 
 // Dominant eigenpair by power iteration with a Rayleigh quotient (one block, FP64). Each warp
