@@ -81,14 +81,17 @@ __global__ void k_wproj(int nw, const c128* __restrict__ Uh, const double* __res
 }
 
 // err[j][T] += sum_r (W_jr - sum_{t<T} E_jt v_tr)^2 for T = 0 .. nw, v_t = sum_j P_jt W_j.
-// Tiles of 64 pair rows: W and v of the tile in shared memory; thread (j, quarter) keeps the
-// running residual of frequency j over 16 rows and its squares for every T in registers.
+// Tiles of 64 pair rows: W and v of the tile in shared memory; thread (j, grp) keeps the running
+// residual of frequency j over its rows of the tile and its squares for every T in registers.
 __global__ void __launch_bounds__(256) k_wresid(int K, int nw, const double* __restrict__ delta,
                                                 const double* __restrict__ freq, const double* __restrict__ E,
                                                 const double* __restrict__ Pm, double* __restrict__ err) {
   __shared__ double ws[64][65];  // [row][j]
   __shared__ double vs[64][65];  // [row][t]
-  const int j = threadIdx.x % 64, quarter = threadIdx.x / 64;
+  // residual phase: thread (j, grp) takes frequency j and rows grp, grp + ng, ... of the chunk, so
+  // that ng * nw <= 256 threads are busy for every nw (not 64 of each 64-thread quarter)
+  const int ng = blockDim.x / nw;
+  const int j = threadIdx.x % nw, grp = threadIdx.x / nw;
   double acc[65];
 #pragma unroll
   for (int T = 0; T < 65; ++T) acc[T] = 0.0;
@@ -110,8 +113,8 @@ __global__ void __launch_bounds__(256) k_wresid(int K, int nw, const double* __r
       vs[rr][t] = sv;
     }
     __syncthreads();
-    if (j < nw) {
-      for (int rr = quarter * 16; rr < quarter * 16 + 16; ++rr) {
+    if (grp < ng) {
+      for (int rr = grp; rr < 64; rr += ng) {
         double res = ws[rr][j];
 #pragma unroll
         for (int T = 0; T < 65; ++T) {
@@ -124,8 +127,17 @@ __global__ void __launch_bounds__(256) k_wresid(int K, int nw, const double* __r
     }
     __syncthreads();
   }
-  if (j < nw)
-    for (int T = 0; T <= nw; ++T) atomicAdd(&err[j * (nw + 1) + T], acc[T]);
+  // the groups' sums meet in shared memory (ws is free now), then one global add per (j, T)
+  double* red = &ws[0][0];
+  for (int e = threadIdx.x; e < nw * (nw + 1); e += blockDim.x) red[e] = 0.0;
+  __syncthreads();
+  if (grp < ng) {
+#pragma unroll
+    for (int T = 0; T < 65; ++T)
+      if (T <= nw) atomicAdd(&red[j * (nw + 1) + T], acc[T]);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nw * (nw + 1); e += blockDim.x) atomicAdd(&err[e], red[e]);
 }
 
 // v[t][r] = sum_j P[j][t] W_jr (FP64 sum, fp32 out) for t < T, r < Kpad (0 beyond K)

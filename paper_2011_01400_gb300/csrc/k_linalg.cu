@@ -750,14 +750,19 @@ void launch_q0_correction(int N, int nw, c128* eps_t, const c128* x1, const c128
 // Cartesian pieces, accumulated over pair rows (all k): the head tensor
 //   A6[w] = pref sum_r 2 Re(conj(p_a) p_b) / (D (D^2 + w^2)),  (a, b) = xx, yy, zz, xy, xz, yz,
 // and the wing vectors h3[w][a][nu] = sum_r conj(p_a,r) M^nu_r 2 / (w^2 + D^2), pq3[a][r] = p_a(k)_{ia}.
+constexpr int HW3_NB = 8;   // wing rows nu per block: the weight and the p_a(r) loads serve all of them
+
+// Grid (nw, ceil(N / HW3_NB) + 1): the frequency varies fastest, so the blocks that read the same
+// rows of M run together and share them in L2; the last row of blocks computes A6.
 template <typename T>
-__global__ void k_head_wings3(int N, int K, const cplx<T>* __restrict__ Mt, long long ldm,
-                              const double* __restrict__ delta, const c128* __restrict__ pq3, long long ldp,
-                              const double* __restrict__ freq, double pref, double* A6, c128* h3) {
+__global__ void __launch_bounds__(256) k_head_wings3(int N, int K, const cplx<T>* __restrict__ Mt, long long ldm,
+                                                     const double* __restrict__ delta, const c128* __restrict__ pq3,
+                                                     long long ldp, const double* __restrict__ freq, double pref,
+                                                     double* A6, c128* h3) {
   __shared__ double red[32];
-  const int nu = blockIdx.x, w_i = blockIdx.y;
+  const int w_i = blockIdx.x;
   const double om = freq[w_i];
-  if (nu == N) {
+  if ((int)blockIdx.y * HW3_NB >= N) {
     double part[6] = {0, 0, 0, 0, 0, 0};
     for (int r = threadIdx.x; r < K; r += blockDim.x) {
       const double d = delta[r];
@@ -776,24 +781,48 @@ __global__ void k_head_wings3(int N, int K, const cplx<T>* __restrict__ Mt, long
     }
     return;
   }
-  double sr[3] = {0, 0, 0}, si[3] = {0, 0, 0};
+  const int nu0 = blockIdx.y * HW3_NB;
+  const int nv = min(HW3_NB, N - nu0);
+  double sr[HW3_NB][3], si[HW3_NB][3];
+#pragma unroll
+  for (int u = 0; u < HW3_NB; ++u)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) sr[u][a] = si[u][a] = 0.0;
   for (int r = threadIdx.x; r < K; r += blockDim.x) {
     const double d = delta[r];
     const double wt = 2.0 / (om * om + d * d);
-    const cplx<T> m = Mt[(long long)nu * ldm + r];
+    c128 pw[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const c128 pp = pq3[a * ldp + r];
-      sr[a] += wt * (pp.re * (double)m.re + pp.im * (double)m.im);
-      si[a] += wt * (pp.re * (double)m.im - pp.im * (double)m.re);
+      pw[a] = c128{wt * pp.re, wt * pp.im};
+    }
+#pragma unroll
+    for (int u = 0; u < HW3_NB; ++u) {
+      if (u < nv) {
+        const cplx<T> m = Mt[(long long)(nu0 + u) * ldm + r];
+        const double mr = (double)m.re, mi = (double)m.im;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          sr[u][a] += pw[a].re * mr + pw[a].im * mi;
+          si[u][a] += pw[a].re * mi - pw[a].im * mr;
+        }
+      }
     }
   }
-  for (int a = 0; a < 3; ++a) {
-    const double x = block_sum(sr[a], red);
-    const double y = block_sum(si[a], red);
-    if (threadIdx.x == 0) {
-      h3[((long long)w_i * 3 + a) * N + nu].re += x;
-      h3[((long long)w_i * 3 + a) * N + nu].im += y;
+#pragma unroll
+  for (int u = 0; u < HW3_NB; ++u) {
+    if (u < nv) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const double x = block_sum(sr[u][a], red);
+        const double y = block_sum(si[u][a], red);
+        if (threadIdx.x == 0) {
+          c128& o = h3[((long long)w_i * 3 + a) * N + nu0 + u];
+          o.re += x;
+          o.im += y;
+        }
+      }
     }
   }
 }
@@ -801,7 +830,7 @@ template <typename T>
 void launch_head_wings3(int N, int K, const cplx<T>* Mt, long long ldm, const double* delta, const c128* pq3,
                         long long ldp, const double* freq, int nw, double pref, double* A6, c128* h3,
                         cudaStream_t st) {
-  dim3 grid(N + 1, nw);
+  dim3 grid(nw, (N + HW3_NB - 1) / HW3_NB + 1);
   ++::gw::g_launch_count, k_head_wings3<T><<<grid, 256, 0, st>>>(N, K, Mt, ldm, delta, pq3, ldp, freq, pref, A6, h3);
 }
 template void launch_head_wings3<double>(int, int, const c128*, long long, const double*, const c128*, long long,
