@@ -44,6 +44,7 @@
 #ifndef GW_H
 #define GW_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus

@@ -53,3 +53,28 @@ def test_null_arguments_are_rejected_without_gpu():
     assert b"NULL" in lib.gw_last_error()
     assert lib.gw_chi0(None, 0, 0, None) == gw.GW_ERR_ARG
     assert lib.gw_plan_destroy(None) == gw.GW_OK
+
+
+@pytest.mark.skipif(B.shutil.which("gcc") is None, reason="no C compiler")
+def test_header_is_plain_c_and_cxx(tmp_path):
+    """include/gw.h compiles on its own as C99 and as C++11 (pedantic, warnings as errors), and a C
+    caller's sizeof(gw_problem) equals the library's."""
+    import subprocess
+    inc = os.path.join(ROOT, "include")
+    src = tmp_path / "caller.c"
+    src.write_text('#include "gw.h"\n#include <stdio.h>\n'
+                   'int main(void) { printf("%zu %zu\\n", sizeof(gw_problem), gw_problem_bytes()); return 0; }\n')
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, "-c", str(src),
+                    "-o", str(tmp_path / "caller.o")], check=True)
+    cxx = tmp_path / "caller.cpp"
+    cxx.write_text('#include "gw.h"\nint main() { return sizeof(gw_problem) > 0 ? 0 : 1; }\n')
+    if B.shutil.which("g++"):
+        subprocess.run(["g++", "-std=c++11", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, "-c", str(cxx),
+                        "-o", str(tmp_path / "caller_cxx.o")], check=True)
+    B.build()
+    lib_dir = os.path.dirname(gw.LIB_PATH)
+    exe = tmp_path / "caller"
+    subprocess.run(["gcc", str(tmp_path / "caller.o"), "-L", lib_dir, "-lgw", "-Wl,-rpath," + lib_dir, "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert out[0] == out[1]
