@@ -125,6 +125,7 @@ def load():
     lib.gw_surrogate_data.argtypes = [vp, i32, vp, vp, vp]
     lib.gw_surrogate_fit_moments.argtypes = [vp, vp, ctypes.c_double]
     lib.gw_surrogate_fit_scale.argtypes = [vp, vp, vp, i64, dpp]
+    lib.gw_last_error.argtypes = []
     lib.gw_last_error.restype = ctypes.c_char_p
     lib.gw_problem_bytes.argtypes = []
     lib.gw_problem_bytes.restype = ctypes.c_size_t

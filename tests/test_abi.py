@@ -78,3 +78,18 @@ def test_header_is_plain_c_and_cxx(tmp_path):
                    check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     assert out[0] == out[1]
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every declared entry point has as many ctypes argument types in the binding as the header
+    declares parameters (a dropped or extra argument would shift every pointer after it)."""
+    src = open(os.path.join(ROOT, "include", "gw.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    decls = re.findall(r"(?:gw_status|const char\*|size_t)\s+(gw_\w+)\s*\(([^)]*)\)\s*;", src)
+    assert len(decls) == len(gw.EXPORTS)
+    B.build()
+    lib = gw.load()
+    for name, args in decls:
+        a = args.strip()
+        n = 0 if a in ("", "void") else a.count(",") + 1
+        assert len(getattr(lib, name).argtypes) == n, name
