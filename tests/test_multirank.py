@@ -1,8 +1,10 @@
 """The N > 1 host path of bench.py on CPU: two gloo ranks (world size 2) on 127.0.0.1.
 
-bench.py runs one replica per GPU (weak scaling, no data-path collective). Its only cross-rank
-steps are the barrier around the timed region and the maximum of the step times over the
-ranks; the whole-job value is the systems all ranks processed over that maximum. Here the same
+In its replica mode (`--parallel replicas`: one independent system per GPU, weak scaling, no
+data-path collective) bench.py's only cross-rank steps are the barrier around the timed region
+and the maximum of the step times over the ranks; the whole-job value is the systems all ranks
+processed over that maximum. The q-sharded default mode (one system, one sum of Sigma_c over the
+ranks) is covered by test_shard_gloo.py. Here the same
 helpers run under gloo with planted per-rank times, and the reference arm's rank handling (rank 0
 alone prints) is checked in-process."""
 import io
