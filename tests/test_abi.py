@@ -1,4 +1,5 @@
-"""The C-ABI library builds for sm_103a, loads without a GPU and exports every declared symbol."""
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every declared symbol; the
+header is plain C and C++, and the binding's struct layout and argument counts match it."""
 import os
 import re
 

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on identical seeded inputs.
 
-Tolerances: FP64 method 1e-11 relative; split precision (3xTF32, 3xBF16) relative
+Tolerances: FP64 method 1e-11 relative; split precision (3xTF32, 3xBF16, 3xFP16) relative
 Frobenius error of chi0 <= 1e-6 per (q, w); Sigma_c and the QP gap within 1 meV. W^c has no target
 of its own: W^c = V^1/2 (eps~^-1 - 1) V^1/2 is, at the top frequencies, a difference 1e-2..1e-3 of
 its terms, so its relative error is the terms' rounding divided by that ratio; it is bounded at
