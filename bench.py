@@ -688,7 +688,7 @@ def run_device(args, system, world, rank):
         data="synthetic",
         config=dict(workload=WORKLOADS[args.config] + (f" (k mesh overridden to {args.nk})" if args.nk else ""),
                     name=args.config, precision=args.prec, systems_per_step=1 if qshard else world,
-                    q_loop="q-parallel (gw_g0w0_qset + Sigma_c sum over ranks)" if qshard else args.qloop,
+                    q_loop="q-parallel (gw_g0w0_qset, pairs {q, -q} kept on one rank, + Sigma_c sum over ranks)" if qshard else args.qloop,
                     global_batch=1 if qshard else world, seq_len=0, parallelism=mode if world > 1 else "single",
                     time_reversal=bool(getattr(s, "trs", False)),
                     q0={0: "regular formula", 1: "head and wings along x", 2: "head and wings averaged over the "

@@ -76,3 +76,36 @@ def test_partition_covers_the_mesh_once_and_balances(n_q, world):
 def test_single_process_needs_no_group():
     acc = shard.sharded_sigma(lambda qs, a: a.add_(len(qs)), 4, 1, 1, "cpu")
     assert float(acc.real.sum()) == 16.0
+
+
+@pytest.mark.parametrize("nk", [(2, 2, 2), (3, 3, 3), (4, 2, 1), (6, 6, 6), (5, 1, 3)])
+def test_minus_q_is_the_mesh_inversion(nk):
+    n_q = nk[0] * nk[1] * nk[2]
+    assert shard.minus_q(nk, 0) == 0
+    for q in range(n_q):
+        mq = shard.minus_q(nk, q)
+        assert 0 <= mq < n_q and shard.minus_q(nk, mq) == q
+        i = (q // (nk[1] * nk[2]), (q // nk[2]) % nk[1], q % nk[2])
+        j = (mq // (nk[1] * nk[2]), (mq // nk[2]) % nk[1], mq % nk[2])
+        assert all((a + b) % n == 0 for a, b, n in zip(i, j, nk))      # k + (-k) on the mesh
+
+
+@pytest.mark.parametrize("nk", [(2, 2, 2), (3, 3, 3), (4, 2, 1), (6, 6, 6)])
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_pair_partition_keeps_q_and_minus_q_together(nk, world):
+    """With time-reversal pairing every rank's list is closed under q -> -q (its q loop computes
+    chi0 / eps~ / W^c once per pair), the mesh is covered once, and the ranks' work differs by at
+    most one unit."""
+    n_q = nk[0] * nk[1] * nk[2]
+    parts = shard.q_partition(n_q, world, nk=nk)
+    flat = [q for p in parts for q in p]
+    assert sorted(flat) == list(range(n_q))
+    for p in parts:
+        assert p == sorted(p)
+        assert all(shard.minus_q(nk, q) in p for q in p)
+    units = shard.q_units(n_q, nk)
+    cost = {u[0]: shard.unit_cost(u, nk=nk) for u in units}
+    work = [sum(cost[u[0]] for u in units if u[0] in p) for p in parts]
+    assert max(work) - min(work) <= max(cost.values()) + 1e-12
+    # without pairing nothing changes
+    assert shard.q_partition(n_q, world) == shard.q_partition(n_q, world, nk=None)
