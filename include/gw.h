@@ -94,7 +94,8 @@ typedef struct {
   const gw_complex* pmom;        /* device [N_k][3][n_bands][n_bands] momentum matrix p_mn(k);
                                     may be NULL when head_wings == 0                          */
   double omega_cell;             /* unit-cell volume (bohr^3), > 0 when head_wings != 0      */
-  double qhat[3];                /* direction of q -> 0 for the head and wings               */
+  double qhat[3];                /* direction of q -> 0 for the head and wings: a unit vector
+                                    (|qhat|^2 = 1 within 1e-9, checked when head_wings == 1) */
   int32_t head_wings;            /* 1: Gamma point by Eq. dielectric_func_gamma along qhat;
                                     2: the same with eps~^-1 - 1 averaged over the direction
                                     of q -> 0 (128-point product rule on the sphere: 8 Gauss-

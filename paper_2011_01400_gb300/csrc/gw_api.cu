@@ -571,6 +571,10 @@ gw_status validate(const gw_problem* p, int n_sys) {
     return fail(GW_ERR_ARG, "time_reversal needs an unshifted k mesh (k_offset = 0)");
   if (p->head_wings && (!p->pmom || !(p->omega_cell > 0.0)))
     return fail(GW_ERR_ARG, "head_wings needs pmom and omega_cell > 0");
+  if (p->head_wings == 1) {
+    const double q2 = p->qhat[0] * p->qhat[0] + p->qhat[1] * p->qhat[1] + p->qhat[2] * p->qhat[2];
+    if (!(std::fabs(q2 - 1.0) <= 1e-9)) return fail(GW_ERR_ARG, "head_wings = 1 needs a unit vector qhat");
+  }
   if (p->n_freq < 1 || p->n_freq > 256) return fail(GW_ERR_ARG, "n_freq out of range [1, 256]");
   if ((p->freq == nullptr) != (p->freq_w == nullptr)) return fail(GW_ERR_ARG, "freq and freq_w: both or neither");
   if (p->freq) {

@@ -70,6 +70,9 @@ CASES = [
     ("n_R", lambda p: setattr(p, "n_R", 0), "n_R out of range"),
     ("V NULL", lambda p: setattr(p, "V", None), "a device input pointer is NULL"),
     ("head_wings without pmom", lambda p: setattr(p, "head_wings", 1), "head_wings needs pmom"),
+    ("qhat not a unit vector", lambda p: (setattr(p, "head_wings", 1), setattr(p, "pmom", FAKE),
+                                          p.qhat.__setitem__(slice(0, 3), (0.5, 0.0, 0.0))), "unit vector qhat"),
+    ("qhat zero", lambda p: (setattr(p, "head_wings", 1), setattr(p, "pmom", FAKE)), "unit vector qhat"),
     ("n_freq", lambda p: setattr(p, "n_freq", 0), "n_freq out of range"),
     ("omega0", lambda p: setattr(p, "omega0", 0.0), "omega0 must be > 0"),
     ("sigma window", lambda p: setattr(p, "sigma_hi", 7), "sigma window"),
