@@ -107,7 +107,7 @@ typedef struct {
                                     (1-x_j)^2 (x_j, v_j Gauss-Legendre on (-1, 1)); Ha, > 0     */
   int32_t sigma_lo, sigma_hi;    /* self-energy bands [sigma_lo, sigma_hi), 0-based          */
   double spin;                   /* spin factor in chi0 (2 for doubly occupied bands)        */
-  double mu;                     /* chemical potential; NaN selects midgap                   */
+  double mu;                     /* chemical potential (finite); NaN selects midgap          */
   gw_precision prec;
   int32_t time_reversal;         /* 1: the inputs are time-reversal symmetric (real NAOs and
                                     ABFs, no magnetism): eps(-k) = eps(k), c(-k) = conj(c(k))

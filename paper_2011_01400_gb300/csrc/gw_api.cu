@@ -569,7 +569,7 @@ gw_status validate(const gw_problem* p, int n_sys) {
     if (!(std::fabs(p->k_offset[d]) <= 1.0)) return fail(GW_ERR_ARG, "k_offset components must be in [-1, 1]");
   if (p->time_reversal && (p->k_offset[0] != 0.0 || p->k_offset[1] != 0.0 || p->k_offset[2] != 0.0))
     return fail(GW_ERR_ARG, "time_reversal needs an unshifted k mesh (k_offset = 0)");
-  if (p->head_wings && (!p->pmom || !(p->omega_cell > 0.0)))
+  if (p->head_wings && (!p->pmom || !(p->omega_cell > 0.0) || !std::isfinite(p->omega_cell)))
     return fail(GW_ERR_ARG, "head_wings needs pmom and omega_cell > 0");
   if (p->head_wings == 1) {
     const double q2 = p->qhat[0] * p->qhat[0] + p->qhat[1] * p->qhat[1] + p->qhat[2] * p->qhat[2];
@@ -584,12 +584,13 @@ gw_status validate(const gw_problem* p, int n_sys) {
       for (int i = 0; i < j; ++i)
         if (p->freq[i] == p->freq[j]) return fail(GW_ERR_ARG, "freq must be distinct");
     }
-  } else if (!(p->omega0 > 0.0)) {
+  } else if (!(p->omega0 > 0.0) || !std::isfinite(p->omega0)) {
     return fail(GW_ERR_ARG, "omega0 must be > 0");
   }
   if (p->sigma_lo < 0 || p->sigma_hi > p->n_bands || p->sigma_lo >= p->sigma_hi)
     return fail(GW_ERR_ARG, "sigma window must satisfy 0 <= lo < hi <= n_bands");
-  if (!(p->spin > 0.0)) return fail(GW_ERR_ARG, "spin must be > 0");
+  if (!(p->spin > 0.0) || !std::isfinite(p->spin)) return fail(GW_ERR_ARG, "spin must be > 0");
+  if (std::isinf(p->mu)) return fail(GW_ERR_ARG, "mu must be finite (or NaN for midgap)");
   if (p->prec != GW_FP64 && p->prec != GW_3XTF32 && p->prec != GW_3XBF16 && p->prec != GW_3XFP16)
     return fail(GW_ERR_ARG, "bad precision");
   for (int i = 0; i < p->n_basis; ++i) {

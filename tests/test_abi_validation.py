@@ -78,6 +78,9 @@ CASES = [
     ("sigma window", lambda p: setattr(p, "sigma_hi", 7), "sigma window"),
     ("sigma empty", lambda p: setattr(p, "sigma_lo", 4), "sigma window"),
     ("spin", lambda p: setattr(p, "spin", 0.0), "spin must be > 0"),
+    ("spin infinite", lambda p: setattr(p, "spin", float("inf")), "spin must be > 0"),
+    ("omega0 infinite", lambda p: setattr(p, "omega0", float("inf")), "omega0 must be > 0"),
+    ("mu infinite", lambda p: setattr(p, "mu", float("-inf")), "mu must be finite"),
     ("precision", lambda p: setattr(p, "prec", 9), "bad precision"),
 ]
 
